@@ -1,0 +1,165 @@
+/*
+ * lrspike.h -- C ABI of the GB300-native Low-Rank SPIKE (LR-SPIKE) solver.
+ *
+ * Solves banded systems A x = f (and A^T x = h) with the LR-SPIKE scheme of
+ * Spring, Polizzi and Sameh, "Low-Rank SPIKE Framework for Solving Large Sparse
+ * Linear Systems with Applications" (arXiv 2504.11167):
+ *   - A is n x n with half-bandwidth k on both sides (section 2.1, "SPIKE
+ *     partitioning": a matrix with unequal bandwidths uses the larger one);
+ *   - it is split into p diagonal blocks A_i of roughly equal size n_i > k,
+ *     coupled by k x k blocks B_i (last k rows of partition i, first k columns
+ *     of partition i+1) and C_i (first k rows of partition i, last k columns of
+ *     partition i-1) (section 2.1, block-tridiagonal partition);
+ *   - factor: banded LU of every A_i, the spikes T_i = A_i^{-1}[0; B_i] and
+ *     W_i = A_i^{-1}[C_i; 0] (section 2.1, eq. 'Veqn') compressed to rank r
+ *     (the paper's n_svd, section 3.1), and the reduced system in the
+ *     compressed unknowns (section 3.2);
+ *   - solve: D-stage g = D^{-1} f, reduced solve, low-rank recovery
+ *     (section 2.1 solve summary; section 3.3 table 'solver-list'), used as
+ *     the preconditioner of an FP64 outer iteration.
+ *
+ * Every compute step runs in CUDA kernels of this library on one GPU.  No call
+ * throws or aborts: each returns an lrspike_status, and lrspike_last_error()
+ * gives a detail string.  A handle is not thread-safe; distinct handles are
+ * independent.  All work of a handle is ordered on the CUDA stream given to
+ * lrspike_create (NULL = the legacy default stream).
+ *
+ * Band storage (all entry points): diagonal-major, 2k+1 rows of length ld >= n,
+ *   band[(k + i - j) * ld + j] = A[i][j]   for |i - j| <= k,
+ * entries that fall outside the matrix are ignored.  Vectors are column-major
+ * n x nrhs with leading dimension ld >= n, FP64.
+ */
+#ifndef LRSPIKE_H
+#define LRSPIKE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrspike_ctx *lrspike_handle; /* opaque; owned by the library */
+
+typedef enum {
+    LRSPIKE_OK = 0,
+    LRSPIKE_ERR_INVALID_ARG = 1,   /* bad option, size or pointer                 */
+    LRSPIKE_ERR_STATE = 2,         /* e.g. solve before a successful factor        */
+    LRSPIKE_ERR_OOM = 3,           /* device or pinned host allocation failed      */
+    LRSPIKE_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed  */
+    LRSPIKE_ERR_SINGULAR = 5,      /* zero or non-finite pivot (row in last_error) */
+    LRSPIKE_ERR_NOT_CONVERGED = 6, /* outer iteration hit max_iter or stagnated    */
+    LRSPIKE_ERR_UNSUPPORTED = 7    /* option combination not built                 */
+} lrspike_status;
+
+/* Working precision of the preconditioner (factors, spikes, D-stage,
+ * retrieval).  The residual f - A x, the reduced system and the solution
+ * update are always FP64. */
+enum { LRSPIKE_FP64 = 0, LRSPIKE_MIXED_FP32 = 1, LRSPIKE_MIXED_TF32 = 2 };
+/* Compression of the spikes (section 3.1): SPIKE = truncated SVD of the
+ * explicit spikes T_i, W_i (the paper's choice, optimal by Eckart-Young);
+ * COUPLING = truncated SVD of B_i, C_i, then r-column solves (the cheaper
+ * alternative the paper compares against). */
+enum { LRSPIKE_COMPRESS_SPIKE = 0, LRSPIKE_COMPRESS_COUPLING = 1 };
+/* Reduced system (section 3.3, table 'solver-list'): FULL = the low-rank
+ * reduced system of LR-SPIKE-I, solved directly; TRUNCATED = its truncated
+ * block-diagonal form S~~_r of LR-SPIKE-T (eq. 'red_sys_prec_mid_2'). */
+enum { LRSPIKE_REDUCED_FULL = 0, LRSPIKE_REDUCED_TRUNCATED = 1 };
+/* Outer iteration: IR = iterative refinement x += M^{-1}(f - A x);
+ * BICGSTAB = right-preconditioned BiCGStab (the paper's outer solver);
+ * NONE = one application x = M^{-1} f (the preconditioner alone). */
+enum { LRSPIKE_OUTER_IR = 0, LRSPIKE_OUTER_BICGSTAB = 1, LRSPIKE_OUTER_NONE = 2 };
+
+typedef struct {
+    int64_t n;            /* matrix order, n >= 1                                    */
+    int32_t k;            /* half-bandwidth, 0 <= k <= 64                            */
+    int32_t p;            /* partitions, 1 <= p, every n_i > k when p > 1           */
+    int32_t r;            /* compression rank n_svd, 0 <= r <= k                     */
+    int32_t precision;    /* LRSPIKE_FP64 | LRSPIKE_MIXED_FP32 | LRSPIKE_MIXED_TF32  */
+    int32_t pivoting;     /* 0 = none; 1 = partial pivoting inside each partition   */
+    int32_t compress;     /* LRSPIKE_COMPRESS_*                                      */
+    int32_t reduced;      /* LRSPIKE_REDUCED_*                                       */
+    int32_t outer;        /* LRSPIKE_OUTER_*                                         */
+    int32_t max_iter;     /* outer iteration limit (default 50)                      */
+    double tol;           /* per-column ||f - A x||_2 / ||f||_2 target
+                             (default 1e-12 for FP64, 1e-10 for mixed)               */
+    double rank_tol;      /* singular values <= rank_tol * sigma_1 are dropped
+                             (default 1e-13 FP64, 1e-6 mixed)                        */
+    int32_t max_nrhs;     /* largest nrhs a solve may pass (default 16)              */
+    int32_t profile;      /* 1 = time every kernel with CUDA events (see below)     */
+} lrspike_options;
+
+typedef struct {
+    int32_t iterations;       /* outer iterations done (BiCGStab: full iterations)     */
+    int32_t converged;        /* 1 if every column met tol                             */
+    double max_rel_residual;  /* worst column's final ||f - A x|| / ||f||              */
+    double *rel_residual;     /* caller-owned host array of >= nrhs entries, or NULL   */
+} lrspike_info;
+
+/* Fills *opt with defaults for n, k, p, r (FP64, no pivoting, SPIKE
+ * compression, FULL reduced system, IR).  Returns INVALID_ARG on NULL. */
+lrspike_status lrspike_options_default(lrspike_options *opt, int64_t n, int32_t k, int32_t p,
+                                       int32_t r);
+
+/* Validates *opt, allocates every device workspace the handle needs (sized by
+ * n, k, p, r, precision and max_nrhs) and returns the handle in *out.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream), borrowed.
+ * Errors: INVALID_ARG (n < 1, k < 0 or k > 64, r < 0 or r > k, p < 1,
+ * n_i <= k with p > 1, max_nrhs < 1, unknown enum), UNSUPPORTED, OOM, CUDA. */
+lrspike_status lrspike_create(const lrspike_options *opt, void *cuda_stream, lrspike_handle *out);
+
+/* LR-SPIKE factorisation of the banded A.
+ * band: (2k+1) x ld values as described above, FP64.  Device pointer: borrowed,
+ * not copied -- the caller keeps it alive and unmodified until the next factor
+ * or destroy, because every solve's FP64 residual reads it.  Host pointer
+ * (pinned or pageable): copied into a device buffer owned by the handle.
+ * Errors: INVALID_ARG (NULL, ld < n), SINGULAR (a zero or non-finite pivot in
+ * some A_i; the global row is in lrspike_last_error), CUDA. */
+lrspike_status lrspike_factor(lrspike_handle h, const double *band, int64_t ld);
+
+/* Solves A x = f to the handle's tolerance with the chosen outer iteration.
+ * f, x: n x nrhs column-major FP64 with leading dimension ld >= n, both on the
+ * device or both on the host (host buffers are copied in and out); x must not
+ * alias f.  1 <= nrhs <= max_nrhs.  info may be NULL.
+ * Errors: STATE (no successful factor), INVALID_ARG, NOT_CONVERGED (x holds
+ * the last iterate), CUDA. */
+lrspike_status lrspike_solve(lrspike_handle h, const double *f, double *x, int32_t nrhs,
+                             int64_t ld, lrspike_info *info);
+
+/* Solves A^T lambda = h with the same factors: the outer iteration uses the
+ * transposed preconditioner M^{-T} = D^{-T}(I - V^T R^{-T} U^T), the
+ * transpose of M^{-1} = (I - U R^{-1} V) D^{-1}.  Arguments as lrspike_solve. */
+lrspike_status lrspike_solve_transpose(lrspike_handle hd, const double *h, double *lambda,
+                                       int32_t nrhs, int64_t ld, lrspike_info *info);
+
+/* Releases the handle and every buffer it owns.  NULL is accepted. */
+lrspike_status lrspike_destroy(lrspike_handle h);
+
+/* Detail string of the handle's last error ("" if none); owned by the handle,
+ * valid until its next call.  With h == NULL: the last error of a call that
+ * had no handle (create). */
+const char *lrspike_last_error(lrspike_handle h);
+
+/* ---- introspection (profiling and tests) ------------------------------ */
+
+/* Number of kernel launches this handle has issued since create (all
+ * kernels of the library; reset by lrspike_profile_reset). */
+int64_t lrspike_launch_count(lrspike_handle h);
+
+/* With opt.profile = 1 every kernel launch is bracketed by CUDA events on the
+ * handle's stream.  lrspike_profile_get returns, for kernel id 0..count-1,
+ * its name, its launches and the summed event time in ms (synchronises the
+ * stream).  Returns INVALID_ARG past the last id. */
+lrspike_status lrspike_profile_get(lrspike_handle h, int32_t id, const char **name,
+                                   int64_t *launches, double *total_ms);
+lrspike_status lrspike_profile_reset(lrspike_handle h);
+
+/* Copies the device arrays of the compressed reduced system to host buffers
+ * (any may be NULL): sigma (p x 2 x r singular values of T_i / W_i, zero where
+ * dropped or absent) and R (2r(p-1) squared, row-major, the matrix that is
+ * solved).  Used by the tests to compare the compression with the oracle. */
+lrspike_status lrspike_get_reduced(lrspike_handle h, double *sigma, double *R);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRSPIKE_H */

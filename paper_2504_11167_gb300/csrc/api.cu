@@ -1,0 +1,474 @@
+// Host side of the C ABI declared in lrspike.h: option checks, workspace
+// sizing, the factorisation pipeline, and the FP64 outer iteration that uses
+// the LR-SPIKE operator as its preconditioner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace lrs {
+
+const char *const kKernelNames[KID_COUNT] = {
+    "band_lu",      "prep_inverse",  "spike_rhs",   "spike_sweep", "gram",
+    "gram_reduce",  "coupling_gram", "jacobi",      "make_u",      "reduced_build",
+    "reduced_factor", "norm",        "residual",    "dstage",      "reduced_solve",
+    "retrieve",     "project_t",     "dstage_t",    "vector"};
+
+static cudaEvent_t take_event(Ctx *c) {
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+bool begin_launch(Ctx *c, int kid, cudaEvent_t *ev_end) {
+    *ev_end = nullptr;
+    if (c->profile) {
+        cudaEvent_t a = take_event(c), b = take_event(c);
+        cudaEventRecord(a, c->stream);
+        c->pending.push_back({kid, a, b});
+        *ev_end = b;
+    }
+    return true;
+}
+
+bool end_launch(Ctx *c, int kid, cudaEvent_t ev_end) {
+    const cudaError_t e = cudaGetLastError();
+    if (ev_end) cudaEventRecord(ev_end, c->stream);
+    c->launches++;
+    c->kcount[kid]++;
+    if (e != cudaSuccess) {
+        c->err = std::string("launch of ") + kKernelNames[kid] + " failed: " + cudaGetErrorString(e);
+        return false;
+    }
+    return true;
+}
+
+static void drain_profile(Ctx *c) {
+    if (c->pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto &pd : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pd.a, pd.b) == cudaSuccess) c->kms[pd.kid] += ms;
+        c->free_events.push_back(pd.a);
+        c->free_events.push_back(pd.b);
+    }
+    c->pending.clear();
+}
+
+}  // namespace lrs
+
+using namespace lrs;
+
+static thread_local std::string g_err;
+static const int64_t kNoStatus = INT64_MAX;
+static const int64_t kReducedSingular = INT64_MAX - 1;
+
+static lrspike_status fail(Ctx *c, lrspike_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_err = msg;
+    return st;
+}
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename P>
+static bool dalloc(P **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return true;
+    return cudaMalloc((void **)ptr, bytes) == cudaSuccess;
+}
+
+static void free_all(Ctx *c) {
+    void *ptrs[] = {c->off_d, c->boff_d, c->LT,   c->UT,  c->DI,   c->DS,   c->X,     c->Ucat,
+                    c->PQ,    c->Gram,   c->Gpart, c->sigma, c->E, c->F,    c->Gs,    c->Rinv,
+                    c->Gam,   c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
+                    c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (double *p : c->bv)
+        if (p) cudaFree(p);
+    if (c->host) cudaFreeHost(c->host);
+    for (auto &pd : c->pending) {
+        cudaEventDestroy(pd.a);
+        cudaEventDestroy(pd.b);
+    }
+    for (auto e : c->free_events) cudaEventDestroy(e);
+}
+
+extern "C" lrspike_status lrspike_options_default(lrspike_options *o, int64_t n, int32_t k, int32_t p,
+                                                  int32_t r) {
+    if (!o) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "options pointer is NULL");
+    std::memset(o, 0, sizeof(*o));
+    o->n = n;
+    o->k = k;
+    o->p = p;
+    o->r = r;
+    o->precision = LRSPIKE_FP64;
+    o->pivoting = 0;
+    o->compress = LRSPIKE_COMPRESS_SPIKE;
+    o->reduced = LRSPIKE_REDUCED_FULL;
+    o->outer = LRSPIKE_OUTER_IR;
+    o->max_iter = 50;
+    o->tol = 1e-12;
+    o->rank_tol = 1e-13;
+    o->max_nrhs = 16;
+    o->profile = 0;
+    return LRSPIKE_OK;
+}
+
+extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *stream, lrspike_handle *out) {
+    if (!opt || !out) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "NULL options or output pointer");
+    *out = nullptr;
+    const lrspike_options &o = *opt;
+    if (o.n < 1) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "n must be >= 1");
+    if (o.k < 0 || o.k > 64) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "k must be in 0..64");
+    if (o.p < 1 || o.p > o.n) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "p must be in 1..n");
+    if (o.r < 0 || o.r > o.k) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "r must be in 0..k");
+    if (o.max_nrhs < 1 || o.max_nrhs > 16)
+        return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "max_nrhs must be in 1..16");
+    if (o.precision < LRSPIKE_FP64 || o.precision > LRSPIKE_MIXED_TF32 || o.compress < 0 || o.compress > 1 ||
+        o.reduced < 0 || o.reduced > 1 || o.outer < 0 || o.outer > 2 || o.pivoting < 0 || o.pivoting > 1)
+        return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "unknown enum value in options");
+    if (o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rank_tol >= 0.0))
+        return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "max_iter, tol and rank_tol must be >= 0");
+    if (o.precision == LRSPIKE_MIXED_TF32)
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "TF32 tensor-core factorisation is not built yet");
+    if (o.pivoting) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "partial pivoting is not built yet");
+    if (o.outer == LRSPIKE_OUTER_BICGSTAB)
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "BiCGStab outer iteration is not built yet");
+    if (o.r > 32) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "r > 32 is not built yet");
+
+    Ctx *c = new (std::nothrow) Ctx();
+    if (!c) return fail(nullptr, LRSPIKE_ERR_OOM, "host allocation failed");
+    c->opt = o;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    c->n = o.n;
+    c->k = o.k;
+    c->p = o.p;
+    c->r = o.r;
+    c->KB = 8;
+    while (c->KB < o.k) c->KB *= 2;
+    c->fp64 = (o.precision == LRSPIKE_FP64);
+    c->tsize = c->fp64 ? 8 : 4;
+    c->profile = o.profile != 0;
+    // partitions (first n mod p get one extra row) and their blocks
+    c->off_h.resize(c->p + 1);
+    c->boff_h.resize(c->p + 1);
+    c->off_h[0] = 0;
+    c->boff_h[0] = 0;
+    const int64_t base = c->n / c->p, extra = c->n % c->p;
+    int64_t minnb = INT64_MAX;
+    for (int i = 0; i < c->p; ++i) {
+        const int64_t ni = base + (i < extra ? 1 : 0);
+        if (c->p > 1 && ni <= c->k) {
+            delete c;
+            return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "every partition needs n_i > k (use fewer partitions)");
+        }
+        c->off_h[i + 1] = c->off_h[i] + ni;
+        const int64_t nb = (ni + c->KB - 1) / c->KB;
+        c->boff_h[i + 1] = c->boff_h[i] + nb;
+        c->maxni = std::max(c->maxni, ni);
+        minnb = std::min(minnb, nb);
+    }
+    c->NB = c->boff_h[c->p];
+    const bool spikes = (c->p > 1 && c->r > 0);
+    c->m = spikes ? (o.compress == LRSPIKE_COMPRESS_COUPLING ? 2 * c->r : 2 * c->KB) : 0;
+    c->gram_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(16, minnb));
+    const size_t T = c->tsize, KB = c->KB, NB = c->NB, mx = o.max_nrhs;
+    const size_t n2 = 2 * c->r, ni = (size_t)std::max(0, c->p - 1);
+    const int64_t rb = (c->n + 255) / 256;
+    bool ok = dalloc(&c->off_d, (c->p + 1) * 8) && dalloc(&c->boff_d, (c->p + 1) * 8) &&
+              dalloc(&c->LT, NB * KB * KB * T) && dalloc(&c->UT, NB * KB * KB * T) &&
+              dalloc(&c->DI, NB * KB * T) && dalloc(&c->DS, NB * KB * T) &&
+              dalloc(&c->rv, (size_t)c->n * mx * 8) && dalloc(&c->Yv, (size_t)c->n * mx * T) &&
+              dalloc(&c->Gv, (size_t)c->n * mx * T) && dalloc(&c->nrm, 4 * mx * 8) &&
+              dalloc(&c->partial, (size_t)rb * mx * 8) && dalloc(&c->counter, 64) && dalloc(&c->status, 64);
+    if (ok && spikes) {
+        ok = dalloc(&c->X, NB * KB * c->m * T) && dalloc(&c->Ucat, (size_t)c->n * n2 * T) &&
+             dalloc(&c->PQ, (size_t)c->p * 2 * c->r * KB * T) &&
+             dalloc(&c->Gram, (size_t)c->p * 2 * KB * KB * 8) &&
+             dalloc(&c->Gpart, (size_t)c->p * c->gram_chunks * 2 * KB * KB * 8) &&
+             dalloc(&c->sigma, (size_t)c->p * 2 * c->r * 8) && dalloc(&c->E, ni * n2 * n2 * 8) &&
+             dalloc(&c->F, ni * n2 * n2 * 8) && dalloc(&c->Gs, ni * n2 * n2 * 8) &&
+             dalloc(&c->Rinv, ni * n2 * n2 * 8) && dalloc(&c->Gam, ni * n2 * n2 * 8) &&
+             dalloc(&c->psi, ni * n2 * mx * 8) && dalloc(&c->zr, ni * n2 * mx * 8) &&
+             dalloc(&c->wr, ni * n2 * mx * 8);
+    }
+    if (ok) ok = cudaMallocHost((void **)&c->host, (8 * mx + 8) * 8) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return fail(nullptr, LRSPIKE_ERR_OOM, "device or pinned allocation failed");
+    }
+    cudaMemcpy(c->off_d, c->off_h.data(), (c->p + 1) * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->boff_d, c->boff_h.data(), (c->p + 1) * 8, cudaMemcpyHostToDevice);
+    cudaMemset(c->counter, 0, 64);
+    if (c->Gam) cudaMemset(c->Gam, 0, ni * n2 * n2 * 8);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return fail(nullptr, LRSPIKE_ERR_CUDA, std::string("CUDA error at create: ") + cudaGetErrorString(e));
+    }
+    *out = reinterpret_cast<lrspike_handle>(c);
+    return LRSPIKE_OK;
+}
+
+static Ctx *ctx(lrspike_handle h) { return reinterpret_cast<Ctx *>(h); }
+
+static lrspike_status cuda_fail(Ctx *c, const char *what) {
+    const cudaError_t e = cudaGetLastError();
+    return fail(c, LRSPIKE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, int64_t ld) {
+    Ctx *c = ctx(h);
+    if (!c) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "NULL handle");
+    c->err.clear();
+    if (!band || ld < c->n) return fail(c, LRSPIKE_ERR_INVALID_ARG, "band is NULL or ld < n");
+    cudaSetDevice(c->device);
+    c->factored = false;
+    if (is_device_ptr(band)) {
+        c->band = band;
+    } else {
+        const size_t bytes = (size_t)(2 * c->k + 1) * ld * 8;
+        if (c->band_own_bytes < bytes) {
+            if (c->band_own) cudaFree(c->band_own);
+            c->band_own = nullptr;
+            c->band_own_bytes = 0;
+            if (!dalloc(&c->band_own, bytes)) return fail(c, LRSPIKE_ERR_OOM, "band copy allocation failed");
+            c->band_own_bytes = bytes;
+        }
+        if (cudaMemcpyAsync(c->band_own, band, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return cuda_fail(c, "band host-to-device copy");
+        c->band = c->band_own;
+    }
+    c->ld = ld;
+    *(int64_t *)c->host = kNoStatus;
+    if (cudaMemcpyAsync(c->status, c->host, 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return cuda_fail(c, "status reset");
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "stream sync");
+    bool ok = run_band_lu(c) && run_prep(c);
+    if (ok && c->p > 1 && c->r > 0) {
+        if (c->opt.compress == LRSPIKE_COMPRESS_COUPLING)
+            ok = run_coupling_gram(c) && run_jacobi(c) && run_spike_rhs(c) && run_sweep(c) && run_make_u(c);
+        else
+            ok = run_spike_rhs(c) && run_sweep(c) && run_gram(c) && run_jacobi(c) && run_make_u(c);
+        ok = ok && run_reduced_build(c) && run_reduced_factor(c);
+    }
+    if (!ok) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+    if (cudaMemcpyAsync(c->host, c->status, 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_fail(c, "factorisation");
+    const int64_t st = *(int64_t *)c->host;
+    if (st == kReducedSingular) return fail(c, LRSPIKE_ERR_SINGULAR, "singular reduced system block");
+    if (st != kNoStatus) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "zero or non-finite pivot at global row %lld", (long long)st);
+        return fail(c, LRSPIKE_ERR_SINGULAR, buf);
+    }
+    c->factored = true;
+    return LRSPIKE_OK;
+}
+
+static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs, int64_t ld,
+                                   lrspike_info *info, bool trans) {
+    if (!c) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "NULL handle");
+    c->err.clear();
+    if (!c->factored) return fail(c, LRSPIKE_ERR_STATE, "solve called without a successful factor");
+    if (!f || !x || nrhs < 1 || nrhs > c->opt.max_nrhs || ld < c->n)
+        return fail(c, LRSPIKE_ERR_INVALID_ARG, "bad f/x pointer, nrhs or ld");
+    const size_t span = (size_t)((nrhs - 1) * ld + c->n) * 8;
+    if ((const char *)x < (const char *)f + span && (const char *)f < (const char *)x + span)
+        return fail(c, LRSPIKE_ERR_INVALID_ARG, "x must not alias f");
+    cudaSetDevice(c->device);
+    const bool fdev = is_device_ptr(f), xdev = is_device_ptr(x);
+    if (fdev != xdev) return fail(c, LRSPIKE_ERR_INVALID_ARG, "f and x must both be device or both host");
+    const double *fd = f;
+    double *xd = x;
+    int64_t ldd = ld;
+    if (!fdev) {
+        const size_t bytes = (size_t)c->n * nrhs * 8;
+        if (c->io_bytes < bytes) {
+            if (c->io_f) cudaFree(c->io_f);
+            if (c->io_x) cudaFree(c->io_x);
+            c->io_f = c->io_x = nullptr;
+            c->io_bytes = 0;
+            if (!dalloc(&c->io_f, bytes) || !dalloc(&c->io_x, bytes))
+                return fail(c, LRSPIKE_ERR_OOM, "solve staging allocation failed");
+            c->io_bytes = bytes;
+        }
+        if (cudaMemcpy2DAsync(c->io_f, c->n * 8, f, ld * 8, c->n * 8, nrhs, cudaMemcpyHostToDevice,
+                              c->stream) != cudaSuccess)
+            return cuda_fail(c, "f host-to-device copy");
+        fd = c->io_f;
+        xd = c->io_x;
+        ldd = c->n;
+    }
+    const int mx = c->opt.max_nrhs;
+    if (cudaMemset2DAsync(xd, ldd * 8, 0, c->n * 8, nrhs, c->stream) != cudaSuccess)
+        return cuda_fail(c, "x reset");
+    if (!run_norms(c, fd, ldd, nrhs, c->nrm)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+    double *hf = c->host, *hr = c->host + mx;
+    if (cudaMemcpyAsync(hf, c->nrm, nrhs * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return cuda_fail(c, "norm read");
+    const int outer = c->opt.outer;
+    const int max_it = (outer == LRSPIKE_OUTER_NONE) ? 1 : c->opt.max_iter;
+    std::vector<double> hist;
+    int it = 0;
+    bool converged = false, stalled = false;
+    std::vector<double> rel(nrhs, 0.0);
+    for (it = 0;; ++it) {
+        if (!run_residual(c, fd, xd, ldd, nrhs, trans, it == 0)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        if (outer == LRSPIKE_OUTER_NONE) {
+            if (!apply_precond(c, xd, ldd, nrhs, trans)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+            it = 1;
+            break;
+        }
+        if (cudaMemcpyAsync(hr, c->nrm + mx, nrhs * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return cuda_fail(c, "outer iteration");
+        double worst = 0.0;
+        bool nan = false;
+        for (int q = 0; q < nrhs; ++q) {
+            rel[q] = (hf[q] > 0.0) ? hr[q] / hf[q] : 0.0;
+            if (!(rel[q] == rel[q])) nan = true;
+            worst = std::max(worst, rel[q]);
+        }
+        hist.push_back(worst);
+        if (nan) { stalled = true; break; }
+        if (worst <= c->opt.tol) { converged = true; break; }
+        if (it >= max_it) break;
+        if (it >= 3 && worst > 0.9 * hist[it - 3]) { stalled = true; break; }
+        if (!apply_precond(c, xd, ldd, nrhs, trans)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+    }
+    if (!fdev) {
+        if (cudaMemcpy2DAsync(x, ld * 8, xd, ldd * 8, c->n * 8, nrhs, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess)
+            return cuda_fail(c, "x device-to-host copy");
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "solve");
+    if (outer == LRSPIKE_OUTER_NONE) converged = true;
+    if (info) {
+        info->iterations = it;
+        info->converged = converged ? 1 : 0;
+        info->max_rel_residual = hist.empty() ? NAN : hist.back();
+        if (info->rel_residual)
+            for (int q = 0; q < nrhs; ++q) info->rel_residual[q] = hist.empty() ? NAN : rel[q];
+    }
+    if (!converged) {
+        char buf[200];
+        std::snprintf(buf, sizeof buf, "%s after %d iterations, worst relative residual %.3e",
+                      stalled ? "outer iteration stagnated" : "max_iter reached", it,
+                      hist.empty() ? NAN : hist.back());
+        return fail(c, LRSPIKE_ERR_NOT_CONVERGED, buf);
+    }
+    return LRSPIKE_OK;
+}
+
+extern "C" lrspike_status lrspike_solve(lrspike_handle h, const double *f, double *x, int32_t nrhs, int64_t ld,
+                                        lrspike_info *info) {
+    return solve_common(ctx(h), f, x, nrhs, ld, info, false);
+}
+
+extern "C" lrspike_status lrspike_solve_transpose(lrspike_handle h, const double *hv, double *lam, int32_t nrhs,
+                                                  int64_t ld, lrspike_info *info) {
+    return solve_common(ctx(h), hv, lam, nrhs, ld, info, true);
+}
+
+extern "C" lrspike_status lrspike_destroy(lrspike_handle h) {
+    Ctx *c = ctx(h);
+    if (!c) return LRSPIKE_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return LRSPIKE_OK;
+}
+
+extern "C" const char *lrspike_last_error(lrspike_handle h) {
+    Ctx *c = ctx(h);
+    return c ? c->err.c_str() : g_err.c_str();
+}
+
+extern "C" int64_t lrspike_launch_count(lrspike_handle h) {
+    Ctx *c = ctx(h);
+    return c ? c->launches : 0;
+}
+
+extern "C" lrspike_status lrspike_profile_get(lrspike_handle h, int32_t id, const char **name, int64_t *launches,
+                                              double *total_ms) {
+    Ctx *c = ctx(h);
+    if (!c || id < 0 || id >= KID_COUNT) return fail(c, LRSPIKE_ERR_INVALID_ARG, "bad handle or kernel id");
+    drain_profile(c);
+    if (name) *name = kKernelNames[id];
+    if (launches) *launches = c->kcount[id];
+    if (total_ms) *total_ms = c->kms[id];
+    return LRSPIKE_OK;
+}
+
+extern "C" lrspike_status lrspike_profile_reset(lrspike_handle h) {
+    Ctx *c = ctx(h);
+    if (!c) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "NULL handle");
+    drain_profile(c);
+    for (int i = 0; i < KID_COUNT; ++i) {
+        c->kcount[i] = 0;
+        c->kms[i] = 0.0;
+    }
+    c->launches = 0;
+    return LRSPIKE_OK;
+}
+
+extern "C" lrspike_status lrspike_get_reduced(lrspike_handle h, double *sigma, double *R) {
+    Ctx *c = ctx(h);
+    if (!c) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "NULL handle");
+    if (!c->factored) return fail(c, LRSPIKE_ERR_STATE, "no successful factor");
+    cudaSetDevice(c->device);
+    const int r = c->r, n2 = 2 * r, ni = c->p - 1;
+    const bool spikes = (c->p > 1 && r > 0);
+    if (sigma) {
+        const size_t cnt = (size_t)c->p * 2 * r;
+        if (spikes) {
+            if (cudaMemcpy(sigma, c->sigma, cnt * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return cuda_fail(c, "sigma copy");
+        } else {
+            std::fill(sigma, sigma + cnt, 0.0);
+        }
+    }
+    if (R && spikes) {
+        const size_t nz = (size_t)n2 * ni, nn = (size_t)n2 * n2;
+        std::vector<double> E(ni * nn), F(ni * nn), G(ni * nn);
+        if (cudaMemcpy(E.data(), c->E, ni * nn * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(F.data(), c->F, ni * nn * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(G.data(), c->Gs, ni * nn * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return cuda_fail(c, "reduced copy");
+        std::fill(R, R + nz * nz, 0.0);
+        const bool full = (c->opt.reduced == LRSPIKE_REDUCED_FULL);
+        for (int i = 0; i < ni; ++i)
+            for (int a = 0; a < n2; ++a)
+                for (int b = 0; b < n2; ++b) {
+                    const size_t row = (size_t)i * n2 + a;
+                    R[row * nz + (size_t)i * n2 + b] = E[i * nn + a * n2 + b];
+                    if (full && i + 1 < ni) R[row * nz + (size_t)(i + 1) * n2 + b] = F[i * nn + a * n2 + b];
+                    if (full && i >= 1) R[row * nz + (size_t)(i - 1) * n2 + b] = G[i * nn + a * n2 + b];
+                }
+    }
+    return LRSPIKE_OK;
+}

@@ -1,0 +1,431 @@
+// Spikes and their rank-r compression (paper section 2.1, eq. 'Veqn';
+// section 3.1).
+//
+//   k_spike_rhs   right-hand sides [0; B_i] and [C_i; 0] (SPIKE mode) or
+//                 [0; B_i V_B] and [C_i V_C; 0] (COUPLING mode) in the spike
+//                 buffer X, one KB x m panel per block
+//   k_sweep       X <- A_i^{-1} X per partition: forward then backward chain
+//                 over the packed factor tiles (m = 2KB or 2r columns)
+//   k_gram        partial Gram matrices T_i^T T_i and W_i^T W_i per chunk
+//   k_gram_reduce fixed-order sum of the chunk partials (deterministic)
+//   k_coupling_gram  B_i^T B_i and C_i^T C_i straight from the band
+//   k_jacobi      cyclic two-sided Jacobi eigensolver (round-robin ordering,
+//                 KB/2 disjoint rotations at a time) of each Gram matrix; the
+//                 r leading eigenvectors V_r give the truncated SVD subspace
+//   k_make_u      u-factors of the low-rank spikes
+//
+// Compression identity used here: for a spike X with SVD U S V^T, the best
+// rank-r approximation is X V_r V_r^T, so the low-rank spike is stored as
+// u = X V_r (n_i x r, columns orthogonal with norms sigma_j) and P = V_r^T
+// (r x k).  V_r comes from the eigenvectors of X^T X.  COUPLING mode
+// (section 3.1's alternative) truncates B_i = U_B S_B V_B^T instead:
+// T~_i = A_i^{-1}[0; B_i V_B,r] V_B,r^T, so u is the solve of r columns.
+// The rank guard drops sigma_j <= rank_tol * sigma_1 (the paper lowers n_svd
+// when singular values approach zero, section 4.2).
+#include "common.cuh"
+#include "internal.h"
+#include "tile_ops.cuh"
+
+namespace lrs {
+
+// ---------------------------------------------------------------------------
+template <typename T, int KB>
+__global__ void k_spike_rhs(const double *__restrict__ band, int64_t ld, int k, Parts P, int r,
+                            int coupling, const T *__restrict__ PQ, T *__restrict__ X, int m) {
+    const int part = blockIdx.x;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int64_t b0 = P.boff[part];
+    // local row rho -> X[(b0 + rho / KB) * KB * m + (rho % KB) * m + col]
+    auto xat = [&](int64_t rho, int col) -> T & {
+        return X[(b0 + rho / KB) * (int64_t)KB * m + (rho % KB) * m + col];
+    };
+    if (part < P.p - 1) {  // right spike: rows ni-k..ni-1 hold B_i
+        const int64_t sn = s + ni;
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+            const int a = e / k, b = e % k;
+            if (!coupling) {
+                // B_i[a][b] = A[sn-k+a][sn+b], nonzero for b <= a
+                xat(ni - k + a, b) = (b <= a) ? (T)band[(int64_t)(a - b) * ld + sn + b] : T(0);
+            }
+        }
+        if (coupling) {
+            for (int e = threadIdx.x; e < k * r; e += blockDim.x) {
+                const int a = e / r, c = e % r;
+                double acc = 0.0;
+                for (int b = 0; b <= a; ++b)
+                    acc += band[(int64_t)(a - b) * ld + sn + b] *
+                           (double)PQ[(((int64_t)part * 2 + 0) * r + c) * KB + b];
+                xat(ni - k + a, c) = (T)acc;
+            }
+        }
+    }
+    if (part > 0) {  // left spike: rows 0..k-1 hold C_i
+        const int wc = coupling ? r : KB;  // first column of the W panel
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+            const int a = e / k, b = e % k;
+            if (!coupling) {
+                // C_i[a][b] = A[s+a][s-k+b], nonzero for a <= b
+                xat(a, wc + b) =
+                    (a <= b) ? (T)band[(int64_t)(2 * k + a - b) * ld + s - k + b] : T(0);
+            }
+        }
+        if (coupling) {
+            for (int e = threadIdx.x; e < k * r; e += blockDim.x) {
+                const int a = e / r, c = e % r;
+                double acc = 0.0;
+                for (int b = a; b < k; ++b)
+                    acc += band[(int64_t)(2 * k + a - b) * ld + s - k + b] *
+                           (double)PQ[(((int64_t)part * 2 + 1) * r + c) * KB + b];
+                xat(a, wc + c) = (T)acc;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int KB>
+__global__ void __launch_bounds__(Geo<KB>::NT)
+    k_sweep(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI, Parts P,
+            T *__restrict__ X, int m) {
+    constexpr int NT = Geo<KB>::NT, LDS = KB + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ls = reinterpret_cast<T *>(smem_raw);  // KB x LDS
+    T *dsm = Ls + KB * LDS;                   // KB
+    T *Tt = dsm + KB;                         // KB x m
+    T *Yp = Tt + KB * m;                      // KB x m
+    const int part = blockIdx.x;
+    const int64_t b0 = P.boff[part];
+    const int nb = (int)(P.boff[part + 1] - b0);
+    const int pm = KB * m;
+    for (int J = 0; J < nb; ++J) {
+        const int64_t g = b0 + J;
+        load_tile<T, KB>(LT + g * KB * KB, Ls, LDS);
+        for (int e = threadIdx.x; e < pm; e += NT) Tt[e] = X[g * pm + e];
+        __syncthreads();
+        fwd_step<T, KB, Split::COLS>(Ls, LDS, Tt, Yp, m, m, J == 0);
+        for (int e = threadIdx.x; e < pm; e += NT) X[g * pm + e] = Yp[e];
+    }
+    __syncthreads();
+    for (int J = nb - 1; J >= 0; --J) {
+        const int64_t g = b0 + J;
+        load_tile<T, KB>(UT + g * KB * KB, Ls, LDS);
+        if (threadIdx.x < KB) dsm[threadIdx.x] = DI[g * KB + threadIdx.x];
+        for (int e = threadIdx.x; e < pm; e += NT) Tt[e] = X[g * pm + e];
+        __syncthreads();
+        bwd_step<T, KB, Split::COLS>(Ls, LDS, dsm, Tt, Yp, m, m, J == nb - 1);
+        for (int e = threadIdx.x; e < pm; e += NT) X[g * pm + e] = Yp[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrices of the two spike panels, partial sums over a chunk of blocks.
+template <typename T, int KB>
+__global__ void __launch_bounds__(Geo<KB>::NT)
+    k_gram(const T *__restrict__ X, Parts P, int chunks, double *__restrict__ Gpart) {
+    constexpr int NT = Geo<KB>::NT, M = 2 * KB, PER = (2 * KB * KB) / NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);  // KB x M
+    const int part = blockIdx.y, ch = blockIdx.x;
+    const int64_t b0 = P.boff[part];
+    const int nb = (int)(P.boff[part + 1] - b0);
+    const int J0 = (int)((int64_t)ch * nb / chunks), J1 = (int)((int64_t)(ch + 1) * nb / chunks);
+    T acc[PER];
+#pragma unroll
+    for (int t = 0; t < PER; ++t) acc[t] = T(0);
+    for (int J = J0; J < J1; ++J) {
+        const T *src = X + (b0 + J) * (int64_t)KB * M;
+        for (int e = threadIdx.x; e < KB * M; e += NT) Xs[e] = src[e];
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int e = threadIdx.x + NT * t;
+            const int gsel = e / (KB * KB), rem = e % (KB * KB);
+            const int a = rem / KB, b = rem % KB;
+            T sacc = T(0);
+            for (int q = 0; q < KB; ++q) sacc += Xs[q * M + gsel * KB + a] * Xs[q * M + gsel * KB + b];
+            acc[t] += sacc;
+        }
+        __syncthreads();
+    }
+    double *dst = Gpart + ((int64_t)part * chunks + ch) * 2 * KB * KB;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) dst[threadIdx.x + NT * t] = (double)acc[t];
+}
+
+__global__ void k_gram_reduce(const double *__restrict__ Gpart, int chunks, int64_t per_part,
+                              int64_t total, double *__restrict__ G) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t part = e / per_part, rem = e % per_part;
+    double s = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) s += Gpart[(part * chunks + ch) * per_part + rem];
+    G[e] = s;
+}
+
+// B_i^T B_i and C_i^T C_i (KB x KB, zero-padded beyond k), FP64.
+template <int KB>
+__global__ void k_coupling_gram(const double *__restrict__ band, int64_t ld, int k, Parts P,
+                                double *__restrict__ G) {
+    const int part = blockIdx.x;
+    const int64_t s = P.off[part], sn = P.off[part + 1];
+    for (int e = threadIdx.x; e < 2 * KB * KB; e += blockDim.x) {
+        const int gsel = e / (KB * KB), b = (e / KB) % KB, c = e % KB;
+        double acc = 0.0;
+        if (b < k && c < k) {
+            if (gsel == 0 && part < P.p - 1) {
+                for (int a = 0; a < k; ++a) {  // B[a][b] = band[(a-b)*ld + sn+b], b <= a
+                    const double vb = (b <= a) ? band[(int64_t)(a - b) * ld + sn + b] : 0.0;
+                    const double vc = (c <= a) ? band[(int64_t)(a - c) * ld + sn + c] : 0.0;
+                    acc += vb * vc;
+                }
+            } else if (gsel == 1 && part > 0) {
+                for (int a = 0; a < k; ++a) {  // C[a][b] = band[(2k+a-b)*ld + s-k+b], a <= b
+                    const double vb = (a <= b) ? band[(int64_t)(2 * k + a - b) * ld + s - k + b] : 0.0;
+                    const double vc = (a <= c) ? band[(int64_t)(2 * k + a - c) * ld + s - k + c] : 0.0;
+                    acc += vb * vc;
+                }
+            }
+        }
+        G[(int64_t)part * 2 * KB * KB + e] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi eigen-decomposition of one KB x KB symmetric PSD Gram matrix.
+template <typename T> struct Eps;
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+template <> struct Eps<float> { static constexpr float v = 1.1920929e-07f; };
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(Geo<KB>::NT)
+    k_jacobi(const double *__restrict__ Gram, int r, double rank_tol, int max_sweeps,
+             T *__restrict__ PQ, double *__restrict__ sigma) {
+    constexpr int NT = Geo<KB>::NT, LD = KB + 1, NP = KB / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *A = reinterpret_cast<T *>(smem_raw), *V = A + KB * LD;
+    __shared__ T cs[NP], sn[NP];
+    __shared__ int pp[NP], qq[NP];
+    __shared__ int rotated;
+    __shared__ int order[KB];
+    __shared__ T lam[KB];
+    const int id = blockIdx.x;  // part * 2 + g
+    const double *G = Gram + (int64_t)id * KB * KB;
+    for (int e = threadIdx.x; e < KB * KB; e += NT) {
+        const int a = e / KB, b = e % KB;
+        A[a * LD + b] = (T)G[e];
+        V[a * LD + b] = (a == b) ? T(1) : T(0);
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        __syncthreads();
+        for (int round = 0; round < KB - 1; ++round) {
+            if (threadIdx.x < NP) {
+                const int i = threadIdx.x;
+                // circle method: position 0 fixed, positions 1..KB-1 rotate
+                auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (KB - 1); };
+                int p = player(i), q = player(KB - 1 - i);
+                if (p > q) { const int t = p; p = q; q = t; }
+                const T app = A[p * LD + p], aqq = A[q * LD + q], apq = A[p * LD + q];
+                T c = T(1), s = T(0);
+                if (apq != T(0) && fabs((double)apq) > (double)Eps<T>::v * sqrt(fabs((double)app * (double)aqq))) {
+                    const T tau = (aqq - app) / (T(2) * apq);
+                    const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                    c = T(1) / sqrt(T(1) + t * t);
+                    s = t * c;
+                    rotated = 1;
+                }
+                pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < NP * KB; it += NT) {  // rows p, q
+                const int i = it / KB, j = it % KB;
+                const int p = pp[i], q = qq[i];
+                const T c = cs[i], s = sn[i];
+                const T ap = A[p * LD + j], aq = A[q * LD + j];
+                A[p * LD + j] = c * ap - s * aq;
+                A[q * LD + j] = s * ap + c * aq;
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < NP * KB; it += NT) {  // columns p, q and V
+                const int i = it / KB, j = it % KB;
+                const int p = pp[i], q = qq[i];
+                const T c = cs[i], s = sn[i];
+                const T ap = A[j * LD + p], aq = A[j * LD + q];
+                A[j * LD + p] = c * ap - s * aq;
+                A[j * LD + q] = s * ap + c * aq;
+                const T vp = V[j * LD + p], vq = V[j * LD + q];
+                V[j * LD + p] = c * vp - s * vq;
+                V[j * LD + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+        if (!rotated) break;
+        __syncthreads();
+    }
+    // eigenvalues, ranked by decreasing value (ties: lower index first)
+    if (threadIdx.x < KB) lam[threadIdx.x] = A[threadIdx.x * LD + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < KB) {
+        const int j = threadIdx.x;
+        int rk = 0;
+        for (int i = 0; i < KB; ++i) rk += (lam[i] > lam[j]) || (lam[i] == lam[j] && i < j);
+        order[rk] = j;
+    }
+    __syncthreads();
+    const double s1 = sqrt(fmax((double)lam[order[0]], 0.0));
+    T *out = PQ + (int64_t)id * r * KB;
+    for (int c = threadIdx.x / 4; c < r; c += NT / 4) {
+        // all four lanes of the group write part of row c; sign fixed so that
+        // the largest-magnitude entry of each kept vector is positive
+        const int j = order[c];
+        const double sg = sqrt(fmax((double)lam[j], 0.0));
+        const bool keep = (s1 > 0.0) && (sg > rank_tol * s1);
+        int imax = 0;
+        for (int q = 1; q < KB; ++q)
+            if (fabs((double)V[q * LD + j]) > fabs((double)V[imax * LD + j])) imax = q;
+        const T sgn = (V[imax * LD + j] < T(0)) ? T(-1) : T(1);
+        for (int q = threadIdx.x % 4; q < KB; q += 4) out[c * KB + q] = keep ? sgn * V[q * LD + j] : T(0);
+        if (threadIdx.x % 4 == 0) sigma[(int64_t)id * r + c] = keep ? sg : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// u-factors: SPIKE mode u = X V_r (X panel columns times P^T); COUPLING mode
+// the solved columns are u already.  Ucat row = [u_T (r) | u_W (r)].
+template <typename T, int KB>
+__global__ void __launch_bounds__(Geo<KB>::NT)
+    k_make_u(const T *__restrict__ X, int m, const T *__restrict__ PQ, Parts P, int r, int coupling,
+             T *__restrict__ Ucat) {
+    constexpr int NT = Geo<KB>::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);  // KB x m
+    T *Ps = Xs + KB * m;                      // 2 x r x KB
+    const int64_t g = blockIdx.x;
+    const int part = part_of_block(P, g);
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int J = (int)(g - P.boff[part]);
+    for (int e = threadIdx.x; e < KB * m; e += NT) Xs[e] = X[g * KB * m + e];
+    if (!coupling)
+        for (int e = threadIdx.x; e < 2 * r * KB; e += NT) Ps[e] = PQ[(int64_t)part * 2 * r * KB + e];
+    __syncthreads();
+    const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
+    const int64_t row = (int64_t)J * KB + a;
+    if (row >= ni) return;
+    T *dst = Ucat + (s + row) * 2 * r;
+    for (int c = q; c < 2 * r; c += 4) {
+        const int gsel = c / r, cc = c % r;
+        T acc;
+        if (coupling) {
+            acc = Xs[a * m + c];
+        } else {
+            acc = T(0);
+            for (int j = 0; j < KB; ++j) acc += Xs[a * m + gsel * KB + j] * Ps[(gsel * r + cc) * KB + j];
+        }
+        dst[c] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int KB>
+static bool spike_rhs_impl(Ctx *c) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    if (cudaMemsetAsync(c->X, 0, (size_t)c->NB * KB * c->m * sizeof(T), c->stream) != cudaSuccess) {
+        c->err = "cudaMemsetAsync failed";
+        return false;
+    }
+    return launch(c, KID_SPIKE_RHS, [&] {
+        k_spike_rhs<T, KB><<<c->p, 256, 0, c->stream>>>(c->band, c->ld, c->k, P, c->r,
+                                                        c->opt.compress == LRSPIKE_COMPRESS_COUPLING,
+                                                        (const T *)c->PQ, (T *)c->X, c->m);
+    });
+}
+
+template <typename T, int KB>
+static bool sweep_impl(Ctx *c) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    const size_t smem = (KB * (KB + 1) + KB + 2 * KB * c->m) * sizeof(T);
+    auto kern = k_sweep<T, KB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch(c, KID_SWEEP, [&] {
+        kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT,
+                                                     (const T *)c->DI, P, (T *)c->X, c->m);
+    });
+}
+
+template <typename T, int KB>
+static bool gram_impl(Ctx *c) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    dim3 grid(c->gram_chunks, c->p);
+    const size_t smem = (size_t)KB * 2 * KB * sizeof(T);
+    auto kern = k_gram<T, KB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!launch(c, KID_GRAM, [&] {
+            kern<<<grid, Geo<KB>::NT, smem, c->stream>>>((const T *)c->X, P, c->gram_chunks, c->Gpart);
+        }))
+        return false;
+    const int64_t per = 2LL * KB * KB, total = per * c->p;
+    return launch(c, KID_GRAM_REDUCE, [&] {
+        k_gram_reduce<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(c->Gpart, c->gram_chunks,
+                                                                           per, total, c->Gram);
+    });
+}
+
+template <typename T, int KB>
+static bool coupling_gram_impl(Ctx *c) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    return launch(c, KID_COUPLING_GRAM, [&] {
+        k_coupling_gram<KB><<<c->p, 256, 0, c->stream>>>(c->band, c->ld, c->k, P, c->Gram);
+    });
+}
+
+template <typename T, int KB>
+static bool jacobi_impl(Ctx *c) {
+    const size_t smem = 2 * KB * (KB + 1) * sizeof(T);
+    auto kern = k_jacobi<T, KB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch(c, KID_JACOBI, [&] {
+        kern<<<2 * c->p, Geo<KB>::NT, smem, c->stream>>>(c->Gram, c->r, c->opt.rank_tol, 40, (T *)c->PQ,
+                                                         c->sigma);
+    });
+}
+
+template <typename T, int KB>
+static bool make_u_impl(Ctx *c) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    const size_t smem = (KB * c->m + 2 * c->r * KB) * sizeof(T);
+    auto kern = k_make_u<T, KB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch(c, KID_MAKE_U, [&] {
+        kern<<<(unsigned)c->NB, Geo<KB>::NT, smem, c->stream>>>(
+            (const T *)c->X, c->m, (const T *)c->PQ, P, c->r,
+            c->opt.compress == LRSPIKE_COMPRESS_COUPLING, (T *)c->Ucat);
+    });
+}
+
+#define LRS_KB_DISPATCH(FN)                                \
+    template <typename T>                                  \
+    static bool FN##_kb(Ctx *c) {                          \
+        switch (c->KB) {                                   \
+            case 8: return FN<T, 8>(c);                    \
+            case 16: return FN<T, 16>(c);                  \
+            case 32: return FN<T, 32>(c);                  \
+            default: return FN<T, 64>(c);                  \
+        }                                                  \
+    }
+
+LRS_KB_DISPATCH(spike_rhs_impl)
+LRS_KB_DISPATCH(sweep_impl)
+LRS_KB_DISPATCH(gram_impl)
+LRS_KB_DISPATCH(coupling_gram_impl)
+LRS_KB_DISPATCH(jacobi_impl)
+LRS_KB_DISPATCH(make_u_impl)
+
+bool run_spike_rhs(Ctx *c) { return c->fp64 ? spike_rhs_impl_kb<double>(c) : spike_rhs_impl_kb<float>(c); }
+bool run_sweep(Ctx *c) { return c->fp64 ? sweep_impl_kb<double>(c) : sweep_impl_kb<float>(c); }
+bool run_gram(Ctx *c) { return c->fp64 ? gram_impl_kb<double>(c) : gram_impl_kb<float>(c); }
+bool run_coupling_gram(Ctx *c) { return coupling_gram_impl_kb<double>(c); }
+bool run_jacobi(Ctx *c) { return c->fp64 ? jacobi_impl_kb<double>(c) : jacobi_impl_kb<float>(c); }
+bool run_make_u(Ctx *c) { return c->fp64 ? make_u_impl_kb<double>(c) : make_u_impl_kb<float>(c); }
+
+}  // namespace lrs

@@ -1,0 +1,145 @@
+// Internal state and launcher declarations of the LR-SPIKE CUDA library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lrspike.h"
+
+namespace lrs {
+
+enum KernelId {
+    KID_LU = 0,
+    KID_PREP,
+    KID_SPIKE_RHS,
+    KID_SWEEP,
+    KID_GRAM,
+    KID_GRAM_REDUCE,
+    KID_COUPLING_GRAM,
+    KID_JACOBI,
+    KID_MAKE_U,
+    KID_RED_BUILD,
+    KID_RED_FACTOR,
+    KID_NORM,
+    KID_RESIDUAL,
+    KID_DSTAGE,
+    KID_RED_SOLVE,
+    KID_RETRIEVE,
+    KID_PROJECT_T,
+    KID_DSTAGE_T,
+    KID_VEC,
+    KID_COUNT
+};
+
+extern const char *const kKernelNames[KID_COUNT];
+
+struct Pending {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+// One handle.  Device arrays typed void* hold the working precision T
+// (double in FP64 mode, float in the mixed modes).
+struct Ctx {
+    lrspike_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int KB = 8;          // block size (>= k, power of two in 8..64)
+    bool fp64 = true;    // working precision is double
+    size_t tsize = 8;    // sizeof(T)
+    int64_t n = 0, NB = 0, maxni = 0;
+    int k = 0, p = 1, r = 0;
+    int m = 0;           // spike columns: 2*KB (SPIKE) or 2*r (COUPLING)
+    std::vector<int64_t> off_h, boff_h;
+    int64_t *off_d = nullptr, *boff_d = nullptr;
+
+    // factors: LT/UT tiles [NB][KB][KB], DI and DS [NB][KB]
+    void *LT = nullptr, *UT = nullptr, *DI = nullptr, *DS = nullptr;
+    void *X = nullptr;        // spike columns [NB][KB][m]
+    void *Ucat = nullptr;     // low-rank columns [n][2r]: u_T then u_W
+    void *PQ = nullptr;       // projections [p][2][r][KB]: P_i (T~_i), Q_i (W~_i)
+    double *Gram = nullptr;   // [p][2][KB][KB]
+    double *Gpart = nullptr;  // [p][chunks][2][KB][KB]
+    int gram_chunks = 1;
+    double *sigma = nullptr;  // [p][2][r]
+    // reduced system, interfaces i = 0..p-2, blocks of 2r x 2r (row-major)
+    double *E = nullptr, *F = nullptr, *Gs = nullptr;   // diagonal, super, sub blocks
+    double *Rinv = nullptr;   // TRUNCATED: E_i^{-1}; FULL: Delta_i^{-1}
+    double *Gam = nullptr;    // FULL: Gamma_i = G_i Delta_{i-1}^{-1}
+
+    // solve scratch (max_nrhs columns)
+    double *rv = nullptr;     // FP64 residual / work vector, n x max_nrhs
+    void *Yv = nullptr;       // T, n x max_nrhs: forward-sweep results
+    void *Gv = nullptr;       // T, n x max_nrhs: D-stage result g
+    double *psi = nullptr;    // [p-1][2r][max_nrhs]
+    double *zr = nullptr;     // [p-1][2r][max_nrhs]
+    double *wr = nullptr;     // FULL solve work, same size
+    double *nrm = nullptr;    // [4][max_nrhs]: |f|, |r|, 1/|r|, spare
+    double *partial = nullptr;
+    int64_t npartial = 0;
+    unsigned int *counter = nullptr;
+    int64_t *status = nullptr; // first singular global row (INT64_MAX = none)
+    double *host = nullptr;    // pinned host scratch
+    // BiCGStab vectors (FP64, n x max_nrhs each) and scalars
+    double *bv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double *dots = nullptr;
+
+    const double *band = nullptr;
+    int64_t ld = 0;
+    double *band_own = nullptr;
+    size_t band_own_bytes = 0;
+    double *io_f = nullptr, *io_x = nullptr;  // device copies for host-pointer solves
+    size_t io_bytes = 0;
+    bool factored = false;
+
+    std::string err;
+    int64_t launches = 0;
+    bool profile = false;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    int64_t kcount[KID_COUNT] = {};
+    double kms[KID_COUNT] = {};
+};
+
+// Records a kernel launch: counts it and, when profiling, brackets it with
+// events on the handle's stream.  Returns false (with c->err set) when the
+// launch failed.
+bool begin_launch(Ctx *c, int kid, cudaEvent_t *ev_end);
+bool end_launch(Ctx *c, int kid, cudaEvent_t ev_end);
+
+template <typename F>
+inline bool launch(Ctx *c, int kid, F &&f) {
+    cudaEvent_t e = nullptr;
+    if (!begin_launch(c, kid, &e)) return false;
+    f();
+    return end_launch(c, kid, e);
+}
+
+// ---- launchers (each dispatches on the working precision and KB) --------
+bool run_band_lu(Ctx *c);
+bool run_prep(Ctx *c);
+bool run_spike_rhs(Ctx *c);
+bool run_sweep(Ctx *c);
+bool run_gram(Ctx *c);
+bool run_coupling_gram(Ctx *c);
+bool run_jacobi(Ctx *c);
+bool run_make_u(Ctx *c);
+bool run_reduced_build(Ctx *c);
+bool run_reduced_factor(Ctx *c);
+
+// solve-phase pieces; nrhs columns, ld = leading dimension of f / x
+bool run_norms(Ctx *c, const double *v, int64_t ld, int nrhs, double *out);
+bool run_residual(Ctx *c, const double *f, const double *x, int64_t ld, int nrhs, bool trans,
+                  bool x_zero);
+bool run_dstage(Ctx *c, const double *rin, int64_t ld, int nrhs);
+bool run_reduced_solve(Ctx *c, int nrhs, bool trans);
+bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs);
+bool run_project_t(Ctx *c, const double *hin, int64_t ld, int nrhs);
+bool run_dstage_t(Ctx *c, const double *hin, int64_t ldh, double *x, int64_t ldx, int nrhs);
+// M^{-1} (or M^{-T}) applied to the scaled FP64 vector r (in c->rv), result
+// out += |r| * M^{-1}(r/|r|); used by the outer loops.
+bool apply_precond(Ctx *c, double *out, int64_t ldo, int nrhs, bool trans);
+
+}  // namespace lrs

@@ -1,0 +1,307 @@
+// The reduced system of the low-rank spike matrix (paper section 3.2), FP64.
+//
+// Unknowns per interface i = 0..p-2 (between partitions i and i+1):
+//   z_i = [zeta_i ; omega_{i+1}],  zeta_i = P_i x_{i+1,t},  omega_{i+1} = Q_{i+1} x_{i,b}
+// (the r-vectors that the paper exchanges instead of k-row tips).  With
+// x_j = g_j - u_{T,j} zeta_j - u_{W,j} omega_j (low-rank recovery) the
+// reduced matrix R = I + V U is block tridiagonal with 2r x 2r blocks
+//   E_i = [[I, P_i u_{W,i+1}^t], [Q_{i+1} u_{T,i}^b, I]]      (diagonal)
+//   F_i = [[P_i u_{T,i+1}^t, 0], [0, 0]]                      (couples z_{i+1})
+//   G_i = [[0, 0], [0, Q_{i+1} u_{W,i}^b]]                    (couples z_{i-1})
+// TRUNCATED (LR-SPIKE-T, S~~_r of eq. 'red_sys_prec_mid_2') keeps E_i only:
+// the paper drops the top tip of T~ and the bottom tip of W~, which are
+// exactly F and G here.  FULL keeps all blocks (the reduced system of
+// LR-SPIKE-I, here solved directly by block LU: R = L_b U_b with
+// Delta_0 = E_0, Gamma_i = G_i Delta_{i-1}^{-1}, Delta_i = E_i - Gamma_i F_{i-1}).
+#include "common.cuh"
+#include "internal.h"
+
+namespace lrs {
+
+template <typename T, int KB>
+__global__ void k_red_build(const T *__restrict__ PQ, const T *__restrict__ Ucat, Parts P, int k,
+                            int r, double *__restrict__ E, double *__restrict__ F,
+                            double *__restrict__ Gs) {
+    const int i = blockIdx.x;
+    const int n2 = 2 * r;
+    const int64_t sn = P.off[i + 1];
+    const T *Pi = PQ + ((int64_t)i * 2 + 0) * r * KB;          // P_i
+    const T *Qn = PQ + ((int64_t)(i + 1) * 2 + 1) * r * KB;    // Q_{i+1}
+    double *e = E + (int64_t)i * n2 * n2, *f = F + (int64_t)i * n2 * n2, *g = Gs + (int64_t)i * n2 * n2;
+    const bool hasF = (i + 1 <= P.p - 2), hasG = (i >= 1);
+    for (int t = threadIdx.x; t < n2 * n2; t += blockDim.x) {
+        const int a = t / n2, b = t % n2;
+        double ev = (a == b) ? 1.0 : 0.0, fv = 0.0, gv = 0.0;
+        if (a < r && b >= r) {            // P_i u_{W,i+1}^t
+            for (int q = 0; q < k; ++q) ev += (double)Pi[a * KB + q] * (double)Ucat[(sn + q) * n2 + b];
+        } else if (a >= r && b < r) {     // Q_{i+1} u_{T,i}^b
+            for (int q = 0; q < k; ++q)
+                ev += (double)Qn[(a - r) * KB + q] * (double)Ucat[(sn - k + q) * n2 + b];
+        }
+        if (hasF && a < r && b < r)       // P_i u_{T,i+1}^t
+            for (int q = 0; q < k; ++q) fv += (double)Pi[a * KB + q] * (double)Ucat[(sn + q) * n2 + b];
+        if (hasG && a >= r && b >= r)     // Q_{i+1} u_{W,i}^b
+            for (int q = 0; q < k; ++q)
+                gv += (double)Qn[(a - r) * KB + q] * (double)Ucat[(sn - k + q) * n2 + b];
+        e[t] = ev;
+        f[t] = fv;
+        g[t] = gv;
+    }
+}
+
+// In-place inverse of the n x n matrix in Ms (row stride n) by Gauss-Jordan
+// elimination with partial pivoting on [M | I]; aug has room for n x 2n.
+// Returns false (to thread 0) on a zero pivot.
+__device__ bool gj_inverse(double *aug, int n, double *fac, int *pivrow) {
+    const int w = 2 * n;
+    bool ok = true;
+    for (int c = 0; c < n; ++c) {
+        if (threadIdx.x == 0) {
+            int best = c;
+            for (int i = c + 1; i < n; ++i)
+                if (fabs(aug[i * w + c]) > fabs(aug[best * w + c])) best = i;
+            *pivrow = best;
+        }
+        __syncthreads();
+        const int pr = *pivrow;
+        if (pr != c)
+            for (int j = threadIdx.x; j < w; j += blockDim.x) {
+                const double t = aug[c * w + j];
+                aug[c * w + j] = aug[pr * w + j];
+                aug[pr * w + j] = t;
+            }
+        __syncthreads();
+        const double piv = aug[c * w + c];
+        if (piv == 0.0 || !isfinite(piv)) ok = false;
+        const double pinv = (piv == 0.0) ? 1.0 : 1.0 / piv;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = aug[i * w + c];
+        __syncthreads();
+        for (int j = threadIdx.x; j < w; j += blockDim.x) aug[c * w + j] *= pinv;
+        __syncthreads();
+        for (int t = threadIdx.x; t < n * w; t += blockDim.x) {
+            const int i = t / w, j = t % w;
+            if (i != c) aug[t] -= fac[i] * aug[c * w + j];
+        }
+        __syncthreads();
+    }
+    return ok;
+}
+
+__device__ void load_aug(double *aug, const double *M, int n) {
+    const int w = 2 * n;
+    for (int t = threadIdx.x; t < n * w; t += blockDim.x) {
+        const int i = t / w, j = t % w;
+        aug[t] = (j < n) ? M[i * n + j] : ((j - n == i) ? 1.0 : 0.0);
+    }
+    __syncthreads();
+}
+
+__device__ void store_inv(const double *aug, double *out, int n) {
+    const int w = 2 * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) out[t] = aug[(t / n) * w + n + t % n];
+}
+
+__global__ void k_red_factor_trunc(const double *__restrict__ E, int n2, double *__restrict__ Rinv,
+                                   int64_t *status) {
+    extern __shared__ double sm[];
+    double *aug = sm, *fac = aug + 2 * n2 * n2;
+    __shared__ int pivrow;
+    const int i = blockIdx.x;
+    load_aug(aug, E + (int64_t)i * n2 * n2, n2);
+    const bool ok = gj_inverse(aug, n2, fac, &pivrow);
+    if (!ok && threadIdx.x == 0) atomicMin((unsigned long long *)status, 0x7ffffffffffffffeULL);
+    store_inv(aug, Rinv + (int64_t)i * n2 * n2, n2);
+}
+
+// Block LU of the block-tridiagonal R in one CTA (sequential over interfaces).
+__global__ void k_red_factor_full(const double *__restrict__ E, const double *__restrict__ F,
+                                  const double *__restrict__ Gs, int n2, int ni,
+                                  double *__restrict__ Rinv, double *__restrict__ Gam,
+                                  int64_t *status) {
+    extern __shared__ double sm[];
+    double *aug = sm, *fac = aug + 2 * n2 * n2, *tmp = fac + n2;
+    __shared__ int pivrow;
+    const int nn = n2 * n2;
+    for (int i = 0; i < ni; ++i) {
+        // Delta_i = E_i - Gamma_i F_{i-1}, Gamma_i = G_i Delta_{i-1}^{-1}
+        if (i > 0) {
+            const double *Dprev = Rinv + (int64_t)(i - 1) * nn;
+            const double *Gi = Gs + (int64_t)i * nn;
+            double *gam = Gam + (int64_t)i * nn;
+            for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+                const int a = t / n2, b = t % n2;
+                double acc = 0.0;
+                for (int q = 0; q < n2; ++q) acc += Gi[a * n2 + q] * Dprev[q * n2 + b];
+                gam[t] = acc;
+            }
+            __syncthreads();
+            const double *Fp = F + (int64_t)(i - 1) * nn;
+            for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+                const int a = t / n2, b = t % n2;
+                double acc = E[(int64_t)i * nn + t];
+                for (int q = 0; q < n2; ++q) acc -= gam[a * n2 + q] * Fp[q * n2 + b];
+                tmp[t] = acc;
+            }
+            __syncthreads();
+            load_aug(aug, tmp, n2);
+        } else {
+            load_aug(aug, E, n2);
+        }
+        const bool ok = gj_inverse(aug, n2, fac, &pivrow);
+        if (!ok && threadIdx.x == 0) atomicMin((unsigned long long *)status, 0x7ffffffffffffffeULL);
+        store_inv(aug, Rinv + (int64_t)i * nn, n2);
+        __syncthreads();
+    }
+}
+
+// z = R^{-1} psi (or R^{-T} psi), TRUNCATED: per interface.
+__global__ void k_red_solve_trunc(const double *__restrict__ Rinv, const double *__restrict__ psi,
+                                  double *__restrict__ z, int n2, int nrhs, int trans) {
+    const int i = blockIdx.x;
+    const double *M = Rinv + (int64_t)i * n2 * n2;
+    const double *v = psi + (int64_t)i * n2 * nrhs;
+    double *o = z + (int64_t)i * n2 * nrhs;
+    for (int t = threadIdx.x; t < n2 * nrhs; t += blockDim.x) {
+        const int a = t / nrhs, c = t % nrhs;
+        double acc = 0.0;
+        for (int q = 0; q < n2; ++q) acc += (trans ? M[q * n2 + a] : M[a * n2 + q]) * v[q * nrhs + c];
+        o[t] = acc;
+    }
+}
+
+// FULL: one CTA, forward and backward block substitution with R = L_b U_b.
+__global__ void k_red_solve_full(const double *__restrict__ Rinv, const double *__restrict__ F,
+                                 const double *__restrict__ Gam, const double *__restrict__ psi,
+                                 double *__restrict__ w, double *__restrict__ z, int n2, int ni,
+                                 int nrhs, int trans) {
+    const int nn = n2 * n2, nv = n2 * nrhs;
+    if (!trans) {
+        // L_b w = psi:  w_i = psi_i - Gamma_i w_{i-1}
+        for (int i = 0; i < ni; ++i) {
+            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+                const int a = t / nrhs, c = t % nrhs;
+                double acc = psi[(int64_t)i * nv + t];
+                if (i > 0)
+                    for (int q = 0; q < n2; ++q)
+                        acc -= Gam[(int64_t)i * nn + a * n2 + q] * w[(int64_t)(i - 1) * nv + q * nrhs + c];
+                w[(int64_t)i * nv + t] = acc;
+            }
+            __syncthreads();
+        }
+        // U_b z = w:  z_i = Delta_i^{-1} (w_i - F_i z_{i+1})
+        for (int i = ni - 1; i >= 0; --i) {
+            double *tmp = w + (int64_t)i * nv;  // reuse w_i in place as the bracket
+            if (i < ni - 1) {
+                for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+                    const int a = t / nrhs, c = t % nrhs;
+                    double acc = tmp[t];
+                    for (int q = 0; q < n2; ++q)
+                        acc -= F[(int64_t)i * nn + a * n2 + q] * z[(int64_t)(i + 1) * nv + q * nrhs + c];
+                    tmp[t] = acc;
+                }
+                __syncthreads();
+            }
+            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+                const int a = t / nrhs, c = t % nrhs;
+                double acc = 0.0;
+                for (int q = 0; q < n2; ++q) acc += Rinv[(int64_t)i * nn + a * n2 + q] * tmp[q * nrhs + c];
+                z[(int64_t)i * nv + t] = acc;
+            }
+            __syncthreads();
+        }
+    } else {
+        // U_b^T y = psi:  y_i = Delta_i^{-T} (psi_i - F_{i-1}^T y_{i-1})
+        for (int i = 0; i < ni; ++i) {
+            double *tmp = w + (int64_t)i * nv;
+            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+                const int a = t / nrhs, c = t % nrhs;
+                double acc = psi[(int64_t)i * nv + t];
+                if (i > 0)
+                    for (int q = 0; q < n2; ++q)
+                        acc -= F[(int64_t)(i - 1) * nn + q * n2 + a] * z[(int64_t)(i - 1) * nv + q * nrhs + c];
+                tmp[t] = acc;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+                const int a = t / nrhs, c = t % nrhs;
+                double acc = 0.0;
+                for (int q = 0; q < n2; ++q) acc += Rinv[(int64_t)i * nn + q * n2 + a] * tmp[q * nrhs + c];
+                z[(int64_t)i * nv + t] = acc;
+            }
+            __syncthreads();
+        }
+        // L_b^T z = y:  z_i = y_i - Gamma_{i+1}^T z_{i+1}   (y held in z)
+        for (int i = ni - 2; i >= 0; --i) {
+            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+                const int a = t / nrhs, c = t % nrhs;
+                double acc = z[(int64_t)i * nv + t];
+                for (int q = 0; q < n2; ++q)
+                    acc -= Gam[(int64_t)(i + 1) * nn + q * n2 + a] * z[(int64_t)(i + 1) * nv + q * nrhs + c];
+                w[(int64_t)i * nv + t] = acc;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < nv; t += blockDim.x) z[(int64_t)i * nv + t] = w[(int64_t)i * nv + t];
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T, int KB>
+static bool build_impl(Ctx *c) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    return launch(c, KID_RED_BUILD, [&] {
+        k_red_build<T, KB><<<c->p - 1, 256, 0, c->stream>>>((const T *)c->PQ, (const T *)c->Ucat, P,
+                                                             c->k, c->r, c->E, c->F, c->Gs);
+    });
+}
+
+bool run_reduced_build(Ctx *c) {
+    if (c->p < 2 || c->r == 0) return true;
+    if (c->fp64) {
+        switch (c->KB) {
+            case 8: return build_impl<double, 8>(c);
+            case 16: return build_impl<double, 16>(c);
+            case 32: return build_impl<double, 32>(c);
+            default: return build_impl<double, 64>(c);
+        }
+    }
+    switch (c->KB) {
+        case 8: return build_impl<float, 8>(c);
+        case 16: return build_impl<float, 16>(c);
+        case 32: return build_impl<float, 32>(c);
+        default: return build_impl<float, 64>(c);
+    }
+}
+
+bool run_reduced_factor(Ctx *c) {
+    if (c->p < 2 || c->r == 0) return true;
+    const int n2 = 2 * c->r, ni = c->p - 1;
+    if (c->opt.reduced == LRSPIKE_REDUCED_TRUNCATED) {
+        const size_t smem = (2 * n2 * n2 + n2) * sizeof(double);
+        cudaFuncSetAttribute(k_red_factor_trunc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return launch(c, KID_RED_FACTOR, [&] {
+            k_red_factor_trunc<<<ni, 256, smem, c->stream>>>(c->E, n2, c->Rinv, c->status);
+        });
+    }
+    const size_t smem = (2 * n2 * n2 + n2 + n2 * n2) * sizeof(double);
+    cudaFuncSetAttribute(k_red_factor_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch(c, KID_RED_FACTOR, [&] {
+        k_red_factor_full<<<1, 256, smem, c->stream>>>(c->E, c->F, c->Gs, n2, ni, c->Rinv, c->Gam,
+                                                       c->status);
+    });
+}
+
+bool run_reduced_solve(Ctx *c, int nrhs, bool trans) {
+    if (c->p < 2 || c->r == 0) return true;
+    const int n2 = 2 * c->r, ni = c->p - 1;
+    if (c->opt.reduced == LRSPIKE_REDUCED_TRUNCATED)
+        return launch(c, KID_RED_SOLVE, [&] {
+            k_red_solve_trunc<<<ni, 128, 0, c->stream>>>(c->Rinv, c->psi, c->zr, n2, nrhs, trans);
+        });
+    return launch(c, KID_RED_SOLVE, [&] {
+        k_red_solve_full<<<1, 256, 0, c->stream>>>(c->Rinv, c->F, c->Gam, c->psi, c->wr, c->zr, n2, ni,
+                                                   nrhs, trans);
+    });
+}
+
+}  // namespace lrs

@@ -1,0 +1,496 @@
+// Solve-phase kernels of one preconditioner application and of the FP64 outer
+// iteration (paper section 2.1 solve summary, eqs. 'D-stage-in-summary' ..
+// 'recovery-stage-in-summary'; section 3.3 low-rank recovery).
+//
+//   k_residual  r = f - A x (or f - A^T x) in FP64 from the band, with the
+//               per-column sum of squares reduced deterministically (fixed
+//               per-CTA partials, summed in order by the last CTA to finish)
+//   k_sumsq     the same reduction for a plain vector (||f||)
+//   k_dstage    g_i = A_i^{-1} (r_i / ||r||) per partition in the working
+//               precision: forward and backward block chains; epilogue forms
+//               psi = V g at both ends of the partition (FP64)
+//   k_retrieve  x += ||r|| (g - u_T zeta - u_W omega)  (update in FP64)
+//   k_project_t a = U^T h (transposed preconditioner, first step)
+//   k_dstage_t  l = D^{-T}(h - V^T w), then x += ||r|| l
+#include "common.cuh"
+#include "internal.h"
+#include "tile_ops.cuh"
+
+namespace lrs {
+
+constexpr int RBS = 256;  // rows per CTA in the row-parallel kernels
+
+// Block reduction of NR per-column sums into partial[blockIdx.x][c]; the last
+// CTA (atomic ticket) sums all partials in CTA order and writes the norms.
+template <int NR>
+__device__ void reduce_columns(double (&ss)[NR], int nrhs, double *partial, unsigned *counter,
+                               double *nrm_out, double *inv_out) {
+    __shared__ double red[NR][RBS / 32];
+    __shared__ bool is_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+        const double v = warp_sum(ss[c]);
+        if (lane == 0) red[c][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nrhs) {
+        double t = 0.0;
+        for (int w = 0; w < RBS / 32; ++w) t += red[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * nrhs + threadIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (is_last && threadIdx.x < nrhs) {
+        __threadfence();
+        double t = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) t += *((volatile double *)&partial[(int64_t)b * nrhs + threadIdx.x]);
+        const double nv = sqrt(t);
+        nrm_out[threadIdx.x] = nv;
+        if (inv_out) inv_out[threadIdx.x] = (nv > 0.0) ? 1.0 / nv : 0.0;
+    }
+    if (is_last && threadIdx.x == 0) *counter = 0u;  // ready for the next launch
+}
+
+template <int NR>
+__global__ void __launch_bounds__(RBS)
+    k_residual(const double *__restrict__ band, int64_t ldb, int k, int64_t n,
+               const double *__restrict__ f, const double *__restrict__ x, int64_t ld, int nrhs,
+               int trans, int xzero, double *__restrict__ r, double *partial, unsigned *counter,
+               double *nrm_out, double *inv_out) {
+    const int64_t i = blockIdx.x * (int64_t)RBS + threadIdx.x;
+    double acc[NR], ss[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) { acc[c] = 0.0; ss[c] = 0.0; }
+    if (i < n) {
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+            if (c < nrhs) acc[c] = f[c * ld + i];
+        if (!xzero) {
+            for (int t = 0; t <= 2 * k; ++t) {
+                const int64_t j = i - k + t;
+                if (j < 0 || j >= n) continue;
+                // A[i][j] = band[(k+i-j) ld + j];  A^T[i][j] = A[j][i] = band[(k+j-i) ld + i]
+                const double a = trans ? band[(int64_t)t * ldb + i] : band[(int64_t)(2 * k - t) * ldb + j];
+#pragma unroll
+                for (int c = 0; c < NR; ++c)
+                    if (c < nrhs) acc[c] -= a * x[c * ld + j];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+            if (c < nrhs) {
+                r[c * n + i] = acc[c];
+                ss[c] = acc[c] * acc[c];
+            }
+    }
+    reduce_columns<NR>(ss, nrhs, partial, counter, nrm_out, inv_out);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(RBS)
+    k_sumsq(const double *__restrict__ v, int64_t ld, int64_t n, int nrhs, double *partial,
+            unsigned *counter, double *nrm_out, double *inv_out) {
+    const int64_t i = blockIdx.x * (int64_t)RBS + threadIdx.x;
+    double ss[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+        ss[c] = 0.0;
+        if (i < n && c < nrhs) { const double t = v[c * ld + i]; ss[c] = t * t; }
+    }
+    reduce_columns<NR>(ss, nrhs, partial, counter, nrm_out, inv_out);
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int KB, Split S>
+__device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
+                            const T *__restrict__ PQ, Parts P, int k, int r, int64_t n,
+                            const double *__restrict__ rin, const double *__restrict__ inv,
+                            int nrhs, T *__restrict__ Yv, T *__restrict__ Gv, double *__restrict__ psi,
+                            unsigned char *smem_raw) {
+    constexpr int NT = Geo<KB>::NT, LDS = KB + 1;
+    T *Ls = reinterpret_cast<T *>(smem_raw);
+    T *dsm = Ls + KB * LDS;
+    T *Tt = dsm + KB;
+    T *Yp = Tt + KB * nrhs;
+    const int part = blockIdx.x;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int64_t b0 = P.boff[part];
+    const int nb = (int)(P.boff[part + 1] - b0);
+    const int pm = KB * nrhs;
+    for (int J = 0; J < nb; ++J) {
+        load_tile<T, KB>(LT + (b0 + J) * KB * KB, Ls, LDS);
+        for (int e = threadIdx.x; e < pm; e += NT) {
+            const int a = e / nrhs, c = e % nrhs;
+            const int64_t row = (int64_t)J * KB + a;
+            Tt[e] = (row < ni) ? (T)(rin[c * n + s + row] * inv[c]) : T(0);
+        }
+        __syncthreads();
+        fwd_step<T, KB, S>(Ls, LDS, Tt, Yp, nrhs, nrhs, J == 0);
+        for (int e = threadIdx.x; e < pm; e += NT) {
+            const int a = e / nrhs, c = e % nrhs;
+            const int64_t row = (int64_t)J * KB + a;
+            if (row < ni) Yv[c * n + s + row] = Yp[e];
+        }
+    }
+    __syncthreads();
+    for (int J = nb - 1; J >= 0; --J) {
+        load_tile<T, KB>(UT + (b0 + J) * KB * KB, Ls, LDS);
+        if (threadIdx.x < KB) dsm[threadIdx.x] = DI[(b0 + J) * KB + threadIdx.x];
+        for (int e = threadIdx.x; e < pm; e += NT) {
+            const int a = e / nrhs, c = e % nrhs;
+            const int64_t row = (int64_t)J * KB + a;
+            Tt[e] = (row < ni) ? Yv[c * n + s + row] : T(0);
+        }
+        __syncthreads();
+        bwd_step<T, KB, S>(Ls, LDS, dsm, Tt, Yp, nrhs, nrhs, J == nb - 1);
+        for (int e = threadIdx.x; e < pm; e += NT) {
+            const int a = e / nrhs, c = e % nrhs;
+            const int64_t row = (int64_t)J * KB + a;
+            if (row < ni) Gv[c * n + s + row] = Yp[e];
+        }
+    }
+    __syncthreads();
+    if (r == 0) return;
+    // psi_{part-1}[0:r] = P_{part-1} g_t ;  psi_part[r:2r] = Q_{part+1} g_b
+    const int n2 = 2 * r;
+    for (int o = threadIdx.x; o < 2 * r * nrhs; o += NT) {
+        const int side = o / (r * nrhs), rem = o % (r * nrhs), j = rem / nrhs, c = rem % nrhs;
+        if (side == 0 && part >= 1) {
+            const T *Pm = PQ + ((int64_t)(part - 1) * 2 + 0) * r * KB + j * KB;
+            double acc = 0.0;
+            for (int q = 0; q < k; ++q) acc += (double)Pm[q] * (double)Gv[c * n + s + q];
+            psi[((int64_t)(part - 1) * n2 + j) * nrhs + c] = acc;
+        } else if (side == 1 && part <= P.p - 2) {
+            const T *Qm = PQ + ((int64_t)(part + 1) * 2 + 1) * r * KB + j * KB;
+            double acc = 0.0;
+            for (int q = 0; q < k; ++q) acc += (double)Qm[q] * (double)Gv[c * n + s + ni - k + q];
+            psi[((int64_t)part * n2 + r + j) * nrhs + c] = acc;
+        }
+    }
+}
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(Geo<KB>::NT)
+    k_dstage(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
+             const T *__restrict__ PQ, Parts P, int k, int r, int64_t n, const double *__restrict__ rin,
+             const double *__restrict__ inv, int nrhs, T *__restrict__ Yv, T *__restrict__ Gv,
+             double *__restrict__ psi) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (nrhs < 4)
+        dstage_body<T, KB, Split::DOTS>(LT, UT, DI, PQ, P, k, r, n, rin, inv, nrhs, Yv, Gv, psi, smem_raw);
+    else
+        dstage_body<T, KB, Split::COLS>(LT, UT, DI, PQ, P, k, r, n, rin, inv, nrhs, Yv, Gv, psi, smem_raw);
+}
+
+// x (+)= nrm * (g - u_T zeta - u_W omega) for one partition's rows.
+template <typename T>
+__global__ void __launch_bounds__(RBS)
+    k_retrieve(const T *__restrict__ Gv, const T *__restrict__ Ucat, const double *__restrict__ zr,
+               Parts P, int r, int64_t n, int nrhs, const double *__restrict__ nrm, double *__restrict__ x,
+               int64_t ld, int accumulate) {
+    extern __shared__ double zs[];  // [2r][nrhs]: zeta_part, omega_part
+    const int part = blockIdx.y;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int n2 = 2 * r;
+    for (int e = threadIdx.x; e < n2 * nrhs; e += RBS) {
+        const int j = e / nrhs, c = e % nrhs;
+        double v = 0.0;
+        if (j < r) { if (part <= P.p - 2) v = zr[((int64_t)part * n2 + j) * nrhs + c]; }
+        else if (part >= 1) v = zr[((int64_t)(part - 1) * n2 + j) * nrhs + c];
+        zs[e] = v;
+    }
+    __syncthreads();
+    const int64_t row = blockIdx.x * (int64_t)RBS + threadIdx.x;
+    if (row >= ni) return;
+    const int64_t gi = s + row;
+    for (int c = 0; c < nrhs; ++c) {
+        T d = Gv[c * n + gi];
+        for (int j = 0; j < n2; ++j) d -= Ucat[gi * n2 + j] * (T)zs[j * nrhs + c];
+        const double upd = nrm[c] * (double)d;
+        x[c * ld + gi] = accumulate ? x[c * ld + gi] + upd : upd;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a = U^T h per partition: alpha_i = u_{T,i}^T h_i -> interface i, rows 0..r-1;
+// beta_i = u_{W,i}^T h_i -> interface i-1, rows r..2r-1.
+template <typename T>
+__global__ void k_project_t(const T *__restrict__ Ucat, Parts P, int r, int64_t n,
+                            const double *__restrict__ hin, const double *__restrict__ inv, int nrhs,
+                            double *__restrict__ psi) {
+    extern __shared__ double red[];
+    const int part = blockIdx.x;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int n2 = 2 * r, O = n2 * nrhs;
+    auto put = [&](int o, double v) {
+        const int j = o / nrhs, c = o % nrhs;
+        if (j < r) { if (part <= P.p - 2) psi[((int64_t)part * n2 + j) * nrhs + c] = v; }
+        else if (part >= 1) psi[((int64_t)(part - 1) * n2 + j) * nrhs + c] = v;
+    };
+    auto dot = [&](int o, int64_t r0, int64_t step) {
+        const int j = o / nrhs, c = o % nrhs;
+        double acc = 0.0;
+        for (int64_t row = r0; row < ni; row += step)
+            acc += (double)(Ucat[(s + row) * n2 + j] * (T)(hin[c * n + s + row] * inv[c]));
+        return acc;
+    };
+    if (O <= (int)blockDim.x) {
+        const int groups = blockDim.x / O;
+        const int g = threadIdx.x / O, o = threadIdx.x % O;
+        if (g < groups) red[g * O + o] = dot(o, g, groups);
+        __syncthreads();
+        if ((int)threadIdx.x < O) {
+            double acc = 0.0;
+            for (int q = 0; q < groups; ++q) acc += red[q * O + threadIdx.x];
+            put(threadIdx.x, acc);
+        }
+    } else {
+        for (int o = threadIdx.x; o < O; o += blockDim.x) put(o, dot(o, 0, 1));
+    }
+}
+
+template <typename T, int KB, Split S>
+__device__ void dstage_t_body(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
+                              const T *__restrict__ PQ, Parts P, int k, int r, int64_t n,
+                              const double *__restrict__ hin, const double *__restrict__ inv,
+                              const double *__restrict__ zr, int nrhs, T *__restrict__ Yv,
+                              const double *__restrict__ nrm, double *__restrict__ x, int64_t ldx,
+                              int accumulate, unsigned char *smem_raw) {
+    constexpr int NT = Geo<KB>::NT, LDS = KB + 1;
+    T *Ta = reinterpret_cast<T *>(smem_raw);   // tile buffer 0
+    T *Tb = Ta + KB * LDS;                     // tile buffer 1
+    T *Tt = Tb + KB * LDS;
+    T *Zp = Tt + KB * nrhs;
+    T *corr = Zp + KB * nrhs;                  // [2][KB][nrhs]: top / bottom tip corrections
+    const int part = blockIdx.x;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int64_t b0 = P.boff[part];
+    const int nb = (int)(P.boff[part + 1] - b0);
+    const int pm = KB * nrhs, n2 = 2 * r;
+    // y = h - V^T w: top rows get P_{part-1}^T w_zeta(part-1), bottom rows Q_{part+1}^T w_omega(part)
+    for (int e = threadIdx.x; e < 2 * pm; e += NT) {
+        const int side = e / pm, rem = e % pm, q = rem / nrhs, c = rem % nrhs;
+        double acc = 0.0;
+        if (q < k && r > 0) {
+            if (side == 0 && part >= 1) {
+                const T *Pm = PQ + ((int64_t)(part - 1) * 2 + 0) * r * KB;
+                for (int j = 0; j < r; ++j)
+                    acc += (double)Pm[j * KB + q] * zr[((int64_t)(part - 1) * n2 + j) * nrhs + c];
+            } else if (side == 1 && part <= P.p - 2) {
+                const T *Qm = PQ + ((int64_t)(part + 1) * 2 + 1) * r * KB;
+                for (int j = 0; j < r; ++j)
+                    acc += (double)Qm[j * KB + q] * zr[((int64_t)part * n2 + r + j) * nrhs + c];
+            }
+        }
+        corr[e] = (T)acc;
+    }
+    __syncthreads();
+    // forward with U^T, carrying z^ = D z
+    for (int J = 0; J < nb; ++J) {
+        T *Ucur = (J & 1) ? Tb : Ta;
+        T *Uprev = (J & 1) ? Ta : Tb;
+        load_tile<T, KB>(UT + (b0 + J) * KB * KB, Ucur, LDS);
+        for (int e = threadIdx.x; e < pm; e += NT) {
+            const int a = e / nrhs, c = e % nrhs;
+            const int64_t row = (int64_t)J * KB + a;
+            T v = T(0);
+            if (row < ni) {
+                v = (T)(hin[c * n + s + row] * inv[c]);
+                if (row < k) v -= corr[row * nrhs + c];
+                if (row >= ni - k) v -= corr[pm + (row - (ni - k)) * nrhs + c];
+            }
+            Tt[e] = v;
+        }
+        __syncthreads();
+        fwdT_step<T, KB, S>(Uprev, Ucur, LDS, Tt, Zp, nrhs, nrhs, J == 0);
+        for (int e = threadIdx.x; e < pm; e += NT) {
+            const int a = e / nrhs, c = e % nrhs;
+            const int64_t row = (int64_t)J * KB + a;
+            if (row < ni) Yv[c * n + s + row] = Zp[e] * DI[(b0 + J) * KB + a];
+        }
+    }
+    __syncthreads();
+    // backward with L^T
+    for (int J = nb - 1; J >= 0; --J) {
+        T *Lcur = (J & 1) ? Tb : Ta;
+        T *Lnext = (J & 1) ? Ta : Tb;
+        load_tile<T, KB>(LT + (b0 + J) * KB * KB, Lcur, LDS);
+        for (int e = threadIdx.x; e < pm; e += NT) {
+            const int a = e / nrhs, c = e % nrhs;
+            const int64_t row = (int64_t)J * KB + a;
+            Tt[e] = (row < ni) ? Yv[c * n + s + row] : T(0);
+        }
+        __syncthreads();
+        bwdT_step<T, KB, S>(Lnext, Lcur, LDS, Tt, Zp, nrhs, nrhs, J == nb - 1);
+        for (int e = threadIdx.x; e < pm; e += NT) {
+            const int a = e / nrhs, c = e % nrhs;
+            const int64_t row = (int64_t)J * KB + a;
+            if (row < ni) {
+                const double upd = nrm[c] * (double)Zp[e];
+                const int64_t xi = c * ldx + s + row;
+                x[xi] = accumulate ? x[xi] + upd : upd;
+            }
+        }
+    }
+}
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(Geo<KB>::NT)
+    k_dstage_t(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
+               const T *__restrict__ PQ, Parts P, int k, int r, int64_t n, const double *__restrict__ hin,
+               const double *__restrict__ inv, const double *__restrict__ zr, int nrhs, T *__restrict__ Yv,
+               const double *__restrict__ nrm, double *__restrict__ x, int64_t ldx, int accumulate) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (nrhs < 4)
+        dstage_t_body<T, KB, Split::DOTS>(LT, UT, DI, PQ, P, k, r, n, hin, inv, zr, nrhs, Yv, nrm, x, ldx,
+                                          accumulate, smem_raw);
+    else
+        dstage_t_body<T, KB, Split::COLS>(LT, UT, DI, PQ, P, k, r, n, hin, inv, zr, nrhs, Yv, nrm, x, ldx,
+                                          accumulate, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+static inline unsigned row_blocks(int64_t n) { return (unsigned)((n + RBS - 1) / RBS); }
+
+template <int NR>
+static bool residual_nr(Ctx *c, const double *f, const double *x, int64_t ld, int nrhs, bool trans,
+                        bool xz) {
+    return launch(c, KID_RESIDUAL, [&] {
+        k_residual<NR><<<row_blocks(c->n), RBS, 0, c->stream>>>(
+            c->band, c->ld, c->k, c->n, f, x, ld, nrhs, trans, xz, c->rv, c->partial, c->counter,
+            c->nrm + c->opt.max_nrhs, c->nrm + 2 * c->opt.max_nrhs);
+    });
+}
+
+bool run_residual(Ctx *c, const double *f, const double *x, int64_t ld, int nrhs, bool trans, bool xz) {
+    if (nrhs <= 1) return residual_nr<1>(c, f, x, ld, nrhs, trans, xz);
+    if (nrhs <= 2) return residual_nr<2>(c, f, x, ld, nrhs, trans, xz);
+    if (nrhs <= 4) return residual_nr<4>(c, f, x, ld, nrhs, trans, xz);
+    if (nrhs <= 8) return residual_nr<8>(c, f, x, ld, nrhs, trans, xz);
+    return residual_nr<16>(c, f, x, ld, nrhs, trans, xz);
+}
+
+template <int NR>
+static bool sumsq_nr(Ctx *c, const double *v, int64_t ld, int nrhs, double *out, double *inv) {
+    return launch(c, KID_NORM, [&] {
+        k_sumsq<NR><<<row_blocks(c->n), RBS, 0, c->stream>>>(v, ld, c->n, nrhs, c->partial, c->counter,
+                                                            out, inv);
+    });
+}
+
+bool run_norms(Ctx *c, const double *v, int64_t ld, int nrhs, double *out) {
+    if (nrhs <= 1) return sumsq_nr<1>(c, v, ld, nrhs, out, nullptr);
+    if (nrhs <= 2) return sumsq_nr<2>(c, v, ld, nrhs, out, nullptr);
+    if (nrhs <= 4) return sumsq_nr<4>(c, v, ld, nrhs, out, nullptr);
+    if (nrhs <= 8) return sumsq_nr<8>(c, v, ld, nrhs, out, nullptr);
+    return sumsq_nr<16>(c, v, ld, nrhs, out, nullptr);
+}
+
+template <typename T, int KB>
+static bool dstage_impl(Ctx *c, const double *rin, int nrhs) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    const size_t smem = (KB * (KB + 1) + KB + 2 * KB * nrhs) * sizeof(T);
+    auto kern = k_dstage<T, KB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch(c, KID_DSTAGE, [&] {
+        kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT, (const T *)c->DI,
+                                                     (const T *)c->PQ, P, c->k, c->r, c->n, rin,
+                                                     c->nrm + 2 * c->opt.max_nrhs, nrhs, (T *)c->Yv,
+                                                     (T *)c->Gv, c->psi);
+    });
+}
+
+template <typename T, int KB>
+static bool dstage_t_impl(Ctx *c, const double *hin, double *x, int64_t ldx, int nrhs, int acc) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    const size_t smem = (2 * KB * (KB + 1) + 4 * KB * nrhs) * sizeof(T);
+    auto kern = k_dstage_t<T, KB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch(c, KID_DSTAGE_T, [&] {
+        kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT, (const T *)c->DI,
+                                                     (const T *)c->PQ, P, c->k, c->r, c->n, hin,
+                                                     c->nrm + 2 * c->opt.max_nrhs, c->zr, nrhs, (T *)c->Yv,
+                                                     c->nrm + c->opt.max_nrhs, x, ldx, acc);
+    });
+}
+
+template <typename T>
+static bool retrieve_impl(Ctx *c, double *x, int64_t ld, int nrhs, int acc) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    dim3 grid(row_blocks(c->maxni), c->p);
+    const size_t smem = (size_t)(2 * c->r * nrhs + 1) * sizeof(double);
+    return launch(c, KID_RETRIEVE, [&] {
+        k_retrieve<T><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r,
+                                                     c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc);
+    });
+}
+
+template <typename T>
+static bool project_t_impl(Ctx *c, const double *hin, int nrhs) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    const size_t smem = (size_t)256 * sizeof(double) + (size_t)2 * c->r * nrhs * sizeof(double);
+    return launch(c, KID_PROJECT_T, [&] {
+        k_project_t<T><<<c->p, 256, smem, c->stream>>>((const T *)c->Ucat, P, c->r, c->n, hin,
+                                                      c->nrm + 2 * c->opt.max_nrhs, nrhs, c->psi);
+    });
+}
+
+bool run_dstage(Ctx *c, const double *rin, int64_t, int nrhs) {
+    if (c->fp64) {
+        switch (c->KB) {
+            case 8: return dstage_impl<double, 8>(c, rin, nrhs);
+            case 16: return dstage_impl<double, 16>(c, rin, nrhs);
+            case 32: return dstage_impl<double, 32>(c, rin, nrhs);
+            default: return dstage_impl<double, 64>(c, rin, nrhs);
+        }
+    }
+    switch (c->KB) {
+        case 8: return dstage_impl<float, 8>(c, rin, nrhs);
+        case 16: return dstage_impl<float, 16>(c, rin, nrhs);
+        case 32: return dstage_impl<float, 32>(c, rin, nrhs);
+        default: return dstage_impl<float, 64>(c, rin, nrhs);
+    }
+}
+
+bool run_dstage_t(Ctx *c, const double *hin, int64_t, double *x, int64_t ldx, int nrhs) {
+    const int acc = 1;
+    if (c->fp64) {
+        switch (c->KB) {
+            case 8: return dstage_t_impl<double, 8>(c, hin, x, ldx, nrhs, acc);
+            case 16: return dstage_t_impl<double, 16>(c, hin, x, ldx, nrhs, acc);
+            case 32: return dstage_t_impl<double, 32>(c, hin, x, ldx, nrhs, acc);
+            default: return dstage_t_impl<double, 64>(c, hin, x, ldx, nrhs, acc);
+        }
+    }
+    switch (c->KB) {
+        case 8: return dstage_t_impl<float, 8>(c, hin, x, ldx, nrhs, acc);
+        case 16: return dstage_t_impl<float, 16>(c, hin, x, ldx, nrhs, acc);
+        case 32: return dstage_t_impl<float, 32>(c, hin, x, ldx, nrhs, acc);
+        default: return dstage_t_impl<float, 64>(c, hin, x, ldx, nrhs, acc);
+    }
+}
+
+bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs) {
+    return c->fp64 ? retrieve_impl<double>(c, x, ld, nrhs, 1) : retrieve_impl<float>(c, x, ld, nrhs, 1);
+}
+
+bool run_project_t(Ctx *c, const double *hin, int64_t, int nrhs) {
+    if (c->p < 2 || c->r == 0) return true;
+    return c->fp64 ? project_t_impl<double>(c, hin, nrhs) : project_t_impl<float>(c, hin, nrhs);
+}
+
+bool apply_precond(Ctx *c, double *out, int64_t ldo, int nrhs, bool trans) {
+    if (!trans) {
+        if (!run_dstage(c, c->rv, c->n, nrhs)) return false;
+        if (!run_reduced_solve(c, nrhs, false)) return false;
+        return run_retrieve(c, out, ldo, nrhs);
+    }
+    if (!run_project_t(c, c->rv, c->n, nrhs)) return false;
+    if (!run_reduced_solve(c, nrhs, true)) return false;
+    return run_dstage_t(c, c->rv, c->n, out, ldo, nrhs);
+}
+
+}  // namespace lrs

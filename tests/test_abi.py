@@ -1,0 +1,78 @@
+"""Host-only checks of the C ABI: the library loads, exports every function that
+include/lrspike.h declares, and rejects bad options before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2504_11167_gb300 import solver
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lrspike.h")).read()
+    return sorted(set(re.findall(r"\b(lrspike_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_11167_gb300 import _build
+    _build.build()
+    return solver.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "lrspike_create" in names and "lrspike_solve_transpose" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(solver.EXPORTS)
+
+
+def _opts(lib, n=1000, k=8, p=4, r=2):
+    o = solver.Options()
+    assert lib.lrspike_options_default(ctypes.byref(o), n, k, p, r) == 0
+    return o
+
+
+def test_defaults(lib):
+    o = _opts(lib)
+    assert (o.n, o.k, o.p, o.r) == (1000, 8, 4, 2)
+    assert o.precision == 0 and o.compress == 0 and o.reduced == 0 and o.outer == 0
+    assert o.tol == 1e-12 and o.max_iter == 50 and o.max_nrhs == 16
+    assert lib.lrspike_options_default(None, 1, 1, 1, 1) == 1
+
+
+@pytest.mark.parametrize("field,value", [("k", 65), ("k", -1), ("r", 9), ("r", -1), ("p", 0),
+                                         ("n", 0), ("max_nrhs", 0), ("max_nrhs", 17),
+                                         ("precision", 7), ("outer", 5), ("compress", 2)])
+def test_create_rejects_bad_options(lib, field, value):
+    o = _opts(lib)
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    st = lib.lrspike_create(ctypes.byref(o), None, ctypes.byref(h))
+    assert st == 1, (field, value, st)
+    assert not h.value
+    assert len(lib.lrspike_last_error(None)) > 0
+
+
+def test_create_rejects_partitions_not_wider_than_k(lib):
+    o = _opts(lib, n=40, k=8, p=5, r=2)      # n_i = 8 = k
+    h = ctypes.c_void_p()
+    assert lib.lrspike_create(ctypes.byref(o), None, ctypes.byref(h)) == 1
+    assert b"n_i > k" in lib.lrspike_last_error(None)
+
+
+def test_null_handle_calls(lib):
+    assert lib.lrspike_destroy(None) == 0
+    assert lib.lrspike_factor(None, None, 0) == 1
+    assert lib.lrspike_solve(None, None, None, 1, 1, None) == 1
+    assert lib.lrspike_launch_count(None) == 0
+
+
+def test_missing_library_raises(tmp_path, monkeypatch):
+    monkeypatch.setattr(solver, "_lib", None)
+    with pytest.raises(solver.LRSpikeError):
+        solver.load_library(str(tmp_path / "nope.so"))
