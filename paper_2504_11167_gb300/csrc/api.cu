@@ -161,7 +161,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     c->n = o.n;
     c->k = o.k;
     c->p = o.p;
-    c->r = o.r;
+    c->r = (o.p > 1) ? o.r : 0;  // one partition has no spikes and no reduced system
     c->KB = 8;
     while (c->KB < o.k) c->KB *= 2;
     c->fp64 = (o.precision == LRSPIKE_FP64);
@@ -444,7 +444,7 @@ extern "C" lrspike_status lrspike_get_reduced(lrspike_handle h, double *sigma, d
     const int r = c->r, n2 = 2 * r, ni = c->p - 1;
     const bool spikes = (c->p > 1 && r > 0);
     if (sigma) {
-        const size_t cnt = (size_t)c->p * 2 * r;
+        const size_t cnt = (size_t)c->p * 2 * c->opt.r;
         if (spikes) {
             if (cudaMemcpy(sigma, c->sigma, cnt * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
                 return cuda_fail(c, "sigma copy");

@@ -264,7 +264,11 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
         __syncthreads();
     }
     // eigenvalues, ranked by decreasing value (ties: lower index first)
-    if (threadIdx.x < KB) lam[threadIdx.x] = A[threadIdx.x * LD + threadIdx.x];
+    // a NaN (from a singular factorisation) ranks last so that order[] stays a permutation
+    if (threadIdx.x < KB) {
+        const T v = A[threadIdx.x * LD + threadIdx.x];
+        lam[threadIdx.x] = (v == v) ? v : T(-INFINITY);
+    }
     __syncthreads();
     if (threadIdx.x < KB) {
         const int j = threadIdx.x;
