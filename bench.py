@@ -1,0 +1,327 @@
+"""Benchmark of the LR-SPIKE hot path on GB300.
+
+Workload (the large banded mixed-precision configuration): n = 4,194,304,
+half-bandwidth k = 64, p = 256 partitions (n_i = 16,384), rank r = 16, one
+right-hand side, dominance factor 1.1, working precision FP32 with FP64
+iterative refinement to relative residual 1e-10, LR-SPIKE-T (truncated reduced
+system).  One step = the whole path on one batch of input: LR-SPIKE
+factorisation (band LU, spikes, compression, reduced system) plus the solve to
+tolerance.  Metric: solved unknowns per second = n * nrhs / step time.
+
+Also reported on the same inputs: the plain FP64 GPU path (same kernels in
+FP64) for the mixed-versus-FP64 comparison, the end-to-end number through the
+C ABI with host buffers (host-to-device copies of the band and f and the
+device-to-host copy of x inside the timed region), the roofline of the
+dominant kernel, and the CPU oracle timed on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+With N > 1 (torchrun), every rank solves its own copy of the workload (the
+path needs no exchange between independent systems; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, K, P, R, NRHS, DOM, TOL = 4194304, 64, 256, 16, 1, 1.1, 1e-10
+METRIC = "LR-SPIKE solved unknowns/s at rel. residual 1e-10 (mixed FP32+FP64 IR, LR-SPIKE-T)"
+UNIT = "unknowns/s"
+WORKLOAD = "banded n=4194304 k=64 p=256 r=16 nrhs=1 dominance=1.1"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def config_dict(precision="fp32"):
+    return {"workload": WORKLOAD, "n": N, "k": K, "p": P, "r": R, "nrhs": NRHS, "dominance": DOM,
+            "precision": precision, "reduced": "truncated", "compress": "spike", "outer": "ir",
+            "tol": TOL, "l2": "inputs larger than L2 (4.3 GB FP64 band re-read each step)",
+            "seed": int(__import__("paper_2504_11167_gb300.inputs", fromlist=["x"]).SEED_BASE + 2)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the reference arm and the cpu_baseline key)
+# --------------------------------------------------------------------------
+def cpu_sample(parts: int, threads: int):
+    """Oracle LR-SPIKE-T on `parts` partitions of the workload's geometry
+    (n_i = 16384, k = 64, r = 16, dominance 1.1), IR to 1e-10."""
+    from oracle import lrspike_oracle as O
+    from paper_2504_11167_gb300 import inputs
+    n = parts * (N // P)
+    seed = inputs.SEED_BASE + 2
+    ab = inputs.dominant_band(n, K, DOM, seed)
+    f = np.ascontiguousarray(inputs.rhs(n, NRHS, seed))
+    t0 = time.perf_counter()
+    fac = O.factor(ab, K, parts, R, reduced="truncated", threads=threads)
+    res = O.ir_solve(ab, K, fac, f, tol=TOL)
+    dt = time.perf_counter() - t0
+    assert res.converged, res.rel_residual
+    return n * NRHS / dt, dt, n, res.iterations
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    parts = int(os.environ.get("LRSPIKE_CPU_PARTS", "32"))
+    vals, times = [], []
+    for i in range(args.warmup + args.steps):
+        v, dt, n, its = cpu_sample(parts, threads)
+        if i >= args.warmup:
+            vals.append(v)
+            times.append(dt)
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.median(times)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict("fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{parts} partitions of the workload geometry "
+                                       f"(n={n}, k={K}, r={R}), factor + IR to {TOL}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in self.rows:
+            try:
+                sm.append(float(row[1]))
+                mx = float(row[2])
+                for nm, v in zip(names, row[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+def kernel_work(name: str, prof: dict, precision_bytes: int):
+    """Algorithmic bytes moved (HBM-bound kernels) or flops (compute-bound
+    kernels) of one launch, from the workload's sizes."""
+    n, k, kb, r, nrhs = N, K, 64, R, NRHS
+    tb = precision_bytes
+    if name == "residual":          # FP64 band + f, x read, r written
+        return "hbm", (2 * k + 1) * n * 8 + n * nrhs * 8 * 3
+    if name == "dstage":            # packed factor tiles (2 KB^2 + KB per block) + r, y, g
+        return "hbm", n * (2 * kb + 1) * tb + n * nrhs * (8 + 4 * tb)
+    if name == "retrieve":          # u columns + g + x read/write
+        return "hbm", n * 2 * r * tb + n * nrhs * (tb + 16)
+    if name == "band_lu":           # 2 n k^2 flops (block steps on KB = k)
+        return "alu", 2.0 * n * k * k
+    if name == "spike_sweep":       # triangular block products, V fwd skipped? (counted as done)
+        return "alu", 6.0 * n * k * k
+    return None, None
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_2504_11167_gb300 import inputs
+    from paper_2504_11167_gb300.solver import LRSpike
+
+    seed = inputs.SEED_BASE + 2
+    ab = inputs.dominant_band(N, K, DOM, seed)
+    f = np.ascontiguousarray(inputs.rhs(N, NRHS, seed).T)          # (nrhs, n)
+    dev = torch.device("cuda", local)
+    band = torch.from_numpy(ab).to(dev)
+    ft = torch.from_numpy(f).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def run(precision, steps, warmup, profile):
+        s = LRSpike(N, K, P, R, precision=precision, reduced="truncated", tol=TOL, max_nrhs=NRHS,
+                    profile=profile)
+        for _ in range(warmup):
+            s.factor(band)
+            s.solve(ft)
+        s.profile_reset()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        info = None
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            l0 = s.launch_count()
+            for _ in range(steps):
+                s.factor(band)
+                x, info = s.solve(ft)
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1) / steps
+        launches = s.launch_count() - l0
+        prof = s.profile() if profile else {}
+        x = x.clone()
+        s.close()
+        return ms, launches, prof, info, clk.summary(), x
+
+    ms, launches, prof, info, clocks, x = run("fp32", args.steps, args.warmup, True)
+    # independent FP64 check of the final residual (torch ops, not the library)
+    res = ft.clone()
+    for d in range(2 * K + 1):
+        off = d - K                                       # A[j+off, j] = band[d, j]
+        lo, hi = max(0, -off), min(N, N - off)
+        res[:, lo + off:hi + off] -= band[d, lo:hi] * x[:, lo:hi]
+    relres = float((res.norm(dim=1) / ft.norm(dim=1)).max())
+    assert relres <= TOL * 1.01, relres
+
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * N * NRHS / (ms_max * 1e-3)
+
+    # dominant kernel and its roofline
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roofline = None
+    if top:
+        name, (cnt, tot) = top
+        bound, work = kernel_work(name, prof, 4)
+        per_launch_s = tot / max(cnt, 1) * 1e-3
+        if bound == "hbm":
+            ach = work / per_launch_s / 1e9
+            roofline = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                        "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+        elif bound == "alu":
+            alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # FP32 FMA lanes x clock
+            ach = work / per_launch_s / 1e12
+            roofline = {"kernel": name, "bound": "alu", "achieved": ach, "peak": alu_peak,
+                        "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    kernels = {k_: {"launches": c_, "ms_total": round(t_, 4)} for k_, (c_, t_) in prof.items() if c_}
+
+    # plain FP64 GPU path on the same inputs
+    fp64 = None
+    if not args.no_fp64:
+        ms64, _, _, info64, _, _ = run("fp64", max(1, args.steps // 2), 1, False)
+        fp64 = {"value": N * NRHS / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                "iterations": info64["iterations"], "tol": TOL}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    try:
+        hb = torch.from_numpy(ab).pin_memory()
+        hf = torch.from_numpy(f).pin_memory()
+        hx = torch.empty_like(hf).pin_memory()
+        s = LRSpike(N, K, P, R, precision="fp32", reduced="truncated", tol=TOL, max_nrhs=NRHS)
+        s.factor(hb)
+        s.solve(hf, hx)
+        barrier()
+        t0 = time.perf_counter()
+        esteps = max(1, args.steps // 2)
+        for _ in range(esteps):
+            s.factor(hb)
+            s.solve(hf, hx)
+        barrier()
+        e_ms = (time.perf_counter() - t0) * 1e3 / esteps
+        s.close()
+        e2e = {"value": world * N * NRHS / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(hb.numel() * 8 + hf.numel() * 8),
+               "d2h_bytes_per_step": int(hx.numel() * 8)}
+    except Exception as exc:  # report, do not hide
+        e2e = {"error": repr(exc)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        parts = int(os.environ.get("LRSPIKE_CPU_PARTS", "32"))
+        v, dt, n_s, its = cpu_sample(parts, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{parts} partitions of the workload geometry (n={n_s}, k={K}, r={R}), "
+                         f"factor + IR to {TOL}: {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": config_dict(), "iterations": info["iterations"],
+                "rel_residual": relres, "gpu_launches": launches, "roofline": roofline,
+                "kernels": kernels, "fp64_gpu": fp64, "e2e": e2e, "cpu_baseline": cpu,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

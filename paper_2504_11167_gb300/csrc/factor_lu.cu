@@ -199,13 +199,14 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
 }
 
 // Per block: L^{-1} (unit lower), the unit upper inverse of D^{-1}U, D^{-1}
-// and D^{-1} U_{J,J+1}.  Thread c < KB inverts column c of L by forward
-// substitution; thread KB + c column c of U by back substitution.
+// and D^{-1} U_{J,J+1}.  Both inverses are built right-looking: for pivot j
+// every entry below (L) or above (U) it is updated at once, one barrier per
+// j; half of the CTA works on L, the other half on U.
 template <typename T, int KB>
 __global__ void __launch_bounds__(Geo<KB>::NT)
     k_prep_inverse(T *__restrict__ LT, T *__restrict__ UT, const T *__restrict__ DS,
                    T *__restrict__ DI) {
-    constexpr int NT = Geo<KB>::NT, LD = KB + 1;
+    constexpr int NT = Geo<KB>::NT, LD = KB + 1, HALF = NT / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *L = reinterpret_cast<T *>(smem_raw), *U = L + KB * LD, *XL = U + KB * LD, *XU = XL + KB * LD;
     const int64_t blk = blockIdx.x;
@@ -213,29 +214,45 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
     T *ut = UT + blk * KB * KB;
     for (int e = threadIdx.x; e < KB * KB; e += NT) {
         const int a = e / KB, b = e % KB;
-        L[a * LD + b] = lt[e];
-        U[a * LD + b] = ut[e];
+        const T lv = lt[e], uv = ut[e];
+        L[a * LD + b] = lv;
+        U[a * LD + b] = uv;
+        XL[a * LD + b] = (a == b) ? T(1) : T(0);
+        XU[a * LD + b] = T(0);
     }
     __syncthreads();
-    const int t = threadIdx.x;
-    if (t < KB) {
-        const int c = t;
-        XL[c * LD + c] = T(1);
-        for (int a = c + 1; a < KB; ++a) {
-            T acc = T(0);
-            for (int j = c; j < a; ++j) acc += L[a * LD + j] * XL[j * LD + c];
-            XL[a * LD + c] = -acc;
-        }
-    } else if (t < 2 * KB) {
-        const int c = t - KB;
-        XU[c * LD + c] = T(1) / U[c * LD + c];
-        for (int a = c - 1; a >= 0; --a) {
-            T acc = T(0);
-            for (int j = a + 1; j <= c; ++j) acc += U[a * LD + j] * XU[j * LD + c];
-            XU[a * LD + c] = -acc / U[a * LD + a];
-        }
-    }
+    if (threadIdx.x < KB) XU[threadIdx.x * LD + threadIdx.x] = T(1) / U[threadIdx.x * LD + threadIdx.x];
     __syncthreads();
+    // step j: XL[a][c] -= L[a][j] XL[j][c] for a > j, c <= j  (X = L^{-1}, unit lower)
+    //         XU[a][c] -= U[a][j] XU[j][c] / U[a][a] for a < j', processed with j' = KB-1-j
+    //         (X = U^{-1}, back substitution by columns from the right)
+    const bool lower = threadIdx.x < HALF;
+    const int t = lower ? threadIdx.x : threadIdx.x - HALF;
+    for (int j = 0; j < KB; ++j) {
+        if (lower) {
+            const int rows = KB - 1 - j, cols = j + 1;
+            for (int e = t; e < rows * cols; e += HALF) {
+                const int a = j + 1 + e / cols, c = e % cols;
+                XL[a * LD + c] -= L[a * LD + j] * XL[j * LD + c];
+            }
+        } else {
+            const int jj = KB - 1 - j;           // finished row of U^{-1}
+            const int rows = jj, cols = KB - jj;
+            for (int e = t; e < rows * cols; e += HALF) {
+                const int a = e / cols, c = jj + e % cols;
+                XU[a * LD + c] -= U[a * LD + jj] * XU[jj * LD + c];
+            }
+        }
+        __syncthreads();
+        if (!lower) {
+            // row KB-2-j of U^{-1} is complete once all pivots to its right are
+            // applied; scale it by 1 / u_aa (the diagonal entry was set above)
+            const int a = KB - 2 - j;
+            if (a >= 0)
+                for (int c = a + 1 + t; c < KB; c += HALF) XU[a * LD + c] /= U[a * LD + a];
+        }
+        __syncthreads();
+    }
     for (int e = threadIdx.x; e < KB * KB; e += NT) {
         const int a = e / KB, b = e % KB;
         if (a > b) {

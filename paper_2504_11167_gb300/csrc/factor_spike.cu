@@ -210,10 +210,16 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
     __shared__ T lam[KB];
     const int id = blockIdx.x;  // part * 2 + g
     const double *G = Gram + (int64_t)id * KB * KB;
+    __shared__ T amax;
     for (int e = threadIdx.x; e < KB * KB; e += NT) {
         const int a = e / KB, b = e % KB;
         A[a * LD + b] = (T)G[e];
         V[a * LD + b] = (a == b) ? T(1) : T(0);
+    }
+    if (threadIdx.x == 0) {
+        T m = T(0);
+        for (int a = 0; a < KB; ++a) m = fmax(m, fabs((T)G[a * KB + a]));
+        amax = m;
     }
     __syncthreads();
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -228,7 +234,12 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
                 if (p > q) { const int t = p; p = q; q = t; }
                 const T app = A[p * LD + p], aqq = A[q * LD + q], apq = A[p * LD + q];
                 T c = T(1), s = T(0);
-                if (apq != T(0) && fabs((double)apq) > (double)Eps<T>::v * sqrt(fabs((double)app * (double)aqq))) {
+                // rotate while the pair is not yet diagonal to working precision:
+                // relative to the pair, with an absolute floor of eps * (largest
+                // initial diagonal entry) below which off-diagonals are rounding noise
+                const double thr = fmax((double)Eps<T>::v * sqrt(fabs((double)app * (double)aqq)),
+                                        2.0 * (double)Eps<T>::v * (double)amax);
+                if (apq != T(0) && fabs((double)apq) > thr) {
                     const T tau = (aqq - app) / (T(2) * apq);
                     const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
                     c = T(1) / sqrt(T(1) + t * t);
@@ -389,7 +400,7 @@ static bool jacobi_impl(Ctx *c) {
     auto kern = k_jacobi<T, KB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_JACOBI, [&] {
-        kern<<<2 * c->p, Geo<KB>::NT, smem, c->stream>>>(c->Gram, c->r, c->opt.rank_tol, 40, (T *)c->PQ,
+        kern<<<2 * c->p, Geo<KB>::NT, smem, c->stream>>>(c->Gram, c->r, c->opt.rank_tol, c->fp64 ? 30 : 20, (T *)c->PQ,
                                                          c->sigma);
     });
 }

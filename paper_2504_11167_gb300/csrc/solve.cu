@@ -43,13 +43,25 @@ __device__ void reduce_columns(double (&ss)[NR], int nrhs, double *partial, unsi
     __syncthreads();
     if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (is_last && threadIdx.x < nrhs) {
+    if (is_last) {
+        // fixed assignment of partials to threads and a fixed tree: deterministic
         __threadfence();
-        double t = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) t += *((volatile double *)&partial[(int64_t)b * nrhs + threadIdx.x]);
-        const double nv = sqrt(t);
-        nrm_out[threadIdx.x] = nv;
-        if (inv_out) inv_out[threadIdx.x] = (nv > 0.0) ? 1.0 / nv : 0.0;
+        __shared__ double tot[RBS / 32];
+        for (int c = 0; c < nrhs; ++c) {
+            double t = 0.0;
+            for (unsigned b = threadIdx.x; b < gridDim.x; b += RBS) t += __ldcg(&partial[(int64_t)b * nrhs + c]);
+            t = warp_sum(t);
+            if (lane == 0) tot[wid] = t;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < RBS / 32; ++w) sum += tot[w];
+                const double nv = sqrt(sum);
+                nrm_out[c] = nv;
+                if (inv_out) inv_out[c] = (nv > 0.0) ? 1.0 / nv : 0.0;
+            }
+            __syncthreads();
+        }
     }
     if (is_last && threadIdx.x == 0) *counter = 0u;  // ready for the next launch
 }
