@@ -188,8 +188,11 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     }
     c->NB = c->boff_h[c->p];
     const bool spikes = (c->p > 1 && c->r > 0);
-    c->m = spikes ? (o.compress == LRSPIKE_COMPRESS_COUPLING ? 2 * c->r : 2 * c->KB) : 0;
-    c->gram_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(16, minnb));
+    // spike panel columns: a multiple of 16 (the register-tiled sweep's column
+    // groups); T_i in the first half, W_i in the second half
+    c->m = spikes ? (o.compress == LRSPIKE_COMPRESS_COUPLING ? 16 * ((2 * c->r + 15) / 16) : 2 * c->KB) : 0;
+    if (c->m == 48) c->m = 64;  // column groups of 1, 2, 4 or 8
+    c->gram_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(32, minnb));
     const size_t T = c->tsize, KB = c->KB, NB = c->NB, mx = o.max_nrhs;
     const size_t n2 = 2 * c->r, ni = (size_t)std::max(0, c->p - 1);
     const int64_t rb = (c->n + 255) / 256;

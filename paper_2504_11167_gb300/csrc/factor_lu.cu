@@ -67,19 +67,33 @@ __device__ void load_colblock(const double *__restrict__ band, int64_t ld, int k
     __syncthreads();
 }
 
+// Register layout of the LU window: a TY x TX thread grid; in each of the three
+// live quadrants (TL = S_J, TR = A_{J,J+1}, BL = A_{J+1,J}) a thread owns the
+// entries (ty + TY*i, tx + TX*j), i < RY, j < RX.  The fourth quadrant (the
+// next diagonal block) is not touched by the column steps: it is updated once
+// per block step by the Schur product S_{J+1} = A_{J+1,J+1} - L_{J+1,J} U_{J,J+1}.
+template <int KB> struct LuGeo {
+    static constexpr int NT = 4 * KB;
+    static constexpr int TX = (KB >= 16) ? 16 : 8;
+    static constexpr int TY = NT / TX;
+    static constexpr int RY = KB / TY;
+    static constexpr int RX = KB / TX;
+};
+
 template <typename T, int KB>
-__global__ void __launch_bounds__(Geo<KB>::NT)
+__global__ void __launch_bounds__(4 * KB)
     k_band_lu(const double *__restrict__ band, int64_t ld, int k, Parts P, T *__restrict__ LT,
               T *__restrict__ UT, T *__restrict__ DS, int64_t *__restrict__ status) {
-    using G = Geo<KB>;
-    constexpr int W = G::W, TX = G::TX, TY = G::TY, RY = G::RY, RX = G::RX;
-    constexpr int HY = RY / 2, HX = RX / 2;  // register index of the quadrant split
+    using G = LuGeo<KB>;
+    constexpr int TX = G::TX, TY = G::TY, RY = G::RY, RX = G::RX, LDT = KB + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *up = reinterpret_cast<T *>(smem_raw);
-    T *dg = up + KB * KB;
-    T *lo2 = dg + KB * KB;        // two lower tiles (ping-pong by block parity)
-    T *rowb = lo2 + 2 * KB * KB;  // [2][W]
-    T *colb = rowb + 2 * W;       // [2][W]
+    T *up = reinterpret_cast<T *>(smem_raw);  // A_{J,J+1}
+    T *dg = up + KB * KB;                     // A_{J+1,J+1}
+    T *lo2 = dg + KB * KB;                    // A_{J+1,J}, two buffers by block parity
+    T *Ys = lo2 + 2 * KB * KB;                // L_{J+1,J}  (KB x LDT)
+    T *Zs = Ys + KB * LDT;                    // U_{J,J+1}  (KB x LDT)
+    T *rowb = Zs + KB * LDT;                  // [2][2KB]: pivot row of [TL | TR]
+    T *colb = rowb + 4 * KB;                  // [2][2KB]: pivot column of [TL ; BL]
 
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
@@ -87,190 +101,248 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
     const int nb = (int)(P.boff[part + 1] - b0);
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
 
-    T w[RY][RX];
-    // column block 0: A_00 into the window, A_10 into lo2[0]
+    T tl[RY][RX], tr[RY][RX], bl[RY][RX];
     load_colblock<T, KB>(band, ld, k, s, ni, 0, up, dg, lo2);
 #pragma unroll
-    for (int i = 0; i < HY; ++i)
+    for (int i = 0; i < RY; ++i)
 #pragma unroll
-        for (int j = 0; j < HX; ++j) w[i][j] = dg[(ty + TY * i) * KB + tx + TX * j];
+        for (int j = 0; j < RX; ++j) tl[i][j] = dg[(ty + TY * i) * KB + tx + TX * j];
     __syncthreads();
 
     for (int J = 0; J < nb; ++J) {
         const bool last = (J == nb - 1);
-        T *lo_cur = lo2 + (J & 1) * KB * KB;        // A_{J+1,J}
-        T *lo_next = lo2 + ((J + 1) & 1) * KB * KB;  // receives A_{J+2,J+1}
+        const T *lo_cur = lo2 + (J & 1) * KB * KB;
+        T *lo_next = lo2 + ((J + 1) & 1) * KB * KB;
         if (!last) load_colblock<T, KB>(band, ld, k, s, ni, J + 1, up, dg, lo_next);
-        // remaining quadrants of the window
 #pragma unroll
         for (int i = 0; i < RY; ++i)
 #pragma unroll
             for (int j = 0; j < RX; ++j) {
-                if (i < HY && j < HX) continue;
                 const int a = ty + TY * i, b = tx + TX * j;
-                T v;
-                if (last) v = (a == b) ? T(1) : T(0);
-                else if (i < HY) v = up[a * KB + (b - KB)];
-                else if (j < HX) v = lo_cur[(a - KB) * KB + b];
-                else v = dg[(a - KB) * KB + (b - KB)];
-                w[i][j] = v;
+                tr[i][j] = last ? T(0) : up[a * KB + b];
+                bl[i][j] = last ? T(0) : lo_cur[a * KB + b];
             }
-        // publish pivot row / column 0
-#pragma unroll
-        for (int i = 0; i < RY; ++i)
+        if (ty == 0)
 #pragma unroll
             for (int j = 0; j < RX; ++j) {
-                const int a = ty + TY * i, b = tx + TX * j;
-                if (a == 0) rowb[b] = w[i][j];
-                if (b == 0) colb[a] = w[i][j];
+                rowb[tx + TX * j] = tl[0][j];
+                rowb[KB + tx + TX * j] = tr[0][j];
+            }
+        if (tx == 0)
+#pragma unroll
+            for (int i = 0; i < RY; ++i) {
+                colb[ty + TY * i] = tl[i][0];
+                colb[KB + ty + TY * i] = bl[i][0];
             }
         __syncthreads();
 
         for (int c = 0; c < KB; ++c) {
-            const T *rb = rowb + (c & 1) * W;
-            const T *cb = colb + (c & 1) * W;
-            T *rn = rowb + ((c + 1) & 1) * W;
-            T *cn = colb + ((c + 1) & 1) * W;
+            const T *rb = rowb + (c & 1) * 2 * KB;
+            const T *cb = colb + (c & 1) * 2 * KB;
             const T piv = rb[c];
             const bool bad = (piv == T(0)) || !finite_val(piv);
             if (bad && threadIdx.x == 0)
                 atomicMin((unsigned long long *)status, (unsigned long long)(s + (int64_t)J * KB + c));
             const T pinv = bad ? T(1) : T(1) / piv;
-            T urow[RX];
-#pragma unroll
-            for (int j = 0; j < RX; ++j) urow[j] = rb[tx + TX * j];
+            T lt[RY], lb[RY], ut[RX], ur[RX];
 #pragma unroll
             for (int i = 0; i < RY; ++i) {
                 const int a = ty + TY * i;
-                if (a <= c) continue;
-                const T l = cb[a] * pinv;
+                lt[i] = (a > c) ? cb[a] * pinv : T(0);
+                lb[i] = cb[KB + a] * pinv;
+            }
+#pragma unroll
+            for (int j = 0; j < RX; ++j) {
+                const int b = tx + TX * j;
+                ut[j] = (b > c) ? rb[b] : T(0);
+                ur[j] = rb[KB + b];
+            }
+#pragma unroll
+            for (int i = 0; i < RY; ++i)
 #pragma unroll
                 for (int j = 0; j < RX; ++j) {
-                    const int b = tx + TX * j;
-                    if (b > c) w[i][j] -= l * urow[j];
-                    else if (b == c) w[i][j] = l;
+                    tl[i][j] -= lt[i] * ut[j];
+                    tr[i][j] -= lt[i] * ur[j];
+                    bl[i][j] -= lb[i] * ut[j];
                 }
+            if (tx == c % TX) {  // this thread holds column c: store the multipliers
+                const int jc = c / TX;
+#pragma unroll
+                for (int j = 0; j < RX; ++j)
+                    if (j == jc)
+#pragma unroll
+                        for (int i = 0; i < RY; ++i) {
+                            if (ty + TY * i > c) tl[i][j] = lt[i];
+                            bl[i][j] = lb[i];
+                        }
             }
             if (c + 1 < KB) {
+                const int r1 = c + 1;
+                T *rn = rowb + (r1 & 1) * 2 * KB;
+                T *cn = colb + (r1 & 1) * 2 * KB;
+                if (ty == r1 % TY) {
+                    const int ir = r1 / TY;
 #pragma unroll
-                for (int i = 0; i < RY; ++i)
+                    for (int i = 0; i < RY; ++i)
+                        if (i == ir)
 #pragma unroll
-                    for (int j = 0; j < RX; ++j) {
-                        const int a = ty + TY * i, b = tx + TX * j;
-                        if (a == c + 1 && b >= c + 1) rn[b] = w[i][j];
-                        if (b == c + 1 && a > c + 1) cn[a] = w[i][j];
-                    }
+                            for (int j = 0; j < RX; ++j) {
+                                rn[tx + TX * j] = tl[i][j];
+                                rn[KB + tx + TX * j] = tr[i][j];
+                            }
+                }
+                if (tx == r1 % TX) {
+                    const int jr = r1 / TX;
+#pragma unroll
+                    for (int j = 0; j < RX; ++j)
+                        if (j == jr)
+#pragma unroll
+                            for (int i = 0; i < RY; ++i) {
+                                cn[ty + TY * i] = tl[i][j];
+                                cn[KB + ty + TY * i] = bl[i][j];
+                            }
+                }
             }
             __syncthreads();
         }
 
-        // write the factors of block J (and L_{J+1,J} of block J+1)
+        // factors of block J, and L_{J+1,J} into block J+1's tile
         const int64_t gJ = b0 + J;
-        T *lt = LT + gJ * KB * KB;
-        T *ut = UT + gJ * KB * KB;
+        T *lt_g = LT + gJ * KB * KB;
+        T *ut_g = UT + gJ * KB * KB;
 #pragma unroll
         for (int i = 0; i < RY; ++i)
 #pragma unroll
             for (int j = 0; j < RX; ++j) {
                 const int a = ty + TY * i, b = tx + TX * j;
-                const T v = w[i][j];
-                if (i < HY && j < HX) {
-                    if (a > b) lt[a * KB + b] = v;
-                    else {
-                        ut[a * KB + b] = v;
-                        if (J == 0) lt[a * KB + b] = T(0);  // L_{0,-1} does not exist
-                    }
-                } else if (i < HY) {  // U_{J,J+1}, lower triangular
-                    const int bb = b - KB;
-                    if (bb < a) ut[a * KB + bb] = v;
-                    else if (bb == a) DS[gJ * KB + a] = v;
-                } else if (j < HX) {  // L_{J+1,J}, upper triangular
-                    const int aa = a - KB;
-                    if (!last && b >= aa) LT[(gJ + 1) * KB * KB + aa * KB + b] = v;
+                if (a > b) lt_g[a * KB + b] = tl[i][j];
+                else {
+                    ut_g[a * KB + b] = tl[i][j];
+                    if (J == 0) lt_g[a * KB + b] = T(0);  // L_{0,-1} does not exist
+                }
+                if (b < a) ut_g[a * KB + b] = tr[i][j];
+                else if (b == a) DS[gJ * KB + a] = tr[i][j];
+                if (!last && b >= a) LT[(gJ + 1) * KB * KB + a * KB + b] = bl[i][j];
+                if (!last) {
+                    Ys[a * LDT + b] = bl[i][j];
+                    Zs[a * LDT + b] = tr[i][j];
                 }
             }
-        // S_{J+1} becomes the next top-left quadrant
+        if (last) break;
+        __syncthreads();
+        // S_{J+1} = A_{J+1,J+1} - L_{J+1,J} U_{J,J+1}; L_{J+1,J} is upper and
+        // U_{J,J+1} lower triangular, so only q >= max(a, b) contributes
+        T acc[RY][RX];
 #pragma unroll
-        for (int i = 0; i < HY; ++i)
+        for (int i = 0; i < RY; ++i)
 #pragma unroll
-            for (int j = 0; j < HX; ++j) w[i][j] = w[i + HY][j + HX];
+            for (int j = 0; j < RX; ++j) acc[i][j] = dg[(ty + TY * i) * KB + tx + TX * j];
+        const int q0 = (ty > tx) ? ty : tx;
+        for (int q = q0; q < KB; ++q) {
+            T yv[RY], zv[RX];
+#pragma unroll
+            for (int i = 0; i < RY; ++i) yv[i] = Ys[(ty + TY * i) * LDT + q];
+#pragma unroll
+            for (int j = 0; j < RX; ++j) zv[j] = Zs[q * LDT + tx + TX * j];
+#pragma unroll
+            for (int i = 0; i < RY; ++i)
+#pragma unroll
+                for (int j = 0; j < RX; ++j) acc[i][j] -= yv[i] * zv[j];
+        }
+#pragma unroll
+        for (int i = 0; i < RY; ++i)
+#pragma unroll
+            for (int j = 0; j < RX; ++j) tl[i][j] = acc[i][j];
         __syncthreads();
     }
 }
 
 // Per block: L^{-1} (unit lower), the unit upper inverse of D^{-1}U, D^{-1}
-// and D^{-1} U_{J,J+1}.  Both inverses are built right-looking: for pivot j
-// every entry below (L) or above (U) it is updated at once, one barrier per
-// j; half of the CTA works on L, the other half on U.
+// and D^{-1} U_{J,J+1}.  Each inverse is built column by column by plain
+// substitution; a thread owns columns c and KB-1-c (equal total work), so no
+// barrier is needed: every value a thread reads is its own earlier result or
+// input.  Results are kept transposed in the unused triangle of the same
+// shared tile.  A CTA of 128 threads serves 128/KB blocks (one warp, or part
+// of one, per triangular factor).
 template <typename T, int KB>
-__global__ void __launch_bounds__(Geo<KB>::NT)
+__global__ void __launch_bounds__(128)
     k_prep_inverse(T *__restrict__ LT, T *__restrict__ UT, const T *__restrict__ DS,
-                   T *__restrict__ DI) {
-    constexpr int NT = Geo<KB>::NT, LD = KB + 1, HALF = NT / 2;
+                   T *__restrict__ DI, int64_t NB) {
+    constexpr int LD = KB + 1, TPM = KB / 2, BPC = 128 / KB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *L = reinterpret_cast<T *>(smem_raw), *U = L + KB * LD, *XL = U + KB * LD, *XU = XL + KB * LD;
-    const int64_t blk = blockIdx.x;
-    T *lt = LT + blk * KB * KB;
-    T *ut = UT + blk * KB * KB;
-    for (int e = threadIdx.x; e < KB * KB; e += NT) {
-        const int a = e / KB, b = e % KB;
-        const T lv = lt[e], uv = ut[e];
-        L[a * LD + b] = lv;
-        U[a * LD + b] = uv;
-        XL[a * LD + b] = (a == b) ? T(1) : T(0);
-        XU[a * LD + b] = T(0);
+    T *tiles = reinterpret_cast<T *>(smem_raw);  // [BPC][2][KB x LD]
+    T *dinv = tiles + BPC * 2 * KB * LD;          // [BPC][KB]
+    const int64_t blk0 = (int64_t)blockIdx.x * BPC;
+    for (int e = threadIdx.x; e < BPC * KB * KB; e += 128) {
+        const int bb = e / (KB * KB), rem = e % (KB * KB), a = rem / KB, b = rem % KB;
+        const int64_t blk = blk0 + bb;
+        if (blk >= NB) continue;
+        T *Ls = tiles + (bb * 2 + 0) * KB * LD, *Us = tiles + (bb * 2 + 1) * KB * LD;
+        Ls[a * LD + b] = (a > b) ? LT[blk * KB * KB + rem] : T(0);
+        const T u = UT[blk * KB * KB + rem];
+        Us[a * LD + b] = (a <= b) ? u : T(0);
+        if (a == b) dinv[bb * KB + a] = T(1) / u;
     }
     __syncthreads();
-    if (threadIdx.x < KB) XU[threadIdx.x * LD + threadIdx.x] = T(1) / U[threadIdx.x * LD + threadIdx.x];
-    __syncthreads();
-    // step j: XL[a][c] -= L[a][j] XL[j][c] for a > j, c <= j  (X = L^{-1}, unit lower)
-    //         XU[a][c] -= U[a][j] XU[j][c] / U[a][a] for a < j', processed with j' = KB-1-j
-    //         (X = U^{-1}, back substitution by columns from the right)
-    const bool lower = threadIdx.x < HALF;
-    const int t = lower ? threadIdx.x : threadIdx.x - HALF;
-    for (int j = 0; j < KB; ++j) {
-        if (lower) {
-            const int rows = KB - 1 - j, cols = j + 1;
-            for (int e = t; e < rows * cols; e += HALF) {
-                const int a = j + 1 + e / cols, c = e % cols;
-                XL[a * LD + c] -= L[a * LD + j] * XL[j * LD + c];
-            }
-        } else {
-            const int jj = KB - 1 - j;           // finished row of U^{-1}
-            const int rows = jj, cols = KB - jj;
-            for (int e = t; e < rows * cols; e += HALF) {
-                const int a = e / cols, c = jj + e % cols;
-                XU[a * LD + c] -= U[a * LD + jj] * XU[jj * LD + c];
+    const int bb = threadIdx.x / (2 * TPM), role = (threadIdx.x / TPM) & 1, t = threadIdx.x % TPM;
+    if (blk0 + bb < NB) {
+        T *S = tiles + (bb * 2 + role) * KB * LD;
+        const T *dv = dinv + bb * KB;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int col = h ? KB - 1 - t : t;
+            if (role == 0) {
+                // X = L^{-1}: X[a][col] = -(L[a][col] + sum_{col<j<a} L[a][j] X[j][col]),
+                // stored at S[col][a] (upper triangle)
+                for (int a = col + 1; a < KB; ++a) {
+                    T s0 = S[a * LD + col], s1 = T(0);
+                    int j = col + 1;
+                    for (; j + 1 < a; j += 2) {
+                        s0 += S[a * LD + j] * S[col * LD + j];
+                        s1 += S[a * LD + j + 1] * S[col * LD + j + 1];
+                    }
+                    if (j < a) s0 += S[a * LD + j] * S[col * LD + j];
+                    S[col * LD + a] = -(s0 + s1);
+                }
+            } else {
+                // X = U^{-1}: X[col][col] = 1/u, X[a][col] = -(sum_{a<j<=col} U[a][j] X[j][col]) / U[a][a],
+                // stored at S[col][a] (lower triangle); the diagonal entry lives in dinv
+                for (int a = col - 1; a >= 0; --a) {
+                    T s0 = S[a * LD + col] * dv[col], s1 = T(0);
+                    int j = a + 1;
+                    for (; j + 1 < col; j += 2) {
+                        s0 += S[a * LD + j] * S[col * LD + j];
+                        s1 += S[a * LD + j + 1] * S[col * LD + j + 1];
+                    }
+                    if (j < col) s0 += S[a * LD + j] * S[col * LD + j];
+                    S[col * LD + a] = -(s0 + s1) * dv[a];
+                }
             }
         }
-        __syncthreads();
-        if (!lower) {
-            // row KB-2-j of U^{-1} is complete once all pivots to its right are
-            // applied; scale it by 1 / u_aa (the diagonal entry was set above)
-            const int a = KB - 2 - j;
-            if (a >= 0)
-                for (int c = a + 1 + t; c < KB; c += HALF) XU[a * LD + c] /= U[a * LD + a];
-        }
-        __syncthreads();
     }
-    for (int e = threadIdx.x; e < KB * KB; e += NT) {
-        const int a = e / KB, b = e % KB;
+    __syncthreads();
+    for (int e = threadIdx.x; e < BPC * KB * KB; e += 128) {
+        const int bb2 = e / (KB * KB), rem = e % (KB * KB), a = rem / KB, b = rem % KB;
+        const int64_t blk = blk0 + bb2;
+        if (blk >= NB) continue;
+        const T *Ls = tiles + (bb2 * 2 + 0) * KB * LD, *Us = tiles + (bb2 * 2 + 1) * KB * LD;
+        const T *dv = dinv + bb2 * KB;
         if (a > b) {
-            lt[e] = XL[a * LD + b];                                  // L^{-1}
-            ut[e] = U[a * LD + b] / U[a * LD + a];                   // D^{-1} U_{J,J+1}
+            LT[blk * KB * KB + rem] = Ls[b * LD + a];                        // L^{-1}
+            UT[blk * KB * KB + rem] = UT[blk * KB * KB + rem] * dv[a];       // D^{-1} U_{J,J+1}
         } else if (a < b) {
-            ut[e] = XU[a * LD + b] * U[b * LD + b];                  // (D^{-1}U)^{-1}
+            UT[blk * KB * KB + rem] = Us[b * LD + a] / dv[b];                // (D^{-1}U)^{-1} = U^{-1} D
         } else {
-            ut[e] = DS[blk * KB + a] / U[a * LD + a];                // diagonal of D^{-1}U_{J,J+1}
+            UT[blk * KB * KB + rem] = DS[blk * KB + a] * dv[a];              // diagonal of D^{-1}U_{J,J+1}
+            DI[blk * KB + a] = dv[a];
         }
     }
-    if (threadIdx.x < KB) DI[blk * KB + threadIdx.x] = T(1) / U[threadIdx.x * LD + threadIdx.x];
 }
 
 template <typename T, int KB>
 static bool lu_impl(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
-    const size_t smem = (4 * KB * KB + 4 * Geo<KB>::W) * sizeof(T);
+    const size_t smem = (4 * KB * KB + 2 * KB * (KB + 1) + 8 * KB) * sizeof(T);
     auto kern = k_band_lu<T, KB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_LU, [&] {
@@ -281,12 +353,13 @@ static bool lu_impl(Ctx *c) {
 
 template <typename T, int KB>
 static bool prep_impl(Ctx *c) {
-    const size_t smem = 4 * KB * (KB + 1) * sizeof(T);
+    constexpr int BPC = 128 / KB;
+    const size_t smem = (BPC * 2 * KB * (KB + 1) + BPC * KB) * sizeof(T);
     auto kern = k_prep_inverse<T, KB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned grid = (unsigned)((c->NB + BPC - 1) / BPC);
     return launch(c, KID_PREP, [&] {
-        kern<<<(unsigned)c->NB, Geo<KB>::NT, smem, c->stream>>>(
-            (T *)c->LT, (T *)c->UT, (const T *)c->DS, (T *)c->DI);
+        kern<<<grid, 128, smem, c->stream>>>((T *)c->LT, (T *)c->UT, (const T *)c->DS, (T *)c->DI, c->NB);
     });
 }
 

@@ -60,7 +60,7 @@ __global__ void k_spike_rhs(const double *__restrict__ band, int64_t ld, int k, 
         }
     }
     if (part > 0) {  // left spike: rows 0..k-1 hold C_i
-        const int wc = coupling ? r : KB;  // first column of the W panel
+        const int wc = m / 2;  // first column of the W panel
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
             const int a = e / k, b = e % k;
             if (!coupling) {
@@ -83,73 +83,157 @@ __global__ void k_spike_rhs(const double *__restrict__ band, int64_t ld, int k, 
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, int KB>
-__global__ void __launch_bounds__(Geo<KB>::NT)
-    k_sweep(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI, Parts P,
-            T *__restrict__ X, int m) {
-    constexpr int NT = Geo<KB>::NT, LDS = KB + 1;
+// X <- A_i^{-1} X for the spike panel of every partition (one CTA each).
+// Panel columns [0, M/2) hold the right spike T_i, [M/2, M) the left spike W_i.
+// The right spike's right-hand side is zero above block Jv0 = (n_i - k)/KB, so
+// its forward chain starts there; partition 0 has no W_i and partition p-1 no
+// T_i, so those halves are skipped entirely.  The packed factor tile of each
+// step is unpacked into two triangular tiles with explicit zeros and the unit
+// diagonal, so the register-tiled products need no masks.
+template <typename T, int KB, int MT, int CG>
+__global__ void __launch_bounds__((KB / 4) * CG)
+    k_sweep(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI, Parts P, int k,
+            T *__restrict__ X) {
+    // MT columns per thread, CG column groups: panel width M = MT * CG
+    constexpr int NT = (KB / 4) * CG, M = MT * CG, LDA = KB + 1, HALFM = M / 2;
+    constexpr int LDM = M + 16 / (int)sizeof(T);  // padded panel rows in shared memory
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Ls = reinterpret_cast<T *>(smem_raw);  // KB x LDS
-    T *dsm = Ls + KB * LDS;                   // KB
-    T *Tt = dsm + KB;                         // KB x m
-    T *Yp = Tt + KB * m;                      // KB x m
+    T *A1 = reinterpret_cast<T *>(smem_raw);  // off-diagonal factor block
+    T *A2 = A1 + KB * LDA;                    // inverse of the diagonal factor
+    T *Tt = A2 + KB * LDA;                    // KB x LDM
+    T *Yp = Tt + KB * LDM;                    // KB x LDM
+    T *dsm = Yp + KB * LDM;                   // KB
     const int part = blockIdx.x;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int64_t b0 = P.boff[part];
     const int nb = (int)(P.boff[part + 1] - b0);
-    const int pm = KB * m;
+    const bool hasV = part < P.p - 1, hasW = part > 0;
+    const int Jv0 = (int)((ni - k) / KB);
+    int ty, tx;
+    PanelMap<KB, CG>::get(threadIdx.x, ty, tx);
+    const int a0 = 4 * ty, c0 = MT * tx;
+    const bool isV = c0 < HALFM;
+    T acc[4][MT];
+
     for (int J = 0; J < nb; ++J) {
         const int64_t g = b0 + J;
-        load_tile<T, KB>(LT + g * KB * KB, Ls, LDS);
-        for (int e = threadIdx.x; e < pm; e += NT) Tt[e] = X[g * pm + e];
+        const T *tile = LT + g * KB * KB;
+        for (int e = threadIdx.x; e < KB * KB; e += NT) {
+            const int a = e / KB, b = e % KB;
+            const T v = tile[e];
+            A1[a * LDA + b] = (a <= b) ? v : T(0);                        // L_{J,J-1}
+            A2[a * LDA + b] = (a > b) ? v : ((a == b) ? T(1) : T(0));     // L_JJ^{-1}
+        }
+        const bool active = isV ? (hasV && J >= Jv0) : hasW;
+        const bool first = (J == 0) || (isV && J == Jv0);
+        T *xg = X + g * KB * M;
+        if (active)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ld_row<T, MT>(xg + (a0 + i) * M + c0, acc[i]);
         __syncthreads();
-        fwd_step<T, KB, Split::COLS>(Ls, LDS, Tt, Yp, m, m, J == 0);
-        for (int e = threadIdx.x; e < pm; e += NT) X[g * pm + e] = Yp[e];
+        if (active) {
+            if (!first) panel_mac<T, MT, true>(acc, A1, LDA, Yp, LDM, a0, c0, a0, KB);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) st_row<T, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < MT; ++j) acc[i][j] = T(0);
+            panel_mac<T, MT, false>(acc, A2, LDA, Tt, LDM, a0, c0, 0, a0 + 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                st_row<T, MT>(Yp + (a0 + i) * LDM + c0, acc[i]);
+                st_row<T, MT>(xg + (a0 + i) * M + c0, acc[i]);
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int J = nb - 1; J >= 0; --J) {
         const int64_t g = b0 + J;
-        load_tile<T, KB>(UT + g * KB * KB, Ls, LDS);
+        const T *tile = UT + g * KB * KB;
+        for (int e = threadIdx.x; e < KB * KB; e += NT) {
+            const int a = e / KB, b = e % KB;
+            const T v = tile[e];
+            A1[a * LDA + b] = (a >= b) ? v : T(0);                        // D^{-1} U_{J,J+1}
+            A2[a * LDA + b] = (a < b) ? v : ((a == b) ? T(1) : T(0));     // (D^{-1} U_JJ)^{-1}
+        }
         if (threadIdx.x < KB) dsm[threadIdx.x] = DI[g * KB + threadIdx.x];
-        for (int e = threadIdx.x; e < pm; e += NT) Tt[e] = X[g * pm + e];
+        const bool active = isV ? hasV : hasW;
+        T *xg = X + g * KB * M;
+        if (active)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ld_row<T, MT>(xg + (a0 + i) * M + c0, acc[i]);
         __syncthreads();
-        bwd_step<T, KB, Split::COLS>(Ls, LDS, dsm, Tt, Yp, m, m, J == nb - 1);
-        for (int e = threadIdx.x; e < pm; e += NT) X[g * pm + e] = Yp[e];
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < MT; ++j) acc[i][j] *= dsm[a0 + i];
+            if (J < nb - 1) panel_mac<T, MT, true>(acc, A1, LDA, Yp, LDM, a0, c0, 0, a0 + 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) st_row<T, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < MT; ++j) acc[i][j] = T(0);
+            panel_mac<T, MT, false>(acc, A2, LDA, Tt, LDM, a0, c0, a0, KB);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                st_row<T, MT>(Yp + (a0 + i) * LDM + c0, acc[i]);
+                st_row<T, MT>(xg + (a0 + i) * M + c0, acc[i]);
+            }
+        }
+        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
 // Gram matrices of the two spike panels, partial sums over a chunk of blocks.
+// Thread tile: 4 rows x GC columns of one Gram matrix (GC = KB/8).
 template <typename T, int KB>
-__global__ void __launch_bounds__(Geo<KB>::NT)
+__global__ void __launch_bounds__(4 * KB)
     k_gram(const T *__restrict__ X, Parts P, int chunks, double *__restrict__ Gpart) {
-    constexpr int NT = Geo<KB>::NT, M = 2 * KB, PER = (2 * KB * KB) / NT;
+    constexpr int NT = 4 * KB, M = 2 * KB, GC = (KB >= 8) ? KB / 8 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);  // KB x M
     const int part = blockIdx.y, ch = blockIdx.x;
     const int64_t b0 = P.boff[part];
     const int nb = (int)(P.boff[part + 1] - b0);
     const int J0 = (int)((int64_t)ch * nb / chunks), J1 = (int)((int64_t)(ch + 1) * nb / chunks);
-    T acc[PER];
+    const int gsel = threadIdx.x / (2 * KB), rem = threadIdx.x % (2 * KB);
+    const int a0 = 4 * (rem / 8), b0c = GC * (rem % 8);
+    const int off = gsel * KB;
+    T acc[4][GC];
 #pragma unroll
-    for (int t = 0; t < PER; ++t) acc[t] = T(0);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < GC; ++j) acc[i][j] = T(0);
     for (int J = J0; J < J1; ++J) {
         const T *src = X + (b0 + J) * (int64_t)KB * M;
         for (int e = threadIdx.x; e < KB * M; e += NT) Xs[e] = src[e];
         __syncthreads();
+        for (int q = 0; q < KB; ++q) {
+            T av[4], bv[GC];
+            ld_row<T, 4>(Xs + q * M + off + a0, av);
+            ld_row<T, GC>(Xs + q * M + off + b0c, bv);
 #pragma unroll
-        for (int t = 0; t < PER; ++t) {
-            const int e = threadIdx.x + NT * t;
-            const int gsel = e / (KB * KB), rem = e % (KB * KB);
-            const int a = rem / KB, b = rem % KB;
-            T sacc = T(0);
-            for (int q = 0; q < KB; ++q) sacc += Xs[q * M + gsel * KB + a] * Xs[q * M + gsel * KB + b];
-            acc[t] += sacc;
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < GC; ++jj) acc[i][jj] += av[i] * bv[jj];
         }
         __syncthreads();
     }
-    double *dst = Gpart + ((int64_t)part * chunks + ch) * 2 * KB * KB;
+    double *dst = Gpart + (((int64_t)part * chunks + ch) * 2 + gsel) * KB * KB;
 #pragma unroll
-    for (int t = 0; t < PER; ++t) dst[threadIdx.x + NT * t] = (double)acc[t];
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < GC; ++jj) dst[(a0 + i) * KB + b0c + jj] = (double)acc[i][jj];
 }
 
 __global__ void k_gram_reduce(const double *__restrict__ Gpart, int chunks, int64_t per_part,
@@ -306,38 +390,69 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
 }
 
 // ---------------------------------------------------------------------------
-// u-factors: SPIKE mode u = X V_r (X panel columns times P^T); COUPLING mode
-// the solved columns are u already.  Ucat row = [u_T (r) | u_W (r)].
-template <typename T, int KB>
-__global__ void __launch_bounds__(Geo<KB>::NT)
+// u-factors: SPIKE mode u = X V_r (panel columns times P^T); COUPLING mode the
+// solved columns are u already.  Ucat row = [u_T (r) | u_W (r)].  One CTA per
+// (chunk of blocks, partition); the projections are staged once.  Thread
+// tile: 4 rows x UC columns of the KB x 2r output block.
+template <typename T, int KB, int UC>
+__global__ void __launch_bounds__(4 * KB)
     k_make_u(const T *__restrict__ X, int m, const T *__restrict__ PQ, Parts P, int r, int coupling,
-             T *__restrict__ Ucat) {
-    constexpr int NT = Geo<KB>::NT;
+             int chunks, T *__restrict__ Ucat) {
+    constexpr int NT = 4 * KB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Xs = reinterpret_cast<T *>(smem_raw);  // KB x m
-    T *Ps = Xs + KB * m;                      // 2 x r x KB
-    const int64_t g = blockIdx.x;
-    const int part = part_of_block(P, g);
+    T *Ps = Xs + KB * m;                      // KB x 2r (transposed projections)
+    const int part = blockIdx.y, ch = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
-    const int J = (int)(g - P.boff[part]);
-    for (int e = threadIdx.x; e < KB * m; e += NT) Xs[e] = X[g * KB * m + e];
+    const int64_t b0 = P.boff[part];
+    const int nb = (int)(P.boff[part + 1] - b0);
+    const int J0 = (int)((int64_t)ch * nb / chunks), J1 = (int)((int64_t)(ch + 1) * nb / chunks);
+    const int n2 = 2 * r, half = m / 2;
     if (!coupling)
-        for (int e = threadIdx.x; e < 2 * r * KB; e += NT) Ps[e] = PQ[(int64_t)part * 2 * r * KB + e];
-    __syncthreads();
-    const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
-    const int64_t row = (int64_t)J * KB + a;
-    if (row >= ni) return;
-    T *dst = Ucat + (s + row) * 2 * r;
-    for (int c = q; c < 2 * r; c += 4) {
-        const int gsel = c / r, cc = c % r;
-        T acc;
-        if (coupling) {
-            acc = Xs[a * m + c];
-        } else {
-            acc = T(0);
-            for (int j = 0; j < KB; ++j) acc += Xs[a * m + gsel * KB + j] * Ps[(gsel * r + cc) * KB + j];
+        for (int e = threadIdx.x; e < n2 * KB; e += NT)
+            Ps[(e % KB) * n2 + e / KB] = PQ[(int64_t)part * n2 * KB + e];
+    const int a0 = 4 * (threadIdx.x / 16), cb = UC * (threadIdx.x % 16);
+    for (int J = J0; J < J1; ++J) {
+        const T *src = X + (b0 + J) * (int64_t)KB * m;
+        for (int e = threadIdx.x; e < KB * m; e += NT) Xs[e] = src[e];
+        __syncthreads();
+        T acc[4][UC];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int u = 0; u < UC; ++u) {
+                const int col = cb + u;
+                const int xcol = (col < r) ? col : half + (col - r);   // coupling: panel column
+                acc[i][u] = (coupling && col < n2) ? Xs[(a0 + i) * m + xcol] : T(0);
+            }
+        if (!coupling) {
+            for (int j = 0; j < KB; ++j) {
+                T xv[4], xw[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    xv[i] = Xs[(a0 + i) * m + j];
+                    xw[i] = Xs[(a0 + i) * m + KB + j];
+                }
+#pragma unroll
+                for (int u = 0; u < UC; ++u) {
+                    const int col = cb + u;
+                    if (col < n2) {
+                        const T pv = Ps[j * n2 + col];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) acc[i][u] += ((col < r) ? xv[i] : xw[i]) * pv;
+                    }
+                }
+            }
         }
-        dst[c] = acc;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t row = (int64_t)J * KB + a0 + i;
+            if (row < ni)
+#pragma unroll
+                for (int u = 0; u < UC; ++u)
+                    if (cb + u < n2) Ucat[(s + row) * n2 + cb + u] = acc[i][u];
+        }
+        __syncthreads();
     }
 }
 
@@ -356,16 +471,30 @@ static bool spike_rhs_impl(Ctx *c) {
     });
 }
 
-template <typename T, int KB>
-static bool sweep_impl(Ctx *c) {
+template <typename T, int KB, int MT, int CG>
+static bool sweep_mt(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
-    const size_t smem = (KB * (KB + 1) + KB + 2 * KB * c->m) * sizeof(T);
-    auto kern = k_sweep<T, KB>;
+    constexpr int M = MT * CG, LDM = M + 16 / (int)sizeof(T), NT = (KB / 4) * CG;
+    const size_t smem = (2 * KB * (KB + 1) + 2 * KB * LDM + KB) * sizeof(T);
+    auto kern = k_sweep<T, KB, MT, CG>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_SWEEP, [&] {
-        kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT,
-                                                     (const T *)c->DI, P, (T *)c->X, c->m);
+        kern<<<c->p, NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT, (const T *)c->DI, P, c->k,
+                                            (T *)c->X);
     });
+}
+
+template <typename T, int KB>
+static bool sweep_impl(Ctx *c) {
+    // wide panels of the widest block use 32 column groups (8 * KB threads)
+    switch (c->m / 16) {
+        case 1: return sweep_mt<T, KB, 1, 16>(c);
+        case 2: return sweep_mt<T, KB, 2, 16>(c);
+        case 4: return sweep_mt<T, KB, 4, 16>(c);
+        default:
+            if constexpr (KB == 64) return sweep_mt<T, KB, 4, 32>(c);
+            else return sweep_mt<T, KB, 8, 16>(c);
+    }
 }
 
 template <typename T, int KB>
@@ -405,17 +534,26 @@ static bool jacobi_impl(Ctx *c) {
     });
 }
 
-template <typename T, int KB>
-static bool make_u_impl(Ctx *c) {
+template <typename T, int KB, int UC>
+static bool make_u_uc(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
     const size_t smem = (KB * c->m + 2 * c->r * KB) * sizeof(T);
-    auto kern = k_make_u<T, KB>;
+    auto kern = k_make_u<T, KB, UC>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(c->gram_chunks, c->p);
     return launch(c, KID_MAKE_U, [&] {
-        kern<<<(unsigned)c->NB, Geo<KB>::NT, smem, c->stream>>>(
-            (const T *)c->X, c->m, (const T *)c->PQ, P, c->r,
-            c->opt.compress == LRSPIKE_COMPRESS_COUPLING, (T *)c->Ucat);
+        kern<<<grid, 4 * KB, smem, c->stream>>>((const T *)c->X, c->m, (const T *)c->PQ, P, c->r,
+                                                c->opt.compress == LRSPIKE_COMPRESS_COUPLING, c->gram_chunks,
+                                                (T *)c->Ucat);
     });
+}
+
+template <typename T, int KB>
+static bool make_u_impl(Ctx *c) {
+    const int uc = (2 * c->r + 15) / 16;
+    if (uc <= 1) return make_u_uc<T, KB, 1>(c);
+    if (uc <= 2) return make_u_uc<T, KB, 2>(c);
+    return make_u_uc<T, KB, 4>(c);
 }
 
 #define LRS_KB_DISPATCH(FN)                                \

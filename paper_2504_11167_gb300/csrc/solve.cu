@@ -122,49 +122,64 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
                             const double *__restrict__ rin, const double *__restrict__ inv,
                             int nrhs, T *__restrict__ Yv, T *__restrict__ Gv, double *__restrict__ psi,
                             unsigned char *smem_raw) {
-    constexpr int NT = Geo<KB>::NT, LDS = KB + 1;
-    T *Ls = reinterpret_cast<T *>(smem_raw);
-    T *dsm = Ls + KB * LDS;
-    T *Tt = dsm + KB;
+    constexpr int NT = Geo<KB>::NT, LDP = KB + 16 / (int)sizeof(T);
+    T *tb = reinterpret_cast<T *>(smem_raw);  // [2][KB x LDP] staged factor tiles
+    T *db = tb + 2 * KB * LDP;                // [2][KB] staged D^{-1}
+    T *Tt = db + 2 * KB;
     T *Yp = Tt + KB * nrhs;
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int64_t b0 = P.boff[part];
     const int nb = (int)(P.boff[part + 1] - b0);
-    const int pm = KB * nrhs;
-    for (int J = 0; J < nb; ++J) {
-        load_tile<T, KB>(LT + (b0 + J) * KB * KB, Ls, LDS);
-        for (int e = threadIdx.x; e < pm; e += NT) {
-            const int a = e / nrhs, c = e % nrhs;
-            const int64_t row = (int64_t)J * KB + a;
-            Tt[e] = (row < ni) ? (T)(rin[c * n + s + row] * inv[c]) : T(0);
+    const int pm = KB * nrhs, steps = 2 * nb;
+    // step t < nb: forward block t with LT; step t >= nb: backward block 2nb-1-t with UT, DI
+    auto stage = [&](int t) {
+        const int buf = t & 1;
+        if (t < nb) stage_tile<T, KB>(LT + (b0 + t) * KB * KB, tb + buf * KB * LDP, nullptr, nullptr);
+        else {
+            const int64_t g = b0 + (steps - 1 - t);
+            stage_tile<T, KB>(UT + g * KB * KB, tb + buf * KB * LDP, DI + g * KB, db + buf * KB);
+        }
+    };
+    stage(0);
+    cp_async_commit();
+    for (int t = 0; t < steps; ++t) {
+        if (t + 1 < steps) stage(t + 1);
+        cp_async_commit();
+        const T *tile = tb + (t & 1) * KB * LDP;
+        if (t < nb) {
+            const int J = t;
+            for (int e = threadIdx.x; e < pm; e += NT) {
+                const int a = e / nrhs, c = e % nrhs;
+                const int64_t row = (int64_t)J * KB + a;
+                Tt[e] = (row < ni) ? (T)(rin[c * n + s + row] * inv[c]) : T(0);
+            }
+            cp_async_wait1();
+            __syncthreads();
+            fwd_step<T, KB, S>(tile, LDP, Tt, Yp, nrhs, nrhs, J == 0);
+            for (int e = threadIdx.x; e < pm; e += NT) {
+                const int a = e / nrhs, c = e % nrhs;
+                const int64_t row = (int64_t)J * KB + a;
+                if (row < ni) Yv[c * n + s + row] = Yp[e];
+            }
+        } else {
+            const int J = steps - 1 - t;
+            for (int e = threadIdx.x; e < pm; e += NT) {
+                const int a = e / nrhs, c = e % nrhs;
+                const int64_t row = (int64_t)J * KB + a;
+                Tt[e] = (row < ni) ? Yv[c * n + s + row] : T(0);
+            }
+            cp_async_wait1();
+            __syncthreads();
+            bwd_step<T, KB, S>(tile, LDP, db + (t & 1) * KB, Tt, Yp, nrhs, nrhs, J == nb - 1);
+            for (int e = threadIdx.x; e < pm; e += NT) {
+                const int a = e / nrhs, c = e % nrhs;
+                const int64_t row = (int64_t)J * KB + a;
+                if (row < ni) Gv[c * n + s + row] = Yp[e];
+            }
         }
         __syncthreads();
-        fwd_step<T, KB, S>(Ls, LDS, Tt, Yp, nrhs, nrhs, J == 0);
-        for (int e = threadIdx.x; e < pm; e += NT) {
-            const int a = e / nrhs, c = e % nrhs;
-            const int64_t row = (int64_t)J * KB + a;
-            if (row < ni) Yv[c * n + s + row] = Yp[e];
-        }
     }
-    __syncthreads();
-    for (int J = nb - 1; J >= 0; --J) {
-        load_tile<T, KB>(UT + (b0 + J) * KB * KB, Ls, LDS);
-        if (threadIdx.x < KB) dsm[threadIdx.x] = DI[(b0 + J) * KB + threadIdx.x];
-        for (int e = threadIdx.x; e < pm; e += NT) {
-            const int a = e / nrhs, c = e % nrhs;
-            const int64_t row = (int64_t)J * KB + a;
-            Tt[e] = (row < ni) ? Yv[c * n + s + row] : T(0);
-        }
-        __syncthreads();
-        bwd_step<T, KB, S>(Ls, LDS, dsm, Tt, Yp, nrhs, nrhs, J == nb - 1);
-        for (int e = threadIdx.x; e < pm; e += NT) {
-            const int a = e / nrhs, c = e % nrhs;
-            const int64_t row = (int64_t)J * KB + a;
-            if (row < ni) Gv[c * n + s + row] = Yp[e];
-        }
-    }
-    __syncthreads();
     if (r == 0) return;
     // psi_{part-1}[0:r] = P_{part-1} g_t ;  psi_part[r:2r] = Q_{part+1} g_b
     const int n2 = 2 * r;
@@ -220,7 +235,17 @@ __global__ void __launch_bounds__(RBS)
     const int64_t gi = s + row;
     for (int c = 0; c < nrhs; ++c) {
         T d = Gv[c * n + gi];
-        for (int j = 0; j < n2; ++j) d -= Ucat[gi * n2 + j] * (T)zs[j * nrhs + c];
+        const T *u = Ucat + gi * n2;
+        int j = 0;
+        if constexpr (sizeof(T) == 4) {
+            if ((n2 & 3) == 0)
+                for (; j < n2; j += 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(u + j);
+                    d -= v.x * (T)zs[j * nrhs + c] + v.y * (T)zs[(j + 1) * nrhs + c] +
+                         v.z * (T)zs[(j + 2) * nrhs + c] + v.w * (T)zs[(j + 3) * nrhs + c];
+                }
+        }
+        for (; j < n2; ++j) d -= u[j] * (T)zs[j * nrhs + c];
         const double upd = nrm[c] * (double)d;
         x[c * ld + gi] = accumulate ? x[c * ld + gi] + upd : upd;
     }
@@ -404,7 +429,7 @@ bool run_norms(Ctx *c, const double *v, int64_t ld, int nrhs, double *out) {
 template <typename T, int KB>
 static bool dstage_impl(Ctx *c, const double *rin, int nrhs) {
     Parts P{c->off_d, c->boff_d, c->p};
-    const size_t smem = (KB * (KB + 1) + KB + 2 * KB * nrhs) * sizeof(T);
+    const size_t smem = (2 * KB * (KB + 16 / sizeof(T)) + 2 * KB + 2 * KB * nrhs) * sizeof(T);
     auto kern = k_dstage<T, KB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_DSTAGE, [&] {

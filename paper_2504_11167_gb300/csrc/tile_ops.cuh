@@ -177,6 +177,101 @@ __device__ __forceinline__ void bwdT_step(const T *__restrict__ Lnext, const T *
     __syncthreads();
 }
 
+// Thread map for register-tiled panel products on KB x (CG*MT) panels with
+// (KB/4)*CG threads: thread (ty, tx) owns rows 4ty..4ty+3 and columns
+// MT*tx..MT*tx+MT-1.  A warp covers a band of (at most) 16 rows and one half
+// of the columns, so a triangular loop bound is uniform per warp band and a
+// whole half of the panel (e.g. zero spike columns) can be skipped per warp.
+template <int KB, int CG = 16> struct PanelMap {
+    static constexpr int LRG = (KB >= 16) ? 4 : 2;  // row groups per warp
+    static constexpr int CPW = 32 / LRG;            // column groups per warp
+    static constexpr int WR = KB / (4 * LRG);       // warps along the rows
+    __device__ static __forceinline__ void get(int t, int &ty, int &tx) {
+        const int w = t >> 5, l = t & 31;
+        ty = (w % WR) * LRG + (l % LRG);
+        tx = (w / WR) * CPW + (l / LRG);
+    }
+};
+
+// Loads MT consecutive values (16-byte vector loads where the type allows).
+template <typename T, int MT>
+__device__ __forceinline__ void ld_row(const T *p, T (&v)[MT]) {
+    if constexpr (sizeof(T) == 4 && MT % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < MT; j += 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(p + j);
+            v[j] = f.x; v[j + 1] = f.y; v[j + 2] = f.z; v[j + 3] = f.w;
+        }
+    } else if constexpr (sizeof(T) == 8 && MT % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < MT; j += 2) {
+            const double2 d = *reinterpret_cast<const double2 *>(p + j);
+            v[j] = d.x; v[j + 1] = d.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < MT; ++j) v[j] = p[j];
+    }
+}
+
+template <typename T, int MT>
+__device__ __forceinline__ void st_row(T *p, const T (&v)[MT]) {
+    if constexpr (sizeof(T) == 4 && MT % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < MT; j += 4) *reinterpret_cast<float4 *>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    } else if constexpr (sizeof(T) == 8 && MT % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < MT; j += 2) *reinterpret_cast<double2 *>(p + j) = make_double2(v[j], v[j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < MT; ++j) p[j] = v[j];
+    }
+}
+
+// acc[i][j] (+/-)= sum_{q0 <= q < q1} A[(a0+i)*LDA + q] * B[q*LDB + c0 + j]
+template <typename T, int MT, bool SUB>
+__device__ __forceinline__ void panel_mac(T (&acc)[4][MT], const T *__restrict__ A, int LDA,
+                                          const T *__restrict__ B, int LDB, int a0, int c0, int q0,
+                                          int q1) {
+#pragma unroll 4
+    for (int q = q0; q < q1; ++q) {
+        T av[4], bv[MT];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = A[(a0 + i) * LDA + q];
+        ld_row<T, MT>(B + q * LDB + c0, bv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                if (SUB) acc[i][j] -= av[i] * bv[j];
+                else acc[i][j] += av[i] * bv[j];
+            }
+    }
+}
+
+// Asynchronous global->shared copies (16-byte cp.async), used to prefetch the
+// next factor tile of a chain while the current block step computes.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Stages a KB x KB tile into shared memory rows of stride LDP = KB + 16/sizeof(T)
+// (one 16-byte pad per row), plus optionally KB diagonal values.
+template <typename T, int KB>
+__device__ __forceinline__ void stage_tile(const T *__restrict__ src, T *dst, const T *__restrict__ dsrc,
+                                           T *ddst) {
+    constexpr int CH = 16 / sizeof(T), CPR = KB / CH, LDP = KB + CH;
+    for (int e = threadIdx.x; e < KB * CPR; e += Geo<KB>::NT) {
+        const int row = e / CPR, ch = e % CPR;
+        cp_async16(dst + row * LDP + ch * CH, src + row * KB + ch * CH);
+    }
+    if (dsrc)
+        for (int e = threadIdx.x; e < CPR; e += Geo<KB>::NT) cp_async16(ddst + e * CH, dsrc + e * CH);
+}
+
 // Copies a KB x KB row-major tile from global memory into shared memory with
 // row stride LDS (KB + 1 avoids bank conflicts on column reads).
 template <typename T, int KB>
