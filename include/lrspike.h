@@ -159,6 +159,38 @@ lrspike_status lrspike_profile_reset(lrspike_handle h);
  * solved).  Used by the tests to compare the compression with the oracle. */
 lrspike_status lrspike_get_reduced(lrspike_handle h, double *sigma, double *R);
 
+/* ---- allocation-free band residual ----------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code running inside a latency-critical
+ * serving loop, where a cudaMalloc would synchronise the whole device and
+ * stall its other streams, or a host framework that owns all device memory
+ * through its own pool and forbids stray allocations.  It needs no handle
+ * (creating one allocates) and calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * Computes r = f - A x in FP64 from the band (layout as above) and the 2-norm
+ * of every column of r, with the same kernel and the same deterministic
+ * reduction order that lrspike_solve uses for its convergence test.
+ *   band  (2k+1) x ld_band, device; f, x: n x nrhs column-major with leading
+ *   dimension ld >= n, device; r: device, n x nrhs column-major with leading
+ *   dimension n (column q at r + q*n); norms: device, nrhs doubles.
+ *   1 <= nrhs <= 16.  Enqueued on cuda_stream (NULL = legacy default stream);
+ *   the call returns without waiting for the GPU.
+ * Its scratch (one partial sum per 256 rows and column, and a counter) is a
+ * fixed static device array of LRSPIKE_NOALLOC_MAX_PARTIALS doubles that every
+ * GPU loading the library holds until the process exits: sizes with
+ * ceil(n/256) * nrhs > LRSPIKE_NOALLOC_MAX_PARTIALS are rejected with
+ * INVALID_ARG.  The first call on each device looks up that device's address of
+ * the array (with the device current); make that first call before any stream
+ * capture.  All calls on a device share the array, so calls that overlap on the
+ * GPU (other streams or host threads) race and must be serialised by the
+ * caller.  Errors (INVALID_ARG for NULL, host or oversized arguments, CUDA) are
+ * described by lrspike_last_error(NULL). */
+#define LRSPIKE_NOALLOC_MAX_PARTIALS 65536
+lrspike_status lrspike_residual_noalloc(const double *band, int64_t ld_band, int64_t n, int32_t k,
+                                        const double *f, const double *x, double *r, int32_t nrhs,
+                                        int64_t ld, double *norms, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

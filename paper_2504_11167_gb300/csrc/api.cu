@@ -71,6 +71,8 @@ static thread_local std::string g_err;
 static const int64_t kNoStatus = INT64_MAX;
 static const int64_t kReducedSingular = INT64_MAX - 1;
 
+void lrs::set_handleless_error(const std::string &msg) { g_err = msg; }
+
 static lrspike_status fail(Ctx *c, lrspike_status st, const std::string &msg) {
     if (c) c->err = msg;
     else g_err = msg;

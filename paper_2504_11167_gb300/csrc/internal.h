@@ -138,6 +138,11 @@ bool run_reduced_solve(Ctx *c, int nrhs, bool trans);
 bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs);
 bool run_project_t(Ctx *c, const double *hin, int64_t ld, int nrhs);
 bool run_dstage_t(Ctx *c, const double *hin, int64_t ldh, double *x, int64_t ldx, int nrhs);
+bool launch_residual_raw(const double *band, int64_t ldb, int k, int64_t n, const double *f,
+                         const double *x, int64_t ld, int nrhs, double *r, double *partial,
+                         unsigned *counter, double *nrm, cudaStream_t st);
+// error text returned by lrspike_last_error(NULL)
+void set_handleless_error(const std::string &msg);
 // M^{-1} (or M^{-T}) applied to the scaled FP64 vector r (in c->rv), result
 // out += |r| * M^{-1}(r/|r|); used by the outer loops.
 bool apply_precond(Ctx *c, double *out, int64_t ldo, int nrhs, bool trans);

@@ -402,6 +402,22 @@ static bool residual_nr(Ctx *c, const double *f, const double *x, int64_t ld, in
     });
 }
 
+// Launches the residual kernel on caller-provided scratch (per-CTA partial
+// sums and the ticket counter); no handle involved.
+bool launch_residual_raw(const double *band, int64_t ldb, int k, int64_t n, const double *f,
+                         const double *x, int64_t ld, int nrhs, double *r, double *partial,
+                         unsigned *counter, double *nrm, cudaStream_t st) {
+    const unsigned g = row_blocks(n);
+    switch (nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16) {
+        case 1: k_residual<1><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
+        case 2: k_residual<2><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
+        case 4: k_residual<4><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
+        case 8: k_residual<8><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
+        default: k_residual<16><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
+    }
+    return cudaGetLastError() == cudaSuccess;
+}
+
 bool run_residual(Ctx *c, const double *f, const double *x, int64_t ld, int nrhs, bool trans, bool xz) {
     if (nrhs <= 1) return residual_nr<1>(c, f, x, ld, nrhs, trans, xz);
     if (nrhs <= 2) return residual_nr<2>(c, f, x, ld, nrhs, trans, xz);

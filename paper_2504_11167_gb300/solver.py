@@ -53,7 +53,7 @@ _lib = None
 EXPORTS = ["lrspike_options_default", "lrspike_create", "lrspike_factor", "lrspike_solve",
            "lrspike_solve_transpose", "lrspike_destroy", "lrspike_last_error",
            "lrspike_launch_count", "lrspike_profile_get", "lrspike_profile_reset",
-           "lrspike_get_reduced"]
+           "lrspike_get_reduced", "lrspike_residual_noalloc"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -82,6 +82,10 @@ def load_library(path: str = LIB_PATH):
                                         ctypes.POINTER(ctypes.c_int64), dp]
     lib.lrspike_profile_reset.argtypes = [H]
     lib.lrspike_get_reduced.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
+    lib.lrspike_residual_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.c_void_p]
     for name in EXPORTS:
         if name not in ("lrspike_last_error", "lrspike_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
@@ -91,6 +95,28 @@ def load_library(path: str = LIB_PATH):
 
 def _ptr(t) -> int:
     return t.data_ptr()
+
+
+def residual_noalloc(band, k: int, f, x, r, norms, stream=None) -> None:
+    """r = f - A x and the column norms of r, through the allocation-free
+    entry point (no handle; scratch is a static device array).  band: device
+    (2k+1, ld_band); f, x: device (nrhs, ld); r: device (nrhs, n); norms:
+    device (nrhs,).  Enqueued on ``stream`` (default: torch's current stream)."""
+    import torch
+    lib = load_library()
+    F = f.unsqueeze(0) if f.dim() == 1 else f
+    X = x.unsqueeze(0) if x.dim() == 1 else x
+    n = r.shape[-1]
+    nrhs, ld = F.shape
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = lib.lrspike_residual_noalloc(ctypes.c_void_p(_ptr(band)), band.shape[1], n, k,
+                                      ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(_ptr(X)),
+                                      ctypes.c_void_p(_ptr(r)), nrhs, ld,
+                                      ctypes.c_void_p(_ptr(norms)),
+                                      ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise LRSpikeError(st, lib.lrspike_last_error(None).decode(errors="replace"))
 
 
 class LRSpike:
