@@ -12,7 +12,7 @@
 namespace lrs {
 
 const char *const kKernelNames[KID_COUNT] = {
-    "band_lu",      "prep_inverse",  "spike_rhs",   "spike_sweep", "gram",
+    "band_lu",      "spike_rhs",   "spike_sweep", "gram",
     "gram_reduce",  "coupling_gram", "jacobi",      "make_u",      "reduced_build",
     "reduced_factor", "norm",        "residual",    "dstage",      "reduced_solve",
     "retrieve",     "project_t",     "dstage_t",    "vector"};
@@ -96,7 +96,7 @@ static bool dalloc(P **ptr, size_t bytes) {
 }
 
 static void free_all(Ctx *c) {
-    void *ptrs[] = {c->off_d, c->boff_d, c->LT,   c->UT,  c->DI,   c->DS,   c->X,     c->Ucat,
+    void *ptrs[] = {c->off_d, c->boff_d, c->LT,   c->UT,  c->DI,   c->X,     c->Ucat,
                     c->PQ,    c->Gram,   c->Gpart, c->sigma, c->E, c->F,    c->Gs,    c->Rinv,
                     c->Gam,   c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
                     c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots};
@@ -200,7 +200,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     const int64_t rb = (c->n + 255) / 256;
     bool ok = dalloc(&c->off_d, (c->p + 1) * 8) && dalloc(&c->boff_d, (c->p + 1) * 8) &&
               dalloc(&c->LT, NB * KB * KB * T) && dalloc(&c->UT, NB * KB * KB * T) &&
-              dalloc(&c->DI, NB * KB * T) && dalloc(&c->DS, NB * KB * T) &&
+              dalloc(&c->DI, NB * KB * T) &&
               dalloc(&c->rv, (size_t)c->n * mx * 8) && dalloc(&c->Yv, (size_t)c->n * mx * T) &&
               dalloc(&c->Gv, (size_t)c->n * mx * T) && dalloc(&c->nrm, 4 * mx * 8) &&
               dalloc(&c->partial, (size_t)rb * mx * 8) && dalloc(&c->counter, 64) && dalloc(&c->status, 64);
@@ -270,7 +270,7 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
     if (cudaMemcpyAsync(c->status, c->host, 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return cuda_fail(c, "status reset");
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "stream sync");
-    bool ok = run_band_lu(c) && run_prep(c);
+    bool ok = run_band_lu(c);
     if (ok && c->p > 1 && c->r > 0) {
         if (c->opt.compress == LRSPIKE_COMPRESS_COUPLING)
             ok = run_coupling_gram(c) && run_jacobi(c) && run_spike_rhs(c) && run_sweep(c) && run_make_u(c);

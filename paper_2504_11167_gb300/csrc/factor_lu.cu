@@ -4,380 +4,420 @@
 // solver).  No pivoting here; the matrices of this mode are diagonally
 // dominant.
 //
-// Kernel k_band_lu: one CTA per partition walks the chain of nb_i block steps.
-// Step J eliminates the KB columns of block J inside the 2KB x 2KB window
-//     [ S_J         A_{J,J+1}   ]      S_J: diagonal block after the updates
-//     [ A_{J+1,J}   A_{J+1,J+1} ]           of the previous steps
-// (KB right-looking rank-1 steps).  Afterwards the window holds
-//     [ L_JJ \ U_JJ     U_{J,J+1}   ]   L_JJ unit lower, U_JJ upper,
-//     [ L_{J+1,J}       S_{J+1}     ]   U_{J,J+1} lower- and L_{J+1,J}
-// upper-triangular (the band does not grow without pivoting), i.e. exactly
-// the scalar band LU grouped in blocks.  The window lives in registers: the
-// thread that owns entry (a, b) also owns (a + KB, b + KB), so S_{J+1} moves
-// to the top-left quadrant by a register copy.  Pivot rows and columns are
-// broadcast through ping-pong shared buffers, one barrier per column.
-//
-// Outputs per global block J (row-major KB x KB tiles):
-//   LT[J]: strictly lower = L_JJ, upper incl. diagonal = L_{J,J-1}
-//   UT[J]: upper incl. diagonal = U_JJ, strictly lower = U_{J,J+1} (its
-//          diagonal goes to DS[J])
-// k_prep_inverse then replaces L_JJ by L_JJ^{-1}, U_JJ by the unit upper
-// inverse of diag(U_JJ)^{-1} U_JJ, scales U_{J,J+1} by diag(U_JJ)^{-1} and
-// stores DI[J] = 1 / diag(U_JJ): the solve kernels then need only
-// matrix-vector products per block step (no sequential substitution inside
-// a block).
+// One CTA per partition walks the chain of nb_i block steps.  With blocks of
+// KB >= k rows the partition is block tridiagonal, and block step J is
+//   1. S_J = L U, together with L^{-1} and U^{-1}: a recursive blocked
+//      factorisation (halves, then 16 x 16 base cases that eliminate against
+//      appended identity blocks, so that the row operations build L^{-1} and
+//      the column multipliers build U^{-1}); the off-diagonal blocks of the
+//      halves are register-tiled products on shared-memory tiles;
+//   2. U_{J,J+1} = L^{-1} A_{J,J+1},  L_{J+1,J} = A_{J+1,J} U^{-1}  (products);
+//   3. S_{J+1} = A_{J+1,J+1} - L_{J+1,J} U_{J,J+1}                   (product).
+// This is exactly the scalar band LU grouped in blocks (no pivoting, the band
+// does not grow): U_{J,J+1} is lower and L_{J+1,J} upper triangular, and the
+// products skip the structurally zero triangles.  Every step writes the
+// packed solve tiles of its block directly:
+//   LT[J] = [ L_JJ^{-1} strictly lower | L_{J,J-1} upper incl. diagonal ]
+//   UT[J] = [ (D^{-1}U_JJ)^{-1} strictly upper | D^{-1}U_{J,J+1} lower incl. diagonal ]
+//   DI[J] = D^{-1},  D = diag(U_JJ)
+// so the solve kernels need only matrix-vector products per block step.
 #include "common.cuh"
 #include "internal.h"
+#include "tile_ops.cuh"
 
 namespace lrs {
 
-// Stages band column block jc of a partition into three KB x KB tiles:
-// up = A_{jc-1,jc}, dg = A_{jc,jc}, lo = A_{jc+1,jc} (partition-local, with
-// the identity on padding rows).  Reads are coalesced: one diagonal of the
-// band is KB consecutive doubles.
+template <typename T> struct Pad { static constexpr int v = 16 / (int)sizeof(T); };
+
+// Stages band column block jc of a partition into three KB x KB tiles of row
+// stride LDt: up = A_{jc-1,jc}, dg = A_{jc,jc}, lo = A_{jc+1,jc} (partition-
+// local, with the identity on padding rows).  Reads are coalesced (one band
+// diagonal is KB consecutive doubles) and issued eight per thread before any
+// is consumed; the column block after jc is prefetched into L2 for the next
+// block step.
 template <typename T, int KB>
 __device__ void load_colblock(const double *__restrict__ band, int64_t ld, int k, int64_t s,
-                              int64_t ni, int64_t jc, T *up, T *dg, T *lo) {
-    constexpr int NT = Geo<KB>::NT;
-    for (int e = threadIdx.x; e < KB * KB; e += NT) {
+                              int64_t ni, int64_t jc, T *up, T *dg, T *lo, int LDt) {
+    constexpr int NT = 4 * KB, BATCH = 8;
+    for (int e = threadIdx.x; e < KB * LDt; e += NT) {
         up[e] = T(0);
         dg[e] = T(0);
         lo[e] = T(0);
     }
-    __syncthreads();
     const int64_t col0 = jc * KB;
     const int nd = 2 * k + 1;
-    for (int e = threadIdx.x; e < nd * KB; e += NT) {
-        const int d = e / KB, b = e - (e / KB) * KB;
-        const int64_t col = col0 + b;
-        const int arel = b + d - k;  // row - col0
-        const int64_t row = col0 + arel;
-        T v;
-        if (col >= ni) {
-            if (d != k) continue;
-            v = T(1);
-        } else {
-            if (row < 0 || row >= ni) continue;
-            v = (T)band[(int64_t)d * ld + s + col];
+    // L2 prefetch of column block jc+1 (128-byte lines of each diagonal)
+    if ((jc + 1) * KB < ni) {
+        constexpr int LINES = (KB * 8 + 127) / 128 + 1;
+        for (int e = threadIdx.x; e < nd * LINES; e += NT) {
+            const int d = e / LINES, l = e % LINES;
+            const int64_t c0 = (jc + 1) * KB + (int64_t)l * 16;
+            if (c0 < ni) {
+                const double *pa = band + (int64_t)d * ld + s + c0;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+            }
         }
-        if (arel < 0) up[(KB + arel) * KB + b] = v;
-        else if (arel < KB) dg[arel * KB + b] = v;
-        else lo[(arel - KB) * KB + b] = v;
+    }
+    __syncthreads();
+    // scatter one band value (diagonal d, column b of the block) into its tile
+    auto put = [&](int d, int b, double v) {
+        const int64_t col = col0 + b;
+        const int arel = b + d - k;
+        const int64_t row = col0 + arel;
+        if (col >= ni) {
+            if (d != k) return;
+            v = 1.0;
+        } else if (row < 0 || row >= ni) {
+            return;
+        }
+        if (arel < 0) up[(KB + arel) * LDt + b] = (T)v;
+        else if (arel < KB) dg[arel * LDt + b] = (T)v;
+        else lo[(arel - KB) * LDt + b] = (T)v;
+    };
+    const double *src0 = band + s + col0;
+    if (((ld | (s + col0)) & 1) == 0) {
+        // 16-byte loads: a warp reads 64 / KB diagonals per instruction and
+        // all of its loads are issued before any value is stored
+        constexpr int CH = KB / 2;                 // double2 per diagonal segment
+        constexpr int RPI = 32 / CH;               // diagonals per warp instruction
+        constexpr int NW = NT / 32;
+        constexpr int MAXR = (2 * KB + 1 + NW * RPI - 1) / (NW * RPI);
+        constexpr int RB = (MAXR < 9) ? MAXR : 9;  // loads in flight per lane
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        const int dl = l / CH, ch = l % CH;
+        for (int it0 = 0; it0 < MAXR; it0 += RB) {
+            double2 v[RB];
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                const int d = ((it0 + u) * NW + w) * RPI + dl;
+                const int b = 2 * ch;
+                v[u] = make_double2(0.0, 0.0);
+                if (it0 + u < MAXR && d < nd) {
+                    if (col0 + b + 1 < ni)
+                        v[u] = __ldg(reinterpret_cast<const double2 *>(src0 + (int64_t)d * ld + b));
+                    else if (col0 + b < ni)
+                        v[u].x = __ldg(src0 + (int64_t)d * ld + b);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                const int d = ((it0 + u) * NW + w) * RPI + dl;
+                if (it0 + u < MAXR && d < nd) {
+                    put(d, 2 * ch, v[u].x);
+                    put(d, 2 * ch + 1, v[u].y);
+                }
+            }
+        }
+    } else {
+        for (int base = threadIdx.x; base < nd * KB; base += NT * BATCH) {
+            double v[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) {
+                const int e = base + u * NT;
+                v[u] = 0.0;
+                if (e < nd * KB && col0 + e % KB < ni) v[u] = __ldg(src0 + (int64_t)(e / KB) * ld + e % KB);
+            }
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) {
+                const int e = base + u * NT;
+                if (e < nd * KB) put(e / KB, e % KB, v[u]);
+            }
+        }
     }
     __syncthreads();
 }
 
-// Register layout of the LU window: a TY x TX thread grid; in each of the three
-// live quadrants (TL = S_J, TR = A_{J,J+1}, BL = A_{J+1,J}) a thread owns the
-// entries (ty + TY*i, tx + TX*j), i < RY, j < RX.  The fourth quadrant (the
-// next diagonal block) is not touched by the column steps: it is updated once
-// per block step by the Schur product S_{J+1} = A_{J+1,J+1} - L_{J+1,J} U_{J,J+1}.
-template <int KB> struct LuGeo {
-    static constexpr int NT = 4 * KB;
-    static constexpr int TX = (KB >= 16) ? 16 : 8;
-    static constexpr int TY = NT / TX;
-    static constexpr int RY = KB / TY;
-    static constexpr int RX = KB / TX;
+// ---- register-tiled products of S x S shared-memory tiles -----------------
+enum Shape { FULL = 0, LOWER = 1, UPPER = 2 };  // lower/upper incl. the diagonal
+
+template <int S, int NT> struct GemmGeo {
+    static constexpr int EPT = (S * S >= NT) ? S * S / NT : 1;  // outputs per thread
+    static constexpr int TN = (EPT >= 4) ? 4 : EPT;
+    static constexpr int TM = EPT / TN;
+    static constexpr int GX = S / TN, GY = S / TM;
+    static constexpr int ACTIVE = GX * GY;
 };
+
+// One thread's TM x TN tile of A * B (rows a0.., columns b0..), through
+// registers so that the result may overwrite an operand after a barrier.
+// Triangular operands bound the inner index: exact zeros elsewhere.
+template <typename T, int S, int NT, int SA, int SB>
+struct TileGemm {
+    using G = GemmGeo<S, NT>;
+    T acc[G::TM][G::TN];
+    int a0 = 0, b0 = 0;
+    bool act = false;
+    __device__ __forceinline__ void compute(const T *A, const T *B, int ld) {
+        act = threadIdx.x < G::ACTIVE;
+        a0 = (threadIdx.x / G::GX) * G::TM;
+        b0 = (threadIdx.x % G::GX) * G::TN;
+#pragma unroll
+        for (int i = 0; i < G::TM; ++i)
+#pragma unroll
+            for (int j = 0; j < G::TN; ++j) acc[i][j] = T(0);
+        if (!act) return;
+        int qlo = 0, qhi = S;
+        if (SA == UPPER) qlo = a0;
+        if (SB == LOWER) qlo = (b0 > qlo) ? b0 : qlo;
+        if (SA == LOWER) qhi = a0 + G::TM;
+        if (SB == UPPER) qhi = (b0 + G::TN < qhi) ? b0 + G::TN : qhi;
+#pragma unroll 4
+        for (int q = qlo; q < qhi; ++q) {
+            T av[G::TM], bv[G::TN];
+#pragma unroll
+            for (int i = 0; i < G::TM; ++i) av[i] = A[(a0 + i) * ld + q];
+            ld_row<T, G::TN>(B + q * ld + b0, bv);
+#pragma unroll
+            for (int i = 0; i < G::TM; ++i)
+#pragma unroll
+                for (int j = 0; j < G::TN; ++j) acc[i][j] += av[i] * bv[j];
+        }
+    }
+    // mode 0: C = A B; 1: C = -A B; 2: C = C - A B
+    __device__ __forceinline__ void store(T *C, int ld, int mode) const {
+        if (!act) return;
+#pragma unroll
+        for (int i = 0; i < G::TM; ++i)
+#pragma unroll
+            for (int j = 0; j < G::TN; ++j) {
+                T *c = C + (a0 + i) * ld + b0 + j;
+                *c = (mode == 0) ? acc[i][j] : (mode == 1) ? -acc[i][j] : *c - acc[i][j];
+            }
+    }
+};
+
+// Base case: N x N block S (row stride ld) factorised in place into L\U while
+// the row operations turn an identity into L^{-1} and the column multipliers
+// of an identity block appended below S turn into U^{-1}.  One warp does it
+// with the three blocks in registers: lane l owns row l % N and the CPL
+// columns (l / N) * CPL .. + CPL - 1 of S, L^{-1} and U^{-1}; the pivot row
+// and column move by shuffles, so no barrier is needed between pivots.
+// Pivot reciprocal: the hardware approximate reciprocal; in FP64 refined by
+// two Newton-Raphson steps r <- r (2 - v r) (each squares the relative error,
+// from about 2^-22 to below 2^-53).  A pivot below the smallest normal number
+// counts as singular.
+template <typename T> __device__ __forceinline__ T fast_rcp(T v);
+template <> __device__ __forceinline__ float fast_rcp<float>(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+template <> __device__ __forceinline__ double fast_rcp<double>(double v) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
+    r = r * (2.0 - v * r);
+    r = r * (2.0 - v * r);
+    return r;
+}
+template <typename T> __device__ __forceinline__ bool usable_pivot(T v);
+template <> __device__ __forceinline__ bool usable_pivot<float>(float v) { return fabsf(v) >= 1.17549435e-38f && isfinite(v); }
+template <> __device__ __forceinline__ bool usable_pivot<double>(double v) { return fabs(v) >= 2.2250738585072014e-308 && isfinite(v); }
+
+template <typename T, int N, int NT>
+__device__ void base_lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *status) {
+    constexpr int CPL = N * N / 32;  // columns per lane
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x, a = l % N, h = l / N;
+        T sv[CPL], li[CPL], ui[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int b = h * CPL + j;
+            sv[j] = S[a * ld + b];
+            li[j] = (a == b) ? T(1) : T(0);
+            ui[j] = (a == b) ? T(1) : T(0);
+        }
+        // pivot loop fully unrolled: every register index is a compile-time constant
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            const int jc = c % CPL, hc = c / CPL;
+            const T piv = __shfl_sync(0xffffffffu, sv[jc], c + N * hc);
+            const T colS = __shfl_sync(0xffffffffu, sv[jc], a + N * hc);   // S[a][c]
+            const T colU = __shfl_sync(0xffffffffu, ui[jc], a + N * hc);   // Ui[a][c]
+            T rowS[CPL], rowL[CPL];
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                rowS[j] = __shfl_sync(0xffffffffu, sv[j], c + N * h);      // S[c][b]
+                rowL[j] = __shfl_sync(0xffffffffu, li[j], c + N * h);      // Li[c][b]
+            }
+            const bool ok = usable_pivot<T>(piv);
+            if (!ok && l == 0) atomicMin((unsigned long long *)status, (unsigned long long)(grow0 + c));
+            const T pinv = ok ? fast_rcp<T>(piv) : T(1);
+            const T ml = colS * pinv, mu = colU * pinv;
+            const bool below = a > c;
+            const T lrow = below ? ml : T(0), urow = below ? T(0) : mu;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int b = h * CPL + j;
+                const bool right = b > c;
+                const T ns = sv[j] - (right ? lrow : T(0)) * rowS[j];
+                const T nl = li[j] - (right ? T(0) : lrow) * rowL[j];
+                const T nu = ui[j] - (right ? urow : T(0)) * rowS[j];
+                const bool isc = (b == c);
+                sv[j] = (isc && below) ? ml : ns;
+                li[j] = nl;
+                ui[j] = (isc && !below) ? mu : nu;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int b = h * CPL + j;
+            S[a * ld + b] = sv[j];
+            Li[a * ld + b] = li[j];
+            Ui[a * ld + b] = ui[j];
+        }
+    }
+    __syncthreads();
+}
+
+// S = L U with L^{-1} in Li and U^{-1} in Ui (N x N blocks, row stride ld).
+// Halves: S11 = L11 U11 (recursively); U12 = L11^{-1} S12; L21 = S21 U11^{-1};
+// S22 -= L21 U12; S22 = L22 U22 (recursively);
+// (L^{-1})_21 = -L22^{-1} L21 L11^{-1},  (U^{-1})_12 = -U11^{-1} U12 U22^{-1}.
+// The two temporaries live in the unused triangles Li_12 and Ui_21.
+template <typename T, int N, int NT>
+__device__ void lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *status) {
+    if constexpr (N <= 16) {
+        base_lu_inv<T, N, NT>(S, Li, Ui, ld, grow0, status);
+    } else {
+        constexpr int h = N / 2;
+        T *S12 = S + h, *S21 = S + h * ld, *S22 = S + h * ld + h;
+        T *Li12 = Li + h, *Li21 = Li + h * ld, *Li22 = Li + h * ld + h;
+        T *Ui12 = Ui + h, *Ui21 = Ui + h * ld, *Ui22 = Ui + h * ld + h;
+        lu_inv<T, h, NT>(S, Li, Ui, ld, grow0, status);
+        {
+            TileGemm<T, h, NT, LOWER, FULL> g1;
+            TileGemm<T, h, NT, FULL, UPPER> g2;
+            g1.compute(Li, S12, ld);   // U12 = L11^{-1} S12
+            g2.compute(S21, Ui, ld);   // L21 = S21 U11^{-1}
+            __syncthreads();
+            g1.store(S12, ld, 0);
+            g2.store(S21, ld, 0);
+            __syncthreads();
+        }
+        {
+            TileGemm<T, h, NT, FULL, FULL> g;
+            g.compute(S21, S12, ld);
+            g.store(S22, ld, 2);       // S22 -= L21 U12
+            __syncthreads();
+        }
+        lu_inv<T, h, NT>(S22, Li22, Ui22, ld, grow0 + h, status);
+        {
+            TileGemm<T, h, NT, FULL, LOWER> g1;
+            TileGemm<T, h, NT, FULL, UPPER> g2;
+            g1.compute(S21, Li, ld);   // L21 L11^{-1}
+            g2.compute(S12, Ui22, ld); // U12 U22^{-1}
+            g1.store(Li12, ld, 0);
+            g2.store(Ui21, ld, 0);
+            __syncthreads();
+        }
+        {
+            TileGemm<T, h, NT, LOWER, FULL> g1;
+            TileGemm<T, h, NT, UPPER, FULL> g2;
+            g1.compute(Li22, Li12, ld);
+            g2.compute(Ui, Ui21, ld);
+            g1.store(Li21, ld, 1);     // (L^{-1})_21
+            g2.store(Ui12, ld, 1);     // (U^{-1})_12
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < h * h; e += NT) {
+            Li12[(e / h) * ld + e % h] = T(0);
+            Ui21[(e / h) * ld + e % h] = T(0);
+        }
+        __syncthreads();
+    }
+}
 
 template <typename T, int KB>
 __global__ void __launch_bounds__(4 * KB)
     k_band_lu(const double *__restrict__ band, int64_t ld, int k, Parts P, T *__restrict__ LT,
-              T *__restrict__ UT, T *__restrict__ DS, int64_t *__restrict__ status) {
-    using G = LuGeo<KB>;
-    constexpr int TX = G::TX, TY = G::TY, RY = G::RY, RX = G::RX, LDT = KB + 1;
+              T *__restrict__ UT, T *__restrict__ DI, int64_t *__restrict__ status) {
+    constexpr int NT = 4 * KB, LD = KB + Pad<T>::v, TS = KB * LD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *up = reinterpret_cast<T *>(smem_raw);  // A_{J,J+1}
-    T *dg = up + KB * KB;                     // A_{J+1,J+1}
-    T *lo2 = dg + KB * KB;                    // A_{J+1,J}, two buffers by block parity
-    T *Ys = lo2 + 2 * KB * KB;                // L_{J+1,J}  (KB x LDT)
-    T *Zs = Ys + KB * LDT;                    // U_{J,J+1}  (KB x LDT)
-    T *rowb = Zs + KB * LDT;                  // [2][2KB]: pivot row of [TL | TR]
-    T *colb = rowb + 4 * KB;                  // [2][2KB]: pivot column of [TL ; BL]
+    T *Sb = reinterpret_cast<T *>(smem_raw);  // S_J, then A_{J+1,J+1} and S_{J+1}
+    T *Li = Sb + TS;                          // L_JJ^{-1}
+    T *Ui = Li + TS;                          // U_JJ^{-1}
+    T *Bu = Ui + TS;                          // A_{J,J+1}, then U_{J,J+1}
+    T *Bl0 = Bu + TS;                         // A_{J+1,J}, then L_{J+1,J} (two by parity)
+    T *Bl1 = Bl0 + TS;
+    T *dU = Bl1 + TS;                         // diag(U_JJ)
 
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int64_t b0 = P.boff[part];
     const int nb = (int)(P.boff[part + 1] - b0);
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int t = threadIdx.x;
 
-    T tl[RY][RX], tr[RY][RX], bl[RY][RX];
-    load_colblock<T, KB>(band, ld, k, s, ni, 0, up, dg, lo2);
-#pragma unroll
-    for (int i = 0; i < RY; ++i)
-#pragma unroll
-        for (int j = 0; j < RX; ++j) tl[i][j] = dg[(ty + TY * i) * KB + tx + TX * j];
-    __syncthreads();
-
+    load_colblock<T, KB>(band, ld, k, s, ni, 0, Bu, Sb, Bl0, LD);
     for (int J = 0; J < nb; ++J) {
         const bool last = (J == nb - 1);
-        const T *lo_cur = lo2 + (J & 1) * KB * KB;
-        T *lo_next = lo2 + ((J + 1) & 1) * KB * KB;
-        if (!last) load_colblock<T, KB>(band, ld, k, s, ni, J + 1, up, dg, lo_next);
-#pragma unroll
-        for (int i = 0; i < RY; ++i)
-#pragma unroll
-            for (int j = 0; j < RX; ++j) {
-                const int a = ty + TY * i, b = tx + TX * j;
-                tr[i][j] = last ? T(0) : up[a * KB + b];
-                bl[i][j] = last ? T(0) : lo_cur[a * KB + b];
-            }
-        if (ty == 0)
-#pragma unroll
-            for (int j = 0; j < RX; ++j) {
-                rowb[tx + TX * j] = tl[0][j];
-                rowb[KB + tx + TX * j] = tr[0][j];
-            }
-        if (tx == 0)
-#pragma unroll
-            for (int i = 0; i < RY; ++i) {
-                colb[ty + TY * i] = tl[i][0];
-                colb[KB + ty + TY * i] = bl[i][0];
-            }
-        __syncthreads();
+        T *Blc = (J & 1) ? Bl1 : Bl0;
+        T *Bln = (J & 1) ? Bl0 : Bl1;
+        const int64_t gJ = b0 + J;
+        T *lt = LT + gJ * KB * KB;
+        T *ut = UT + gJ * KB * KB;
 
-        for (int c = 0; c < KB; ++c) {
-            const T *rb = rowb + (c & 1) * 2 * KB;
-            const T *cb = colb + (c & 1) * 2 * KB;
-            const T piv = rb[c];
-            const bool bad = (piv == T(0)) || !finite_val(piv);
-            if (bad && threadIdx.x == 0)
-                atomicMin((unsigned long long *)status, (unsigned long long)(s + (int64_t)J * KB + c));
-            const T pinv = bad ? T(1) : T(1) / piv;
-            T lt[RY], lb[RY], ut[RX], ur[RX];
-#pragma unroll
-            for (int i = 0; i < RY; ++i) {
-                const int a = ty + TY * i;
-                lt[i] = (a > c) ? cb[a] * pinv : T(0);
-                lb[i] = cb[KB + a] * pinv;
-            }
-#pragma unroll
-            for (int j = 0; j < RX; ++j) {
-                const int b = tx + TX * j;
-                ut[j] = (b > c) ? rb[b] : T(0);
-                ur[j] = rb[KB + b];
-            }
-#pragma unroll
-            for (int i = 0; i < RY; ++i)
-#pragma unroll
-                for (int j = 0; j < RX; ++j) {
-                    tl[i][j] -= lt[i] * ut[j];
-                    tr[i][j] -= lt[i] * ur[j];
-                    bl[i][j] -= lb[i] * ut[j];
-                }
-            if (tx == c % TX) {  // this thread holds column c: store the multipliers
-                const int jc = c / TX;
-#pragma unroll
-                for (int j = 0; j < RX; ++j)
-                    if (j == jc)
-#pragma unroll
-                        for (int i = 0; i < RY; ++i) {
-                            if (ty + TY * i > c) tl[i][j] = lt[i];
-                            bl[i][j] = lb[i];
-                        }
-            }
-            if (c + 1 < KB) {
-                const int r1 = c + 1;
-                T *rn = rowb + (r1 & 1) * 2 * KB;
-                T *cn = colb + (r1 & 1) * 2 * KB;
-                if (ty == r1 % TY) {
-                    const int ir = r1 / TY;
-#pragma unroll
-                    for (int i = 0; i < RY; ++i)
-                        if (i == ir)
-#pragma unroll
-                            for (int j = 0; j < RX; ++j) {
-                                rn[tx + TX * j] = tl[i][j];
-                                rn[KB + tx + TX * j] = tr[i][j];
-                            }
-                }
-                if (tx == r1 % TX) {
-                    const int jr = r1 / TX;
-#pragma unroll
-                    for (int j = 0; j < RX; ++j)
-                        if (j == jr)
-#pragma unroll
-                            for (int i = 0; i < RY; ++i) {
-                                cn[ty + TY * i] = tl[i][j];
-                                cn[KB + ty + TY * i] = bl[i][j];
-                            }
-                }
-            }
+        lu_inv<T, KB, NT>(Sb, Li, Ui, LD, s + (int64_t)J * KB, status);
+        if (t < KB) dU[t] = Sb[t * LD + t];
+        __syncthreads();
+        for (int e = t; e < KB * KB; e += NT) {
+            const int a = e / KB, b = e % KB;
+            if (a > b) lt[e] = Li[a * LD + b];
+            else if (J == 0) lt[e] = T(0);               // L_{0,-1} does not exist
+            if (a < b) ut[e] = Ui[a * LD + b] * dU[b];   // (D^{-1}U)^{-1} = U^{-1} D
+            else if (last) ut[e] = T(0);                 // no U_{J,J+1} for the last block
+        }
+        if (t < KB) DI[gJ * KB + t] = Ui[t * LD + t];
+        if (last) break;
+
+        load_colblock<T, KB>(band, ld, k, s, ni, J + 1, Bu, Sb, Bln, LD);
+        {
+            TileGemm<T, KB, NT, LOWER, LOWER> gz;
+            TileGemm<T, KB, NT, UPPER, UPPER> gy;
+            gz.compute(Li, Bu, LD);    // U_{J,J+1} = L^{-1} A_{J,J+1}
+            gy.compute(Blc, Ui, LD);   // L_{J+1,J} = A_{J+1,J} U^{-1}
+            __syncthreads();
+            gz.store(Bu, LD, 0);
+            gy.store(Blc, LD, 0);
             __syncthreads();
         }
-
-        // factors of block J, and L_{J+1,J} into block J+1's tile
-        const int64_t gJ = b0 + J;
-        T *lt_g = LT + gJ * KB * KB;
-        T *ut_g = UT + gJ * KB * KB;
-#pragma unroll
-        for (int i = 0; i < RY; ++i)
-#pragma unroll
-            for (int j = 0; j < RX; ++j) {
-                const int a = ty + TY * i, b = tx + TX * j;
-                if (a > b) lt_g[a * KB + b] = tl[i][j];
-                else {
-                    ut_g[a * KB + b] = tl[i][j];
-                    if (J == 0) lt_g[a * KB + b] = T(0);  // L_{0,-1} does not exist
-                }
-                if (b < a) ut_g[a * KB + b] = tr[i][j];
-                else if (b == a) DS[gJ * KB + a] = tr[i][j];
-                if (!last && b >= a) LT[(gJ + 1) * KB * KB + a * KB + b] = bl[i][j];
-                if (!last) {
-                    Ys[a * LDT + b] = bl[i][j];
-                    Zs[a * LDT + b] = tr[i][j];
-                }
-            }
-        if (last) break;
+        {
+            TileGemm<T, KB, NT, UPPER, LOWER> gs;
+            gs.compute(Blc, Bu, LD);
+            gs.store(Sb, LD, 2);       // S_{J+1} = A_{J+1,J+1} - L_{J+1,J} U_{J,J+1}
+        }
+        T *ltn = LT + (gJ + 1) * KB * KB;
+        for (int e = t; e < KB * KB; e += NT) {
+            const int a = e / KB, b = e % KB;
+            if (a >= b) ut[e] = Bu[a * LD + b] / dU[a];  // D^{-1} U_{J,J+1}
+            if (a <= b) ltn[e] = Blc[a * LD + b];        // L_{J+1,J}
+        }
         __syncthreads();
-        // S_{J+1} = A_{J+1,J+1} - L_{J+1,J} U_{J,J+1}; L_{J+1,J} is upper and
-        // U_{J,J+1} lower triangular, so only q >= max(a, b) contributes
-        T acc[RY][RX];
-#pragma unroll
-        for (int i = 0; i < RY; ++i)
-#pragma unroll
-            for (int j = 0; j < RX; ++j) acc[i][j] = dg[(ty + TY * i) * KB + tx + TX * j];
-        const int q0 = (ty > tx) ? ty : tx;
-        for (int q = q0; q < KB; ++q) {
-            T yv[RY], zv[RX];
-#pragma unroll
-            for (int i = 0; i < RY; ++i) yv[i] = Ys[(ty + TY * i) * LDT + q];
-#pragma unroll
-            for (int j = 0; j < RX; ++j) zv[j] = Zs[q * LDT + tx + TX * j];
-#pragma unroll
-            for (int i = 0; i < RY; ++i)
-#pragma unroll
-                for (int j = 0; j < RX; ++j) acc[i][j] -= yv[i] * zv[j];
-        }
-#pragma unroll
-        for (int i = 0; i < RY; ++i)
-#pragma unroll
-            for (int j = 0; j < RX; ++j) tl[i][j] = acc[i][j];
-        __syncthreads();
-    }
-}
-
-// Per block: L^{-1} (unit lower), the unit upper inverse of D^{-1}U, D^{-1}
-// and D^{-1} U_{J,J+1}.  Each inverse is built column by column by plain
-// substitution; a thread owns columns c and KB-1-c (equal total work), so no
-// barrier is needed: every value a thread reads is its own earlier result or
-// input.  Results are kept transposed in the unused triangle of the same
-// shared tile.  A CTA of 128 threads serves 128/KB blocks (one warp, or part
-// of one, per triangular factor).
-template <typename T, int KB>
-__global__ void __launch_bounds__(128)
-    k_prep_inverse(T *__restrict__ LT, T *__restrict__ UT, const T *__restrict__ DS,
-                   T *__restrict__ DI, int64_t NB) {
-    constexpr int LD = KB + 1, TPM = KB / 2, BPC = 128 / KB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tiles = reinterpret_cast<T *>(smem_raw);  // [BPC][2][KB x LD]
-    T *dinv = tiles + BPC * 2 * KB * LD;          // [BPC][KB]
-    const int64_t blk0 = (int64_t)blockIdx.x * BPC;
-    for (int e = threadIdx.x; e < BPC * KB * KB; e += 128) {
-        const int bb = e / (KB * KB), rem = e % (KB * KB), a = rem / KB, b = rem % KB;
-        const int64_t blk = blk0 + bb;
-        if (blk >= NB) continue;
-        T *Ls = tiles + (bb * 2 + 0) * KB * LD, *Us = tiles + (bb * 2 + 1) * KB * LD;
-        Ls[a * LD + b] = (a > b) ? LT[blk * KB * KB + rem] : T(0);
-        const T u = UT[blk * KB * KB + rem];
-        Us[a * LD + b] = (a <= b) ? u : T(0);
-        if (a == b) dinv[bb * KB + a] = T(1) / u;
-    }
-    __syncthreads();
-    const int bb = threadIdx.x / (2 * TPM), role = (threadIdx.x / TPM) & 1, t = threadIdx.x % TPM;
-    if (blk0 + bb < NB) {
-        T *S = tiles + (bb * 2 + role) * KB * LD;
-        const T *dv = dinv + bb * KB;
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            const int col = h ? KB - 1 - t : t;
-            if (role == 0) {
-                // X = L^{-1}: X[a][col] = -(L[a][col] + sum_{col<j<a} L[a][j] X[j][col]),
-                // stored at S[col][a] (upper triangle)
-                for (int a = col + 1; a < KB; ++a) {
-                    T s0 = S[a * LD + col], s1 = T(0);
-                    int j = col + 1;
-                    for (; j + 1 < a; j += 2) {
-                        s0 += S[a * LD + j] * S[col * LD + j];
-                        s1 += S[a * LD + j + 1] * S[col * LD + j + 1];
-                    }
-                    if (j < a) s0 += S[a * LD + j] * S[col * LD + j];
-                    S[col * LD + a] = -(s0 + s1);
-                }
-            } else {
-                // X = U^{-1}: X[col][col] = 1/u, X[a][col] = -(sum_{a<j<=col} U[a][j] X[j][col]) / U[a][a],
-                // stored at S[col][a] (lower triangle); the diagonal entry lives in dinv
-                for (int a = col - 1; a >= 0; --a) {
-                    T s0 = S[a * LD + col] * dv[col], s1 = T(0);
-                    int j = a + 1;
-                    for (; j + 1 < col; j += 2) {
-                        s0 += S[a * LD + j] * S[col * LD + j];
-                        s1 += S[a * LD + j + 1] * S[col * LD + j + 1];
-                    }
-                    if (j < col) s0 += S[a * LD + j] * S[col * LD + j];
-                    S[col * LD + a] = -(s0 + s1) * dv[a];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < BPC * KB * KB; e += 128) {
-        const int bb2 = e / (KB * KB), rem = e % (KB * KB), a = rem / KB, b = rem % KB;
-        const int64_t blk = blk0 + bb2;
-        if (blk >= NB) continue;
-        const T *Ls = tiles + (bb2 * 2 + 0) * KB * LD, *Us = tiles + (bb2 * 2 + 1) * KB * LD;
-        const T *dv = dinv + bb2 * KB;
-        if (a > b) {
-            LT[blk * KB * KB + rem] = Ls[b * LD + a];                        // L^{-1}
-            UT[blk * KB * KB + rem] = UT[blk * KB * KB + rem] * dv[a];       // D^{-1} U_{J,J+1}
-        } else if (a < b) {
-            UT[blk * KB * KB + rem] = Us[b * LD + a] / dv[b];                // (D^{-1}U)^{-1} = U^{-1} D
-        } else {
-            UT[blk * KB * KB + rem] = DS[blk * KB + a] * dv[a];              // diagonal of D^{-1}U_{J,J+1}
-            DI[blk * KB + a] = dv[a];
-        }
     }
 }
 
 template <typename T, int KB>
 static bool lu_impl(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
-    const size_t smem = (4 * KB * KB + 2 * KB * (KB + 1) + 8 * KB) * sizeof(T);
+    constexpr int LD = KB + Pad<T>::v;
+    const size_t smem = (6 * KB * LD + KB) * sizeof(T);
     auto kern = k_band_lu<T, KB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_LU, [&] {
-        kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>(c->band, c->ld, c->k, P, (T *)c->LT,
-                                                   (T *)c->UT, (T *)c->DS, c->status);
+        kern<<<c->p, 4 * KB, smem, c->stream>>>(c->band, c->ld, c->k, P, (T *)c->LT, (T *)c->UT, (T *)c->DI,
+                                                c->status);
     });
 }
 
-template <typename T, int KB>
-static bool prep_impl(Ctx *c) {
-    constexpr int BPC = 128 / KB;
-    const size_t smem = (BPC * 2 * KB * (KB + 1) + BPC * KB) * sizeof(T);
-    auto kern = k_prep_inverse<T, KB>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const unsigned grid = (unsigned)((c->NB + BPC - 1) / BPC);
-    return launch(c, KID_PREP, [&] {
-        kern<<<grid, 128, smem, c->stream>>>((T *)c->LT, (T *)c->UT, (const T *)c->DS, (T *)c->DI, c->NB);
-    });
-}
-
-#define LRS_DISPATCH(FN)                                             \
-    template <typename T>                                            \
-    static bool FN##_kb(Ctx *c) {                                    \
-        switch (c->KB) {                                             \
-            case 8: return FN<T, 8>(c);                              \
-            case 16: return FN<T, 16>(c);                            \
-            case 32: return FN<T, 32>(c);                            \
-            default: return FN<T, 64>(c);                            \
-        }                                                            \
+template <typename T>
+static bool lu_kb(Ctx *c) {
+    switch (c->KB) {
+        case 8: return lu_impl<T, 8>(c);
+        case 16: return lu_impl<T, 16>(c);
+        case 32: return lu_impl<T, 32>(c);
+        default: return lu_impl<T, 64>(c);
     }
+}
 
-LRS_DISPATCH(lu_impl)
-LRS_DISPATCH(prep_impl)
-
-bool run_band_lu(Ctx *c) { return c->fp64 ? lu_impl_kb<double>(c) : lu_impl_kb<float>(c); }
-bool run_prep(Ctx *c) { return c->fp64 ? prep_impl_kb<double>(c) : prep_impl_kb<float>(c); }
+bool run_band_lu(Ctx *c) { return c->fp64 ? lu_kb<double>(c) : lu_kb<float>(c); }
 
 }  // namespace lrs

@@ -91,7 +91,7 @@ __global__ void k_spike_rhs(const double *__restrict__ band, int64_t ld, int k, 
 // step is unpacked into two triangular tiles with explicit zeros and the unit
 // diagonal, so the register-tiled products need no masks.
 template <typename T, int KB, int MT, int CG>
-__global__ void __launch_bounds__((KB / 4) * CG)
+__global__ void __launch_bounds__((KB / 4) * CG, (KB >= 64 && sizeof(T) == 4) ? 2 : 1)
     k_sweep(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI, Parts P, int k,
             T *__restrict__ X) {
     // MT columns per thread, CG column groups: panel width M = MT * CG
@@ -115,9 +115,18 @@ __global__ void __launch_bounds__((KB / 4) * CG)
     const bool isV = c0 < HALFM;
     T acc[4][MT];
 
+    // L2 prefetch of the next block step's factor tile and panel
+    auto prefetch = [&](const T *tile, const T *panel) {
+        constexpr int TL = KB * KB * (int)sizeof(T) / 128, PL = KB * M * (int)sizeof(T) / 128;
+        for (int e = threadIdx.x; e < TL + PL; e += NT) {
+            const char *pa = (e < TL) ? (const char *)tile + e * 128 : (const char *)panel + (e - TL) * 128;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+        }
+    };
     for (int J = 0; J < nb; ++J) {
         const int64_t g = b0 + J;
         const T *tile = LT + g * KB * KB;
+        if (J + 1 < nb) prefetch(LT + (g + 1) * KB * KB, X + (g + 1) * KB * M);
         for (int e = threadIdx.x; e < KB * KB; e += NT) {
             const int a = e / KB, b = e % KB;
             const T v = tile[e];
@@ -154,6 +163,7 @@ __global__ void __launch_bounds__((KB / 4) * CG)
     for (int J = nb - 1; J >= 0; --J) {
         const int64_t g = b0 + J;
         const T *tile = UT + g * KB * KB;
+        if (J > 0) prefetch(UT + (g - 1) * KB * KB, X + (g - 1) * KB * M);
         for (int e = threadIdx.x; e < KB * KB; e += NT) {
             const int a = e / KB, b = e % KB;
             const T v = tile[e];

@@ -12,7 +12,6 @@ namespace lrs {
 
 enum KernelId {
     KID_LU = 0,
-    KID_PREP,
     KID_SPIKE_RHS,
     KID_SWEEP,
     KID_GRAM,
@@ -55,8 +54,8 @@ struct Ctx {
     std::vector<int64_t> off_h, boff_h;
     int64_t *off_d = nullptr, *boff_d = nullptr;
 
-    // factors: LT/UT tiles [NB][KB][KB], DI and DS [NB][KB]
-    void *LT = nullptr, *UT = nullptr, *DI = nullptr, *DS = nullptr;
+    // factors: LT/UT tiles [NB][KB][KB], DI [NB][KB]
+    void *LT = nullptr, *UT = nullptr, *DI = nullptr;
     void *X = nullptr;        // spike columns [NB][KB][m]
     void *Ucat = nullptr;     // low-rank columns [n][2r]: u_T then u_W
     void *PQ = nullptr;       // projections [p][2][r][KB]: P_i (T~_i), Q_i (W~_i)
@@ -119,7 +118,6 @@ inline bool launch(Ctx *c, int kid, F &&f) {
 
 // ---- launchers (each dispatches on the working precision and KB) --------
 bool run_band_lu(Ctx *c);
-bool run_prep(Ctx *c);
 bool run_spike_rhs(Ctx *c);
 bool run_sweep(Ctx *c);
 bool run_gram(Ctx *c);

@@ -123,22 +123,41 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
                             int nrhs, T *__restrict__ Yv, T *__restrict__ Gv, double *__restrict__ psi,
                             unsigned char *smem_raw) {
     constexpr int NT = Geo<KB>::NT, LDP = KB + 16 / (int)sizeof(T);
-    T *tb = reinterpret_cast<T *>(smem_raw);  // [2][KB x LDP] staged factor tiles
-    T *db = tb + 2 * KB * LDP;                // [2][KB] staged D^{-1}
+    const int pm = KB * nrhs;
+    double *ib = reinterpret_cast<double *>(smem_raw);  // [2][KB x nrhs] staged input rows
+    T *tb = reinterpret_cast<T *>(ib + 2 * pm);          // [2][KB x LDP] staged factor tiles
+    T *db = tb + 2 * KB * LDP;                            // [2][KB] staged D^{-1}
     T *Tt = db + 2 * KB;
-    T *Yp = Tt + KB * nrhs;
+    T *Yp = Tt + pm;
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int64_t b0 = P.boff[part];
     const int nb = (int)(P.boff[part + 1] - b0);
-    const int pm = KB * nrhs, steps = 2 * nb;
-    // step t < nb: forward block t with LT; step t >= nb: backward block 2nb-1-t with UT, DI
+    const int steps = 2 * nb;
+    // step t < nb: forward block t (LT, input rows of r); step t >= nb:
+    // backward block 2nb-1-t (UT, DI, input rows of y written by the forward sweep)
     auto stage = [&](int t) {
         const int buf = t & 1;
-        if (t < nb) stage_tile<T, KB>(LT + (b0 + t) * KB * KB, tb + buf * KB * LDP, nullptr, nullptr);
-        else {
-            const int64_t g = b0 + (steps - 1 - t);
+        double *in = ib + buf * pm;
+        if (t < nb) {
+            stage_tile<T, KB>(LT + (b0 + t) * KB * KB, tb + buf * KB * LDP, nullptr, nullptr);
+            for (int e = threadIdx.x; e < pm; e += NT) {
+                const int c = e / KB, a = e % KB;
+                const int64_t row = (int64_t)t * KB + a;
+                if (row < ni) cp_async_small<8>(in + a * nrhs + c, rin + c * n + s + row);
+            }
+        } else {
+            const int J = steps - 1 - t;
+            const int64_t g = b0 + J;
             stage_tile<T, KB>(UT + g * KB * KB, tb + buf * KB * LDP, DI + g * KB, db + buf * KB);
+            if (J < nb - 1) {  // the last forward step's output is still in Yp
+                T *inT = reinterpret_cast<T *>(in);
+                for (int e = threadIdx.x; e < pm; e += NT) {
+                    const int c = e / KB, a = e % KB;
+                    const int64_t row = (int64_t)J * KB + a;
+                    if (row < ni) cp_async_small<(int)sizeof(T)>(inT + a * nrhs + c, Yv + c * n + s + row);
+                }
+            }
         }
     };
     stage(0);
@@ -146,15 +165,17 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
     for (int t = 0; t < steps; ++t) {
         if (t + 1 < steps) stage(t + 1);
         cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
         const T *tile = tb + (t & 1) * KB * LDP;
+        const double *in = ib + (t & 1) * pm;
         if (t < nb) {
             const int J = t;
             for (int e = threadIdx.x; e < pm; e += NT) {
                 const int a = e / nrhs, c = e % nrhs;
                 const int64_t row = (int64_t)J * KB + a;
-                Tt[e] = (row < ni) ? (T)(rin[c * n + s + row] * inv[c]) : T(0);
+                Tt[e] = (row < ni) ? (T)(in[e] * inv[c]) : T(0);
             }
-            cp_async_wait1();
             __syncthreads();
             fwd_step<T, KB, S>(tile, LDP, Tt, Yp, nrhs, nrhs, J == 0);
             for (int e = threadIdx.x; e < pm; e += NT) {
@@ -164,12 +185,12 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
             }
         } else {
             const int J = steps - 1 - t;
+            const T *inT = reinterpret_cast<const T *>(in);
             for (int e = threadIdx.x; e < pm; e += NT) {
-                const int a = e / nrhs, c = e % nrhs;
+                const int a = e / nrhs;
                 const int64_t row = (int64_t)J * KB + a;
-                Tt[e] = (row < ni) ? Yv[c * n + s + row] : T(0);
+                Tt[e] = (row >= ni) ? T(0) : (J == nb - 1) ? Yp[e] : inT[e];
             }
-            cp_async_wait1();
             __syncthreads();
             bwd_step<T, KB, S>(tile, LDP, db + (t & 1) * KB, Tt, Yp, nrhs, nrhs, J == nb - 1);
             for (int e = threadIdx.x; e < pm; e += NT) {
@@ -445,7 +466,8 @@ bool run_norms(Ctx *c, const double *v, int64_t ld, int nrhs, double *out) {
 template <typename T, int KB>
 static bool dstage_impl(Ctx *c, const double *rin, int nrhs) {
     Parts P{c->off_d, c->boff_d, c->p};
-    const size_t smem = (2 * KB * (KB + 16 / sizeof(T)) + 2 * KB + 2 * KB * nrhs) * sizeof(T);
+    const size_t smem = 2 * KB * nrhs * sizeof(double) +
+                        (2 * KB * (KB + 16 / sizeof(T)) + 2 * KB + 2 * KB * nrhs) * sizeof(T);
     auto kern = k_dstage<T, KB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_DSTAGE, [&] {

@@ -17,81 +17,90 @@ namespace lrs {
 
 enum class Split { COLS, DOTS };
 
-// Tt (KB x m, ld LDM) holds b_J on entry; Yp holds y_{J-1} on entry and y_J on exit.
+// All dot products run over the full tile row with the triangle selected by a
+// mask, so the loops have compile-time trip counts and their shared-memory
+// loads are issued back to back.
+//   MODE 0: j >= a (upper incl. diagonal)   MODE 1: j < a (strictly lower)
+//   MODE 2: j <= a (lower incl. diagonal)   MODE 3: j > a (strictly upper)
+// TR = false reads the tile as stored (row a), TR = true reads its transpose
+// (column a), for the transposed sweeps.
+template <int MODE>
+__device__ __forceinline__ bool tri_in(int j, int a) {
+    return MODE == 0 ? j >= a : MODE == 1 ? j < a : MODE == 2 ? j <= a : j > a;
+}
+
+// out[a][c] = base[a][c] (op) sum_j M[a][j] V[j][c] over the masked triangle.
+// SUBTRACT: out = base - sum; else out = base + sum.  base may alias out
+// (each entry is read and written by the same thread).
+template <typename T, int KB, Split S, int MODE, bool TR, bool SUBTRACT>
+__device__ __forceinline__ void tri_product(const T *__restrict__ M, int LDS, const T *V, const T *base,
+                                            T *out, int LDM, int m, const T *rowscale) {
+    const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
+    // FP64 multiply-adds are scarce on this GPU: there the loops stop at the
+    // triangle's edge instead of masking a full row
+    constexpr bool BOUNDED = sizeof(T) == 8;
+    const int jlo = BOUNDED ? ((MODE == 0) ? a : (MODE == 3) ? a + 1 : 0) : 0;
+    const int jhi = BOUNDED ? ((MODE == 1) ? a : (MODE == 2) ? a + 1 : KB) : KB;
+    if (S == Split::COLS) {
+        for (int c = q; c < m; c += 4) {
+            T acc = T(0);
+#pragma unroll 8
+            for (int j = jlo; j < jhi; ++j) {
+                const T mv = TR ? M[j * LDS + a] : M[a * LDS + j];
+                acc += tri_in<MODE>(j, a) ? mv * V[j * LDM + c] : T(0);
+            }
+            T b0 = base[a * LDM + c];
+            if (rowscale) b0 *= rowscale[a];
+            out[a * LDM + c] = SUBTRACT ? b0 - acc : b0 + acc;
+        }
+    } else {
+        for (int c = 0; c < m; ++c) {
+            T acc = T(0);
+            if (BOUNDED) {
+                for (int j = jlo + ((q - jlo) & 3); j < jhi; j += 4) {
+                    const T mv = TR ? M[j * LDS + a] : M[a * LDS + j];
+                    acc += mv * V[j * LDM + c];
+                }
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < KB / 4; ++jj) {
+                    const int j = q + 4 * jj;
+                    const T mv = TR ? M[j * LDS + a] : M[a * LDS + j];
+                    acc += tri_in<MODE>(j, a) ? mv * V[j * LDM + c] : T(0);
+                }
+            }
+            acc = quad_sum(acc);
+            if (q == 0) {
+                T b0 = base[a * LDM + c];
+                if (rowscale) b0 *= rowscale[a];
+                out[a * LDM + c] = SUBTRACT ? b0 - acc : b0 + acc;
+            }
+        }
+    }
+}
+
+// Forward (L y = b): Tt holds b_J on entry; Yp holds y_{J-1} on entry, y_J on exit.
 template <typename T, int KB, Split S>
 __device__ __forceinline__ void fwd_step(const T *__restrict__ Ls, int LDS, T *Tt, T *Yp, int LDM,
                                          int m, bool first) {
-    const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
-    if (!first) {
-        if (S == Split::COLS) {
-            for (int c = q; c < m; c += 4) {
-                T acc = Tt[a * LDM + c];
-                for (int j = a; j < KB; ++j) acc -= Ls[a * LDS + j] * Yp[j * LDM + c];
-                Tt[a * LDM + c] = acc;
-            }
-        } else {
-            for (int c = 0; c < m; ++c) {
-                T acc = T(0);
-                for (int j = a + q; j < KB; j += 4) acc += Ls[a * LDS + j] * Yp[j * LDM + c];
-                acc = quad_sum(acc);
-                if (q == 0) Tt[a * LDM + c] -= acc;
-            }
-        }
-    }
+    if (!first) tri_product<T, KB, S, 0, false, true>(Ls, LDS, Yp, Tt, Tt, LDM, m, nullptr);
     __syncthreads();
-    if (S == Split::COLS) {
-        for (int c = q; c < m; c += 4) {
-            T acc = Tt[a * LDM + c];
-            for (int j = 0; j < a; ++j) acc += Ls[a * LDS + j] * Tt[j * LDM + c];
-            Yp[a * LDM + c] = acc;
-        }
-    } else {
-        for (int c = 0; c < m; ++c) {
-            T acc = T(0);
-            for (int j = q; j < a; j += 4) acc += Ls[a * LDS + j] * Tt[j * LDM + c];
-            acc = quad_sum(acc);
-            if (q == 0) Yp[a * LDM + c] = Tt[a * LDM + c] + acc;
-        }
-    }
+    tri_product<T, KB, S, 1, false, false>(Ls, LDS, Tt, Tt, Yp, LDM, m, nullptr);
     __syncthreads();
 }
 
-// Tt holds y_J on entry; Xn holds x_{J+1} on entry and x_J on exit.
+// Backward (U x = y): Tt holds y_J on entry; Xn holds x_{J+1} on entry, x_J on exit.
 template <typename T, int KB, Split S>
 __device__ __forceinline__ void bwd_step(const T *__restrict__ Us, int LDS, const T *__restrict__ dsm,
                                          T *Tt, T *Xn, int LDM, int m, bool first) {
-    const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
-    if (S == Split::COLS) {
-        for (int c = q; c < m; c += 4) {
-            T acc = dsm[a] * Tt[a * LDM + c];
-            if (!first)
-                for (int j = 0; j <= a; ++j) acc -= Us[a * LDS + j] * Xn[j * LDM + c];
-            Tt[a * LDM + c] = acc;
-        }
+    if (first) {
+        const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
+        for (int c = q; c < m; c += 4) Tt[a * LDM + c] *= dsm[a];
     } else {
-        for (int c = 0; c < m; ++c) {
-            T acc = T(0);
-            if (!first)
-                for (int j = q; j <= a; j += 4) acc += Us[a * LDS + j] * Xn[j * LDM + c];
-            acc = quad_sum(acc);
-            if (q == 0) Tt[a * LDM + c] = dsm[a] * Tt[a * LDM + c] - acc;
-        }
+        tri_product<T, KB, S, 2, false, true>(Us, LDS, Xn, Tt, Tt, LDM, m, dsm);
     }
     __syncthreads();
-    if (S == Split::COLS) {
-        for (int c = q; c < m; c += 4) {
-            T acc = Tt[a * LDM + c];
-            for (int j = a + 1; j < KB; ++j) acc += Us[a * LDS + j] * Tt[j * LDM + c];
-            Xn[a * LDM + c] = acc;
-        }
-    } else {
-        for (int c = 0; c < m; ++c) {
-            T acc = T(0);
-            for (int j = a + 1 + q; j < KB; j += 4) acc += Us[a * LDS + j] * Tt[j * LDM + c];
-            acc = quad_sum(acc);
-            if (q == 0) Xn[a * LDM + c] = Tt[a * LDM + c] + acc;
-        }
-    }
+    tri_product<T, KB, S, 3, false, false>(Us, LDS, Tt, Tt, Xn, LDM, m, nullptr);
     __syncthreads();
 }
 
@@ -100,80 +109,25 @@ __device__ __forceinline__ void bwd_step(const T *__restrict__ Us, int LDS, cons
 //            t = h_J - (D^{-1}U_{J-1,J})^T z^_{J-1};  z^_J = ((D^{-1}U_JJ)^{-1})^T t
 //            (the caller applies z_J = D_J^{-1} z^_J after the sweep)
 //   backward (L^T l = z): t = z_J - L_{J+1,J}^T l_{J+1};  l_J = (L_JJ^{-1})^T t
-// Uprev = UT[J-1], Ucur = UT[J]; Lnext = LT[J+1], Lcur = LT[J].
+// Uprev = UT[J-1], Ucur = UT[J]; Lnext = LT[J+1], Lcur = LT[J].  In the
+// transposed product row a of the result takes column a of the tile, so the
+// triangle conditions flip: (U_{J-1,J}' lower)^T -> j >= a; unit-upper^T -> j < a;
+// (L_{J+1,J} upper)^T -> j <= a; (unit-lower)^T -> j > a.
 template <typename T, int KB, Split S>
 __device__ __forceinline__ void fwdT_step(const T *__restrict__ Uprev, const T *__restrict__ Ucur,
                                           int LDS, T *Tt, T *Zp, int LDM, int m, bool first) {
-    const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
-    if (!first) {
-        if (S == Split::COLS) {
-            for (int c = q; c < m; c += 4) {
-                T acc = Tt[a * LDM + c];
-                for (int j = a; j < KB; ++j) acc -= Uprev[j * LDS + a] * Zp[j * LDM + c];
-                Tt[a * LDM + c] = acc;
-            }
-        } else {
-            for (int c = 0; c < m; ++c) {
-                T acc = T(0);
-                for (int j = a + q; j < KB; j += 4) acc += Uprev[j * LDS + a] * Zp[j * LDM + c];
-                acc = quad_sum(acc);
-                if (q == 0) Tt[a * LDM + c] -= acc;
-            }
-        }
-    }
+    if (!first) tri_product<T, KB, S, 0, true, true>(Uprev, LDS, Zp, Tt, Tt, LDM, m, nullptr);
     __syncthreads();
-    if (S == Split::COLS) {
-        for (int c = q; c < m; c += 4) {
-            T acc = Tt[a * LDM + c];
-            for (int j = 0; j < a; ++j) acc += Ucur[j * LDS + a] * Tt[j * LDM + c];
-            Zp[a * LDM + c] = acc;
-        }
-    } else {
-        for (int c = 0; c < m; ++c) {
-            T acc = T(0);
-            for (int j = q; j < a; j += 4) acc += Ucur[j * LDS + a] * Tt[j * LDM + c];
-            acc = quad_sum(acc);
-            if (q == 0) Zp[a * LDM + c] = Tt[a * LDM + c] + acc;
-        }
-    }
+    tri_product<T, KB, S, 1, true, false>(Ucur, LDS, Tt, Tt, Zp, LDM, m, nullptr);
     __syncthreads();
 }
 
 template <typename T, int KB, Split S>
 __device__ __forceinline__ void bwdT_step(const T *__restrict__ Lnext, const T *__restrict__ Lcur,
                                           int LDS, T *Tt, T *Lp, int LDM, int m, bool first) {
-    const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
-    if (!first) {
-        if (S == Split::COLS) {
-            for (int c = q; c < m; c += 4) {
-                T acc = Tt[a * LDM + c];
-                for (int j = 0; j <= a; ++j) acc -= Lnext[j * LDS + a] * Lp[j * LDM + c];
-                Tt[a * LDM + c] = acc;
-            }
-        } else {
-            for (int c = 0; c < m; ++c) {
-                T acc = T(0);
-                for (int j = q; j <= a; j += 4) acc += Lnext[j * LDS + a] * Lp[j * LDM + c];
-                acc = quad_sum(acc);
-                if (q == 0) Tt[a * LDM + c] -= acc;
-            }
-        }
-    }
+    if (!first) tri_product<T, KB, S, 2, true, true>(Lnext, LDS, Lp, Tt, Tt, LDM, m, nullptr);
     __syncthreads();
-    if (S == Split::COLS) {
-        for (int c = q; c < m; c += 4) {
-            T acc = Tt[a * LDM + c];
-            for (int j = a + 1; j < KB; ++j) acc += Lcur[j * LDS + a] * Tt[j * LDM + c];
-            Lp[a * LDM + c] = acc;
-        }
-    } else {
-        for (int c = 0; c < m; ++c) {
-            T acc = T(0);
-            for (int j = a + 1 + q; j < KB; j += 4) acc += Lcur[j * LDS + a] * Tt[j * LDM + c];
-            acc = quad_sum(acc);
-            if (q == 0) Lp[a * LDM + c] = Tt[a * LDM + c] + acc;
-        }
-    }
+    tri_product<T, KB, S, 3, true, false>(Lcur, LDS, Tt, Tt, Lp, LDM, m, nullptr);
     __syncthreads();
 }
 
@@ -254,6 +208,11 @@ __device__ __forceinline__ void panel_mac(T (&acc)[4][MT], const T *__restrict__
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
