@@ -65,7 +65,12 @@ enum { LRSPIKE_COMPRESS_SPIKE = 0, LRSPIKE_COMPRESS_COUPLING = 1 };
  * block-diagonal form S~~_r of LR-SPIKE-T (eq. 'red_sys_prec_mid_2'). */
 enum { LRSPIKE_REDUCED_FULL = 0, LRSPIKE_REDUCED_TRUNCATED = 1 };
 /* Outer iteration: IR = iterative refinement x += M^{-1}(f - A x);
- * BICGSTAB = right-preconditioned BiCGStab (the paper's outer solver);
+ * BICGSTAB = right-preconditioned BiCGStab (the paper's outer solver, section
+ * 4), FP64 vectors and scalars, one iteration = two applications of M^{-1};
+ * each column stops when its residual meets tol, and convergence is confirmed
+ * with the true residual f - A x (a column whose recurrence drifted is
+ * restarted from it while iterations remain).  BiCGStab allocates 8 extra
+ * FP64 vectors of n x max_nrhs at create;
  * NONE = one application x = M^{-1} f (the preconditioner alone). */
 enum { LRSPIKE_OUTER_IR = 0, LRSPIKE_OUTER_BICGSTAB = 1, LRSPIKE_OUTER_NONE = 2 };
 
@@ -121,7 +126,8 @@ lrspike_status lrspike_factor(lrspike_handle h, const double *band, int64_t ld);
  * device or both on the host (host buffers are copied in and out); x must not
  * alias f.  1 <= nrhs <= max_nrhs.  info may be NULL.
  * Errors: STATE (no successful factor), INVALID_ARG, NOT_CONVERGED (x holds
- * the last iterate), CUDA. */
+ * the last iterate; IR: max_iter reached or the residual stagnated; BiCGStab:
+ * max_iter reached or a breakdown, a zero or non-finite scalar), CUDA. */
 lrspike_status lrspike_solve(lrspike_handle h, const double *f, double *x, int32_t nrhs,
                              int64_t ld, lrspike_info *info);
 

@@ -15,7 +15,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "band_lu",      "spike_rhs",   "spike_sweep", "gram",
     "gram_reduce",  "coupling_gram", "jacobi",      "make_u",      "reduced_build",
     "reduced_factor", "norm",        "residual",    "dstage",      "reduced_solve",
-    "retrieve",     "project_t",     "dstage_t",    "vector"};
+    "retrieve",     "project_t",     "dstage_t",    "bicgstab_vector", "matvec"};
 
 static cudaEvent_t take_event(Ctx *c) {
     if (!c->free_events.empty()) {
@@ -99,7 +99,8 @@ static void free_all(Ctx *c) {
     void *ptrs[] = {c->off_d, c->boff_d, c->LT,   c->UT,  c->DI,   c->X,     c->Ucat,
                     c->PQ,    c->Gram,   c->Gpart, c->sigma, c->E, c->F,    c->Gs,    c->Rinv,
                     c->Gam,   c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
-                    c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots};
+                    c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots,
+                    c->bpartial};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (double *p : c->bv)
@@ -151,8 +152,6 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     if (o.precision == LRSPIKE_MIXED_TF32)
         return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "TF32 tensor-core factorisation is not built yet");
     if (o.pivoting) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "partial pivoting is not built yet");
-    if (o.outer == LRSPIKE_OUTER_BICGSTAB)
-        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "BiCGStab outer iteration is not built yet");
     if (o.r > 32) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "r > 32 is not built yet");
 
     Ctx *c = new (std::nothrow) Ctx();
@@ -215,6 +214,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
              dalloc(&c->psi, ni * n2 * mx * 8) && dalloc(&c->zr, ni * n2 * mx * 8) &&
              dalloc(&c->wr, ni * n2 * mx * 8);
     }
+    if (ok && o.outer == LRSPIKE_OUTER_BICGSTAB) ok = bicgstab_alloc(c);
     if (ok) ok = cudaMallocHost((void **)&c->host, (8 * mx + 8) * 8) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -340,10 +340,29 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
     int it = 0;
     bool converged = false, stalled = false;
     std::vector<double> rel(nrhs, 0.0);
-    for (it = 0;; ++it) {
+    if (outer == LRSPIKE_OUTER_BICGSTAB) {
+        BicgResult br;
+        br.rel.assign(nrhs, 0.0);
+        if (!run_bicgstab(c, fd, xd, ldd, nrhs, trans, br)) {
+            if (c->err.empty()) return cuda_fail(c, "BiCGStab iteration");
+            return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        }
+        it = br.iterations;
+        rel = br.rel;
+        double worst = 0.0;
+        bool nan = false;
+        for (int q = 0; q < nrhs; ++q) {
+            if (!(rel[q] == rel[q])) nan = true;
+            worst = std::max(worst, rel[q]);
+        }
+        hist.push_back(nan ? NAN : worst);
+        converged = !nan && worst <= c->opt.tol;
+        stalled = br.breakdown;
+    }
+    for (; outer != LRSPIKE_OUTER_BICGSTAB; ++it) {
         if (!run_residual(c, fd, xd, ldd, nrhs, trans, it == 0)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
         if (outer == LRSPIKE_OUTER_NONE) {
-            if (!apply_precond(c, xd, ldd, nrhs, trans)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+            if (!apply_precond(c, c->rv, xd, ldd, nrhs, trans, true)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
             it = 1;
             break;
         }
@@ -362,7 +381,7 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
         if (worst <= c->opt.tol) { converged = true; break; }
         if (it >= max_it) break;
         if (it >= 3 && worst > 0.9 * hist[it - 3]) { stalled = true; break; }
-        if (!apply_precond(c, xd, ldd, nrhs, trans)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        if (!apply_precond(c, c->rv, xd, ldd, nrhs, trans, true)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
     }
     if (!fdev) {
         if (cudaMemcpy2DAsync(x, ld * 8, xd, ldd * 8, c->n * 8, nrhs, cudaMemcpyDeviceToHost, c->stream) !=
@@ -381,7 +400,9 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
     if (!converged) {
         char buf[200];
         std::snprintf(buf, sizeof buf, "%s after %d iterations, worst relative residual %.3e",
-                      stalled ? "outer iteration stagnated" : "max_iter reached", it,
+                      stalled ? (outer == LRSPIKE_OUTER_BICGSTAB ? "BiCGStab breakdown" : "outer iteration stagnated")
+                              : "max_iter reached",
+                      it,
                       hist.empty() ? NAN : hist.back());
         return fail(c, LRSPIKE_ERR_NOT_CONVERGED, buf);
     }

@@ -29,6 +29,7 @@ enum KernelId {
     KID_PROJECT_T,
     KID_DSTAGE_T,
     KID_VEC,
+    KID_MATVEC,
     KID_COUNT
 };
 
@@ -81,9 +82,11 @@ struct Ctx {
     unsigned int *counter = nullptr;
     int64_t *status = nullptr; // first singular global row (INT64_MAX = none)
     double *host = nullptr;    // pinned host scratch
-    // BiCGStab vectors (FP64, n x max_nrhs each) and scalars
-    double *bv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // BiCGStab vectors (FP64, n x max_nrhs each: r, shadow r, p, v, s, t,
+    // M^{-1}p, M^{-1}s), per-column scalars and reduction partials
+    double *bv[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double *dots = nullptr;
+    double *bpartial = nullptr;
 
     const double *band = nullptr;
     int64_t ld = 0;
@@ -133,16 +136,26 @@ bool run_residual(Ctx *c, const double *f, const double *x, int64_t ld, int nrhs
                   bool x_zero);
 bool run_dstage(Ctx *c, const double *rin, int64_t ld, int nrhs);
 bool run_reduced_solve(Ctx *c, int nrhs, bool trans);
-bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs);
+bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs, bool accumulate);
 bool run_project_t(Ctx *c, const double *hin, int64_t ld, int nrhs);
-bool run_dstage_t(Ctx *c, const double *hin, int64_t ldh, double *x, int64_t ldx, int nrhs);
+bool run_dstage_t(Ctx *c, const double *hin, int64_t ldh, double *x, int64_t ldx, int nrhs, bool accumulate);
 bool launch_residual_raw(const double *band, int64_t ldb, int k, int64_t n, const double *f,
                          const double *x, int64_t ld, int nrhs, double *r, double *partial,
                          unsigned *counter, double *nrm, cudaStream_t st);
 // error text returned by lrspike_last_error(NULL)
 void set_handleless_error(const std::string &msg);
-// M^{-1} (or M^{-T}) applied to the scaled FP64 vector r (in c->rv), result
-// out += |r| * M^{-1}(r/|r|); used by the outer loops.
-bool apply_precond(Ctx *c, double *out, int64_t ldo, int nrhs, bool trans);
+// M^{-1} (or M^{-T}) applied to the FP64 vector in (n x nrhs, leading
+// dimension n) whose column norms |in| and 1/|in| are at nrm + max_nrhs and
+// nrm + 2 max_nrhs: out (+)= |in| * M^{-1}(in/|in|).  Used by the outer loops.
+bool apply_precond(Ctx *c, const double *in, double *out, int64_t ldo, int nrhs, bool trans, bool accumulate);
+
+// BiCGStab outer iteration (right-preconditioned, FP64 vectors).
+struct BicgResult {
+    int iterations = 0;
+    bool breakdown = false;   // a column hit a zero or non-finite scalar
+    std::vector<double> rel;  // final |f - A x| / |f| per column (true residual)
+};
+bool bicgstab_alloc(Ctx *c);
+bool run_bicgstab(Ctx *c, const double *f, double *x, int64_t ldx, int nrhs, bool trans, BicgResult &res);
 
 }  // namespace lrs

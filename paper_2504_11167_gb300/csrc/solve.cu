@@ -530,8 +530,8 @@ bool run_dstage(Ctx *c, const double *rin, int64_t, int nrhs) {
     }
 }
 
-bool run_dstage_t(Ctx *c, const double *hin, int64_t, double *x, int64_t ldx, int nrhs) {
-    const int acc = 1;
+bool run_dstage_t(Ctx *c, const double *hin, int64_t, double *x, int64_t ldx, int nrhs, bool accumulate) {
+    const int acc = accumulate ? 1 : 0;
     if (c->fp64) {
         switch (c->KB) {
             case 8: return dstage_t_impl<double, 8>(c, hin, x, ldx, nrhs, acc);
@@ -548,8 +548,9 @@ bool run_dstage_t(Ctx *c, const double *hin, int64_t, double *x, int64_t ldx, in
     }
 }
 
-bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs) {
-    return c->fp64 ? retrieve_impl<double>(c, x, ld, nrhs, 1) : retrieve_impl<float>(c, x, ld, nrhs, 1);
+bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs, bool accumulate) {
+    const int acc = accumulate ? 1 : 0;
+    return c->fp64 ? retrieve_impl<double>(c, x, ld, nrhs, acc) : retrieve_impl<float>(c, x, ld, nrhs, acc);
 }
 
 bool run_project_t(Ctx *c, const double *hin, int64_t, int nrhs) {
@@ -557,15 +558,15 @@ bool run_project_t(Ctx *c, const double *hin, int64_t, int nrhs) {
     return c->fp64 ? project_t_impl<double>(c, hin, nrhs) : project_t_impl<float>(c, hin, nrhs);
 }
 
-bool apply_precond(Ctx *c, double *out, int64_t ldo, int nrhs, bool trans) {
+bool apply_precond(Ctx *c, const double *in, double *out, int64_t ldo, int nrhs, bool trans, bool accumulate) {
     if (!trans) {
-        if (!run_dstage(c, c->rv, c->n, nrhs)) return false;
+        if (!run_dstage(c, in, c->n, nrhs)) return false;
         if (!run_reduced_solve(c, nrhs, false)) return false;
-        return run_retrieve(c, out, ldo, nrhs);
+        return run_retrieve(c, out, ldo, nrhs, accumulate);
     }
-    if (!run_project_t(c, c->rv, c->n, nrhs)) return false;
+    if (!run_project_t(c, in, c->n, nrhs)) return false;
     if (!run_reduced_solve(c, nrhs, true)) return false;
-    return run_dstage_t(c, c->rv, c->n, out, ldo, nrhs);
+    return run_dstage_t(c, in, c->n, out, ldo, nrhs, accumulate);
 }
 
 }  // namespace lrs
