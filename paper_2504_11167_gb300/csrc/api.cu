@@ -100,7 +100,7 @@ static void free_all(Ctx *c) {
                     c->PQ,    c->Gram,   c->Gpart, c->sigma, c->E, c->F,    c->Gs,    c->Rinv,
                     c->Gam,   c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
                     c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots,
-                    c->bpartial};
+                    c->bpartial, c->PF, c->PIVP};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (double *p : c->bv)
@@ -151,7 +151,6 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "max_iter, tol and rank_tol must be >= 0");
     if (o.precision == LRSPIKE_MIXED_TF32)
         return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "TF32 tensor-core factorisation is not built yet");
-    if (o.pivoting) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "partial pivoting is not built yet");
     if (o.r > 32) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "r > 32 is not built yet");
 
     Ctx *c = new (std::nothrow) Ctx();
@@ -197,9 +196,11 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     const size_t T = c->tsize, KB = c->KB, NB = c->NB, mx = o.max_nrhs;
     const size_t n2 = 2 * c->r, ni = (size_t)std::max(0, c->p - 1);
     const int64_t rb = (c->n + 255) / 256;
+    const bool piv = o.pivoting != 0;
     bool ok = dalloc(&c->off_d, (c->p + 1) * 8) && dalloc(&c->boff_d, (c->p + 1) * 8) &&
-              dalloc(&c->LT, NB * KB * KB * T) && dalloc(&c->UT, NB * KB * KB * T) &&
-              dalloc(&c->DI, NB * KB * T) &&
+              (piv ? dalloc(&c->PF, NB * 5 * KB * KB * T) && dalloc(&c->PIVP, NB * 2 * KB)
+                   : dalloc(&c->LT, NB * KB * KB * T) && dalloc(&c->UT, NB * KB * KB * T) &&
+                         dalloc(&c->DI, NB * KB * T)) &&
               dalloc(&c->rv, (size_t)c->n * mx * 8) && dalloc(&c->Yv, (size_t)c->n * mx * T) &&
               dalloc(&c->Gv, (size_t)c->n * mx * T) && dalloc(&c->nrm, 4 * mx * 8) &&
               dalloc(&c->partial, (size_t)rb * mx * 8) && dalloc(&c->counter, 64) && dalloc(&c->status, 64);

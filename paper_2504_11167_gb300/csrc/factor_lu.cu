@@ -418,6 +418,9 @@ static bool lu_kb(Ctx *c) {
     }
 }
 
-bool run_band_lu(Ctx *c) { return c->fp64 ? lu_kb<double>(c) : lu_kb<float>(c); }
+bool run_band_lu(Ctx *c) {
+    if (c->opt.pivoting) return run_band_lu_piv(c);
+    return c->fp64 ? lu_kb<double>(c) : lu_kb<float>(c);
+}
 
 }  // namespace lrs

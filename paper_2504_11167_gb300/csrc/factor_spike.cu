@@ -585,7 +585,10 @@ LRS_KB_DISPATCH(jacobi_impl)
 LRS_KB_DISPATCH(make_u_impl)
 
 bool run_spike_rhs(Ctx *c) { return c->fp64 ? spike_rhs_impl_kb<double>(c) : spike_rhs_impl_kb<float>(c); }
-bool run_sweep(Ctx *c) { return c->fp64 ? sweep_impl_kb<double>(c) : sweep_impl_kb<float>(c); }
+bool run_sweep(Ctx *c) {
+    if (c->opt.pivoting) return run_sweep_piv(c);
+    return c->fp64 ? sweep_impl_kb<double>(c) : sweep_impl_kb<float>(c);
+}
 bool run_gram(Ctx *c) { return c->fp64 ? gram_impl_kb<double>(c) : gram_impl_kb<float>(c); }
 bool run_coupling_gram(Ctx *c) { return coupling_gram_impl_kb<double>(c); }
 bool run_jacobi(Ctx *c) { return c->fp64 ? jacobi_impl_kb<double>(c) : jacobi_impl_kb<float>(c); }

@@ -58,6 +58,11 @@ struct Ctx {
     // factors: LT/UT tiles [NB][KB][KB], DI [NB][KB]
     void *LT = nullptr, *UT = nullptr, *DI = nullptr;
     void *X = nullptr;        // spike columns [NB][KB][m]
+    // pivoted factors (pivoting = 1) instead of LT/UT/DI: per block
+    // [L_JJ^{-1}, L_{J+1,J}, U_JJ^{-1}, U_{J,J+1}, U_{J,J+2}] and the gather
+    // permutation of the 2KB stacked rows
+    void *PF = nullptr;
+    unsigned char *PIVP = nullptr;
     void *Ucat = nullptr;     // low-rank columns [n][2r]: u_T then u_W
     void *PQ = nullptr;       // projections [p][2][r][KB]: P_i (T~_i), Q_i (W~_i)
     double *Gram = nullptr;   // [p][2][KB][KB]
@@ -139,6 +144,11 @@ bool run_reduced_solve(Ctx *c, int nrhs, bool trans);
 bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs, bool accumulate);
 bool run_project_t(Ctx *c, const double *hin, int64_t ld, int nrhs);
 bool run_dstage_t(Ctx *c, const double *hin, int64_t ldh, double *x, int64_t ldx, int nrhs, bool accumulate);
+// partial pivoting inside the partitions (pivot.cu)
+bool run_band_lu_piv(Ctx *c);
+bool run_sweep_piv(Ctx *c);
+bool run_dstage_piv(Ctx *c, const double *rin, int nrhs);
+bool run_dstage_t_piv(Ctx *c, const double *hin, double *x, int64_t ldx, int nrhs, bool accumulate);
 bool launch_residual_raw(const double *band, int64_t ldb, int k, int64_t n, const double *f,
                          const double *x, int64_t ld, int nrhs, double *r, double *partial,
                          unsigned *counter, double *nrm, cudaStream_t st);

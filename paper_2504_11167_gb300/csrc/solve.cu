@@ -514,6 +514,7 @@ static bool project_t_impl(Ctx *c, const double *hin, int nrhs) {
 }
 
 bool run_dstage(Ctx *c, const double *rin, int64_t, int nrhs) {
+    if (c->opt.pivoting) return run_dstage_piv(c, rin, nrhs);
     if (c->fp64) {
         switch (c->KB) {
             case 8: return dstage_impl<double, 8>(c, rin, nrhs);
@@ -531,6 +532,7 @@ bool run_dstage(Ctx *c, const double *rin, int64_t, int nrhs) {
 }
 
 bool run_dstage_t(Ctx *c, const double *hin, int64_t, double *x, int64_t ldx, int nrhs, bool accumulate) {
+    if (c->opt.pivoting) return run_dstage_t_piv(c, hin, x, ldx, nrhs, accumulate);
     const int acc = accumulate ? 1 : 0;
     if (c->fp64) {
         switch (c->KB) {
