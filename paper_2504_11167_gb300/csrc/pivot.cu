@@ -35,18 +35,26 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // factorisation
-template <typename T> struct PivThreads;
-template <> struct PivThreads<float> { static constexpr int H = 2; };   // 1.5 KB columns per thread
-template <> struct PivThreads<double> { static constexpr int H = 4; };  // 0.75 KB columns per thread
+// Three threads per window row: group 0 updates the row's KB panel columns,
+// which stay in shared memory (the pivot search reads them there), groups 1
+// and 2 hold the row's 2KB trailing columns in registers (their rank-1 updates
+// never need a column mask).
 
 template <typename T, int KB> struct PivLU {
-    static constexpr int H = PivThreads<T>::H;
+    static constexpr int H = 3;
     static constexpr int R2 = 2 * KB;     // window rows
     static constexpr int WC = 3 * KB;     // window columns
     static constexpr int NT = R2 * H;     // threads
     static constexpr int CPT = WC / H;    // window columns per thread
-    static constexpr int LDS = WC + 1;    // shared row stride
+    static constexpr int LDS = WC + 16 / (int)sizeof(T);  // shared row stride (16-byte rows)
     static constexpr int VW = 16 / (int)sizeof(T);  // vector width of a 16-byte load
+    // FP32: the next block row of the band is prefetched (raw FP64) while the
+    // current block is eliminated; FP64 has no shared memory left for it
+    static constexpr bool PREFETCH = sizeof(T) == 4;
+    static constexpr int RB = PREFETCH ? (2 * KB + 1) * KB : 0;  // raw band doubles
+    static constexpr size_t smem_bytes = (size_t)R2 * LDS * sizeof(T) + (size_t)RB * sizeof(double) +
+                                         (4 * KB + 2 * KB) * sizeof(T) + 2 * R2 * (sizeof(unsigned long long) + sizeof(unsigned)) +
+                                         R2 * sizeof(int);
     static_assert(CPT % VW == 0, "columns per thread must fill vector loads");
 };
 
@@ -55,24 +63,43 @@ __device__ __forceinline__ double abs_t(double v) { return fabs(v); }
 
 template <typename T> __device__ __forceinline__ bool pivot_ok(T v) { return isfinite(v) && abs_t(v) > T(0); }
 
-// Stages block row b of partition A_i (local rows b*KB ..) into window rows
-// wr0 .. wr0+KB-1, window column l <-> local column J*KB + l.  Rows past the
-// partition are identity rows (the padding).  The rows must be zero already.
-template <typename T, int KB>
-__device__ void stage_block_row(const double *__restrict__ band, int64_t ld, int k, int64_t s, int64_t ni,
-                                int b, int J, T *S, int wr0) {
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_all() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Block row b of A_i (local rows b*KB ..) as (band row d, column c) pairs:
+// row = b*KB + c, column = row + k - d, window column = column - J*KB.
+// Consecutive c are consecutive band addresses (coalesced).
+struct BandRowMap {
+    int64_t row, col, wcol;
+    bool inside;  // row and column inside the partition
+};
+template <int KB>
+__device__ __forceinline__ BandRowMap band_row_map(int e, int k, int64_t ni, int b, int J) {
+    const int d = e / KB, c = e % KB;
+    BandRowMap m;
+    m.row = (int64_t)b * KB + c;
+    m.col = m.row + k - d;
+    m.wcol = m.col - (int64_t)J * KB;
+    m.inside = m.row < ni && m.col >= 0 && m.col < ni;
+    return m;
+}
+
+// Scatters block row b into window rows wr0 .. wr0+KB-1 (already zero).
+// Rows past the partition are identity rows (the padding).  src(e) gives
+// the band value of pair e when it is inside the partition.
+template <typename T, int KB, typename Src>
+__device__ void put_block_row(int k, int64_t ni, int b, int J, T *S, int wr0, Src &&src) {
     using G = PivLU<T, KB>;
-    const int64_t row0 = (int64_t)b * KB;
     for (int e = threadIdx.x; e < (2 * k + 1) * KB; e += G::NT) {
-        const int d = e / KB, c = e % KB;  // band row d, consecutive c: coalesced reads
-        const int64_t row = row0 + c, col = row + k - d;
-        const int64_t wcol = col - (int64_t)J * KB;
-        if (row < ni) {
-            if (col >= 0 && col < ni && wcol >= 0 && wcol < G::WC)
-                S[(wr0 + c) * G::LDS + wcol] = (T)band[(int64_t)d * ld + s + col];
-        } else if (d == k && wcol < G::WC) {
-            S[(wr0 + c) * G::LDS + wcol] = T(1);
-        }
+        const BandRowMap m = band_row_map<KB>(e, k, ni, b, J);
+        const int c = e % KB, d = e / KB;
+        if (m.wcol < 0 || m.wcol >= G::WC) continue;
+        if (m.inside) S[(wr0 + c) * G::LDS + m.wcol] = (T)src(e, m);
+        else if (m.row >= ni && d == k) S[(wr0 + c) * G::LDS + m.wcol] = T(1);
     }
 }
 
@@ -84,14 +111,14 @@ __global__ void __launch_bounds__(PivLU<T, KB>::NT)
     constexpr int R2 = G::R2, WC = G::WC, CPT = G::CPT, LDS = G::LDS, NT = G::NT, VW = G::VW;
     constexpr int TT = KB * KB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *S = reinterpret_cast<T *>(smem_raw);       // [R2][LDS] window at its final positions
-    T *rowp = S + R2 * LDS;                        // [2][WC] pivot row (16-byte aligned: R2*LDS*T is)
-    T *colv = rowp + 2 * WC;                       // [2][R2] column j
-    T *absv = colv + 2 * R2;                       // [2][R2] |column j|, -1 for finished rows
-    T *pinvs = absv + 2 * R2;                      // [KB] 1 / pivot of column j
-    T *dinv = pinvs + KB;                          // [KB] 1 / U_jj
-    int *pos = reinterpret_cast<int *>(dinv + KB); // [R2] current position of window row i
-    int *rowAt = pos + R2;                         // [R2] window row at position q
+    T *S = reinterpret_cast<T *>(smem_raw);                       // [R2][LDS] window at final positions
+    double *Rb = reinterpret_cast<double *>(S + R2 * LDS);        // [2k+1][KB] prefetched band (FP32 only)
+    T *rowp = reinterpret_cast<T *>(Rb + G::RB);                  // [2][2KB] trailing part of the pivot row
+    T *pinvs = rowp + 4 * KB;                                     // [KB] 1 / pivot of column j
+    T *dinv = pinvs + KB;                                         // [KB] 1 / U_jj
+    unsigned long long *khi = reinterpret_cast<unsigned long long *>(dinv + KB);  // [2][R2] |value| bits
+    unsigned *klo = reinterpret_cast<unsigned *>(khi + 2 * R2);   // [2][R2] (0xffff - position) << 16 | row
+    int *rowAt = reinterpret_cast<int *>(klo + 2 * R2);           // [R2] window row at final position q
 
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
@@ -99,102 +126,148 @@ __global__ void __launch_bounds__(PivLU<T, KB>::NT)
     const int nb = (int)(P.boff[part + 1] - b0);
     const int i = threadIdx.x % R2, h = threadIdx.x / R2;
     const int lane = threadIdx.x & 31;
+    auto from_band = [&](int e, const BandRowMap &m) { return band[(int64_t)(e / KB) * ld + s + m.col]; };
+    // pivot search key of a row: larger |value| first, then lower position;
+    // finished rows get 0 (below every candidate, including a zero value)
+    auto put_key = [&](int buf, T v, int mypos, bool done) {
+        unsigned long long hi = 0;
+        unsigned lo = 0;
+        if (!done) {
+            const T av = isnan(v) ? T(INFINITY) : abs_t(v);
+            if constexpr (sizeof(T) == 4) hi = (unsigned long long)__float_as_uint(av);
+            else hi = (unsigned long long)__double_as_longlong(av);
+            lo = ((0xffffu - (unsigned)mypos) << 16) | (unsigned)i;
+        }
+        khi[buf * R2 + i] = hi;
+        klo[buf * R2 + i] = lo;
+    };
 
     for (int e = threadIdx.x; e < R2 * LDS; e += NT) S[e] = T(0);
     __syncthreads();
-    stage_block_row<T, KB>(band, ld, k, s, ni, 0, 0, S, 0);
-    stage_block_row<T, KB>(band, ld, k, s, ni, 1, 0, S, KB);
+    put_block_row<T, KB>(k, ni, 0, 0, S, 0, from_band);
+    put_block_row<T, KB>(k, ni, 1, 0, S, KB, from_band);
     __syncthreads();
     T a[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) a[q] = S[i * LDS + h * CPT + q];
 
     for (int J = 0; J < nb; ++J) {
-        if (threadIdx.x < R2) {
-            pos[threadIdx.x] = threadIdx.x;
-            rowAt[threadIdx.x] = threadIdx.x;
+        if constexpr (G::PREFETCH) {
+            // block row J+2 of the band lands in Rb while block J is eliminated
+            if (J + 1 < nb) {
+                for (int e = threadIdx.x; e < (2 * k + 1) * KB; e += NT) {
+                    const BandRowMap m = band_row_map<KB>(e, k, ni, J + 2, J + 1);
+                    if (m.inside) cp_async8(Rb + e, band + (int64_t)(e / KB) * ld + s + m.col);
+                }
+            }
+            cp_async_commit_all();
         }
         bool done = false;
-        int mystep = KB;
-        T nextv = a[0];  // column 0 is slot 0 of h == 0
-        __syncthreads();
+        int mystep = KB, mypos = i;  // positions are tracked by every thread of the row
+        T *prow = S + i * LDS;       // the row's panel columns
+        if (h == 0) put_key(0, prow[0], mypos, false);
         for (int j = 0; j < KB; ++j) {
             const int buf = j & 1;
-            const int hj = j / CPT;
-            if (h == hj) {
-                colv[buf * R2 + i] = nextv;
-                absv[buf * R2 + i] = done ? T(-1) : (isnan(nextv) ? T(INFINITY) : abs_t(nextv));
-            }
             __syncthreads();
-            // pivot search, repeated by every warp: largest |value|, then lowest position
-            T bv = T(-2);
-            int bp = INT_MAX, bi = 0;
+            // pivot search, repeated by every warp
+            unsigned long long bh = 0;
+            unsigned bl = 0;
             for (int q = lane; q < R2; q += 32) {
-                const T v = absv[buf * R2 + q];
-                const int ps = pos[q];
-                if (v > bv || (v == bv && ps < bp)) { bv = v; bp = ps; bi = q; }
+                const unsigned long long vh = khi[buf * R2 + q];
+                const unsigned vl = klo[buf * R2 + q];
+                if (vh > bh || (vh == bh && vl > bl)) { bh = vh; bl = vl; }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; bi = oi; }
+                const unsigned long long oh = __shfl_xor_sync(0xffffffffu, bh, o);
+                const unsigned ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                if (oh > bh || (oh == bh && ol > bl)) { bh = oh; bl = ol; }
             }
-            const int p = bi;
-            const T piv = colv[buf * R2 + p];
+            const int p = (int)(bl & 0xffffu), pos_p = 0xffff - (int)(bl >> 16);
+            const T piv = S[p * LDS + j];
             const bool ok = pivot_ok<T>(piv);
             const T pinv = ok ? T(1) / piv : T(1);
-            if (i == p) {
+            if (i == p && h > 0) {
+                T *dst = rowp + buf * 2 * KB + (h - 1) * KB;
 #pragma unroll
-                for (int q = 0; q < CPT; ++q) rowp[buf * WC + h * CPT + q] = a[q];
+                for (int g = 0; g < CPT / VW; ++g) {
+                    if constexpr (VW == 4)
+                        *reinterpret_cast<float4 *>(dst + 4 * g) = make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]);
+                    else
+                        *reinterpret_cast<double2 *>(dst + 2 * g) = make_double2(a[2 * g], a[2 * g + 1]);
+                }
+            }
+            // gbtf2's row exchange: the row at position j moves to p's position
+            if (i == p) {
                 done = true;
                 mystep = j;
+                mypos = j;
+            } else if (mypos == j) {
+                mypos = pos_p;
             }
-            __syncthreads();
             if (threadIdx.x == 0) {
                 if (!ok) atomicMin((unsigned long long *)status, (unsigned long long)(s + (int64_t)J * KB + j));
                 pinvs[j] = pinv;
-                // exchange positions j and pos[p] (gbtf2's row swap)
-                const int q = rowAt[j], pp = pos[p];
-                rowAt[j] = p;
-                rowAt[pp] = q;
-                pos[p] = j;
-                pos[q] = pp;
             }
-            // rank-1 update of the columns right of j; the multiplier stays
-            // unscaled in column j and is scaled when the window is written out
-            const T m = done ? T(0) : colv[buf * R2 + i] * pinv;
-            const int first = j + 1 - h * CPT;  // first own slot to update (uniform per warp)
-            const T *up = rowp + buf * WC + h * CPT;
-#pragma unroll
-            for (int g = 0; g < CPT / VW; ++g) {
-                if (VW * g + VW - 1 < first) continue;  // whole group left of the update
-                T u[VW];
-                if constexpr (VW == 4) {
-                    const float4 t4 = *reinterpret_cast<const float4 *>(up + VW * g);
-                    u[0] = t4.x; u[1] = t4.y; u[2] = t4.z; u[3] = t4.w;
-                } else {
-                    const double2 t2 = *reinterpret_cast<const double2 *>(up + VW * g);
-                    u[0] = t2.x; u[1] = t2.y;
+            __syncthreads();
+            // rank-1 update right of column j; the multiplier stays unscaled in
+            // column j and is scaled when the window is written out
+            const T m = done ? T(0) : prow[j] * pinv;
+            if (h == 0) {
+                if (!done) {
+                    const T *pr = S + p * LDS;
+                    int l = j + 1;
+                    for (; l < KB && (l % VW) != 0; ++l) prow[l] -= m * pr[l];
+                    for (; l < KB; l += VW) {
+                        if constexpr (VW == 4) {
+                            float4 x = *reinterpret_cast<const float4 *>(prow + l);
+                            const float4 y = *reinterpret_cast<const float4 *>(pr + l);
+                            x.x -= m * y.x; x.y -= m * y.y; x.z -= m * y.z; x.w -= m * y.w;
+                            *reinterpret_cast<float4 *>(prow + l) = x;
+                        } else {
+                            double2 x = *reinterpret_cast<const double2 *>(prow + l);
+                            const double2 y = *reinterpret_cast<const double2 *>(pr + l);
+                            x.x -= m * y.x; x.y -= m * y.y;
+                            *reinterpret_cast<double2 *>(prow + l) = x;
+                        }
+                    }
                 }
+                if (j + 1 < KB) put_key(buf ^ 1, prow[j + 1], mypos, done);
+            } else {
+                const T *up = rowp + buf * 2 * KB + (h - 1) * KB;
 #pragma unroll
-                for (int v = 0; v < VW; ++v) {
-                    const int q = VW * g + v;
-                    if (q >= first) a[q] -= m * u[v];
-                    if (q == first) nextv = a[q];
+                for (int g = 0; g < CPT / VW; ++g) {
+                    if constexpr (VW == 4) {
+                        const float4 u = *reinterpret_cast<const float4 *>(up + 4 * g);
+                        a[4 * g] -= m * u.x;
+                        a[4 * g + 1] -= m * u.y;
+                        a[4 * g + 2] -= m * u.z;
+                        a[4 * g + 3] -= m * u.w;
+                    } else {
+                        const double2 u = *reinterpret_cast<const double2 *>(up + 2 * g);
+                        a[2 * g] -= m * u.x;
+                        a[2 * g + 1] -= m * u.y;
+                    }
                 }
             }
         }
-        __syncthreads();  // thread 0's last position and pivot updates
+        __syncthreads();
         // window rows to their final positions; multipliers scaled by 1/pivot
-        const int fp = pos[i];
+        if (h == 0) {
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int l = h * CPT + q;
-            T v = a[q];
-            if (l < KB && l < mystep) v *= pinvs[l];
-            S[fp * LDS + l] = v;
+            for (int q = 0; q < CPT; ++q) a[q] = (q < mystep) ? prow[q] * pinvs[q] : prow[q];
+            rowAt[mypos] = i;
+        }
+        __syncthreads();
+        {
+            T *dst = S + mypos * LDS + h * CPT;
+#pragma unroll
+            for (int g = 0; g < CPT / VW; ++g) {
+                if constexpr (VW == 4)
+                    *reinterpret_cast<float4 *>(dst + 4 * g) = make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]);
+                else
+                    *reinterpret_cast<double2 *>(dst + 2 * g) = make_double2(a[2 * g], a[2 * g + 1]);
+            }
         }
         __syncthreads();
         const int64_t g = b0 + J;
@@ -211,9 +284,38 @@ __global__ void __launch_bounds__(PivLU<T, KB>::NT)
             dinv[threadIdx.x] = pivot_ok<T>(d) ? T(1) / d : T(1);
         }
         __syncthreads();
-        // triangular inverses by groups of four lanes per column, written over
-        // the L_{J+1,J} block (L^{-1}) and the U_{J,J+1} block (U^{-1}) of S
-        {
+        // triangular inverses, written over the L_{J+1,J} block (L^{-1}) and
+        // the U_{J,J+1} block (U^{-1}) of S
+        if constexpr (sizeof(T) == 4) {
+            // one column per thread, the column held in registers (the window's
+            // registers are free until the next block is loaded)
+            if (threadIdx.x < 2 * KB) {
+                const int c = threadIdx.x % KB;
+                T x[KB];
+                if (threadIdx.x < KB) {  // L^{-1}, unit lower: x_r = -sum_{b<r} L_rb x_b
+#pragma unroll
+                    for (int r = 0; r < KB; ++r) {
+                        T s4[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+                        for (int b = 0; b < r; ++b) s4[b & 3] += S[r * LDS + b] * x[b];
+                        x[r] = (r == c) ? T(1) : -((s4[0] + s4[1]) + (s4[2] + s4[3]));
+                    }
+#pragma unroll
+                    for (int r = 0; r < KB; ++r) S[(KB + r) * LDS + c] = x[r];
+                } else {  // U^{-1}: x_r = -(sum_{b>r} U_rb x_b) / U_rr
+#pragma unroll
+                    for (int r = KB - 1; r >= 0; --r) {
+                        T s4[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+                        for (int b = r + 1; b < KB; ++b) s4[b & 3] += S[r * LDS + b] * x[b];
+                        x[r] = (r > c) ? T(0) : (r == c) ? dinv[c] : -((s4[0] + s4[1]) + (s4[2] + s4[3])) * dinv[r];
+                    }
+#pragma unroll
+                    for (int r = 0; r < KB; ++r) S[r * LDS + KB + c] = x[r];
+                }
+            }
+        } else {
+            // FP64 (register budget of 512 threads): four lanes per column
             const int quad = threadIdx.x >> 2, l4 = threadIdx.x & 3;
             const unsigned qmask = 0xFu << (lane & ~3);
             constexpr int NQ = NT / 4;
@@ -252,25 +354,29 @@ __global__ void __launch_bounds__(PivLU<T, KB>::NT)
             F[2 * TT + e] = S[r * LDS + KB + c];    // U_JJ^{-1}
         }
         if (J + 1 == nb) break;
+        __syncthreads();
         // next window: rows 0..KB-1 <- the Schur rows (columns J+1, J+2),
-        // rows KB..2KB-1 <- block row J+2 of A_i
-        if (i < KB) {
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                const int l = h * CPT + q;
-                a[q] = (l < 2 * KB) ? S[(KB + i) * LDS + KB + l] : T(0);
-            }
+        // rows KB..2KB-1 <- block row J+2 of A_i; then every thread reloads
+        // its row (one unconditional load keeps the registers free above)
+        for (int e = threadIdx.x; e < KB * WC; e += NT) {
+            const int r = e / WC, l = e % WC;
+            S[r * LDS + l] = (l < 2 * KB) ? S[(KB + r) * LDS + KB + l] : T(0);
         }
         __syncthreads();
         for (int e = threadIdx.x; e < KB * LDS; e += NT) S[KB * LDS + e] = T(0);
-        __syncthreads();
-        stage_block_row<T, KB>(band, ld, k, s, ni, J + 2, J + 1, S, KB);
-        __syncthreads();
-        if (i >= KB) {
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) a[q] = S[i * LDS + h * CPT + q];
+        if constexpr (G::PREFETCH) {
+            cp_async_wait_all();
+            __syncthreads();
+            put_block_row<T, KB>(k, ni, J + 2, J + 1, S, KB, [&](int e, const BandRowMap &) { return Rb[e]; });
+        } else {
+            __syncthreads();
+            put_block_row<T, KB>(k, ni, J + 2, J + 1, S, KB, from_band);
         }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) a[q] = S[i * LDS + h * CPT + q];
     }
+    if constexpr (G::PREFETCH) cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -653,7 +759,7 @@ template <typename T, int KB>
 bool lu_piv_impl(Ctx *c) {
     using G = PivLU<T, KB>;
     Parts P{c->off_d, c->boff_d, c->p};
-    const size_t smem = ((size_t)G::R2 * G::LDS + 2 * G::WC + 4 * G::R2 + 2 * KB) * sizeof(T) + 2 * G::R2 * sizeof(int);
+    const size_t smem = G::smem_bytes;
     auto kern = k_band_lu_piv<T, KB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_LU, [&] {
