@@ -14,7 +14,13 @@ C ABI with host buffers (host-to-device copies of the band and f and the
 device-to-host copy of x inside the timed region), the roofline of the
 dominant kernel, and the CPU oracle timed on a bounded sample.
 
+Also on the same band: the weakly dominant variant (diagonal rescaled to
+dominance 0.6) with partial pivoting inside the partitions, reported under
+"variants".
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       python bench.py --profile-case   (one factor + solve at n = 1,048,576,
+                                         p = 64: the case used for ncu captures)
 With N > 1 (torchrun), every rank solves its own copy of the workload (the
 path needs no exchange between independent systems; weak scaling).
 """
@@ -47,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile-case", action="store_true")
     return ap.parse_args()
 
 
@@ -149,6 +157,12 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
+# DRAM bytes (read + write) per launch at this workload, from one ncu capture of
+# the quarter-size case (python bench.py --profile-case: n/4 rows, p/4
+# partitions, same n_i) scaled by 4 (both grow with n).  None = not captured.
+NCU_TRAFFIC = {"band_lu": 4 * (1.083490e9 + 0.512573e9)}
+
+
 def kernel_work(name: str, prof: dict, precision_bytes: int):
     """Algorithmic bytes moved (HBM-bound kernels) or flops (compute-bound
     kernels) of one launch, from the workload's sizes."""
@@ -160,15 +174,39 @@ def kernel_work(name: str, prof: dict, precision_bytes: int):
         return "hbm", n * (2 * kb + 1) * tb + n * nrhs * (8 + 4 * tb)
     if name == "retrieve":          # u columns + g + x read/write
         return "hbm", n * 2 * r * tb + n * nrhs * (tb + 16)
-    if name == "band_lu":           # 2 n k^2 flops (block steps on KB = k)
+    if name == "band_lu":           # 2 n k^2 flops: the textbook band LU count
         return "alu", 2.0 * n * k * k
     if name == "spike_sweep":       # triangular block products, V fwd skipped? (counted as done)
         return "alu", 6.0 * n * k * k
     return None, None
 
 
+def profile_case():
+    """One factor + solve on a quarter-size case (n = 1,048,576, p = 64, same
+    k, r, dominance and n_i): small enough for ncu replays, inputs still larger
+    than L2."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_11167_gb300 import inputs
+    from paper_2504_11167_gb300.solver import LRSpike
+    n, p = N // 4, P // 4
+    seed = inputs.SEED_BASE + 2
+    band = torch.from_numpy(inputs.dominant_band(n, K, DOM, seed)).cuda()
+    f = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, NRHS, seed).T)).cuda()
+    with LRSpike(n, K, p, R, precision="fp32", reduced="truncated", tol=TOL, max_nrhs=NRHS) as s:
+        for _ in range(2):
+            s.factor(band)
+            x, info = s.solve(f)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": {"n": n, "k": K, "p": p, "r": R, "iterations": info["iterations"],
+                                       "rel_residual": info["max_rel_residual"]}}))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -202,11 +240,12 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def run(precision, steps, warmup, profile):
+    def run(precision, steps, warmup, profile, A=None, pivoting=False):
+        A = band if A is None else A
         s = LRSpike(N, K, P, R, precision=precision, reduced="truncated", tol=TOL, max_nrhs=NRHS,
-                    profile=profile)
+                    profile=profile, pivoting=pivoting)
         for _ in range(warmup):
-            s.factor(band)
+            s.factor(A)
             s.solve(ft)
         s.profile_reset()
         barrier()
@@ -216,7 +255,7 @@ def main():
             e0.record(stream)
             l0 = s.launch_count()
             for _ in range(steps):
-                s.factor(band)
+                s.factor(A)
                 x, info = s.solve(ft)
             e1.record(stream)
             barrier()
@@ -259,13 +298,13 @@ def main():
         if bound == "hbm":
             ach = work / per_launch_s / 1e9
             roofline = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                        "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                        "unit": "GB/s", "frac": ach / hbm_peak, "traffic": NCU_TRAFFIC.get(name),
                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
         elif bound == "alu":
             alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # FP32 FMA lanes x clock
             ach = work / per_launch_s / 1e12
             roofline = {"kernel": name, "bound": "alu", "achieved": ach, "peak": alu_peak,
-                        "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                        "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": NCU_TRAFFIC.get(name),
                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     kernels = {k_: {"launches": c_, "ms_total": round(t_, 4)} for k_, (c_, t_) in prof.items() if c_}
 
@@ -275,6 +314,20 @@ def main():
         ms64, _, _, info64, _, _ = run("fp64", max(1, args.steps // 2), 1, False)
         fp64 = {"value": N * NRHS / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                 "iterations": info64["iterations"], "tol": TOL}
+
+    # weakly dominant variant: diagonal rescaled from dominance 1.1 to 0.6, pivoting
+    variants = None
+    if not args.no_variants:
+        A06 = band.clone()
+        A06[K] *= 0.6 / DOM
+        msv, _, profv, infov, _, xv = run("fp32", max(1, args.steps // 2), 1, True, A=A06, pivoting=True)
+        del A06, xv
+        variants = {"pivoted_dominance_0.6": {
+            "value": N * NRHS / (msv * 1e-3), "unit": UNIT, "ms_per_step": msv,
+            "iterations": infov["iterations"], "rel_residual": infov["max_rel_residual"],
+            "pivoting": "partial, inside each partition",
+            "kernels": {k_: {"launches": c_, "ms_total": round(t_, 4)} for k_, (c_, t_) in profv.items() if c_}}}
+        torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -315,7 +368,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": config_dict(), "iterations": info["iterations"],
                 "rel_residual": relres, "gpu_launches": launches, "roofline": roofline,
-                "kernels": kernels, "fp64_gpu": fp64, "e2e": e2e, "cpu_baseline": cpu,
+                "kernels": kernels, "fp64_gpu": fp64, "variants": variants, "e2e": e2e, "cpu_baseline": cpu,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
