@@ -18,7 +18,10 @@ What it computes, step by step in the paper's order:
     low-rank SVD that follows it): T_i ~ u Sigma v, W_i likewise.  Mode SPIKE
     takes the truncated SVD of the explicit spike; mode COUPLING takes the
     truncated SVD of B_i (C_i) and solves with its left factor, the
-    alternative the paper discusses at the end of section 3.1;
+    alternative the paper discusses at the end of section 3.1.  For wide bands
+    (k > 64) the truncation is the randomized SVD the paper uses (section 3.1,
+    Halko-Martinsson-Tropp proto-algorithm with a few passes and oversampling),
+    written here on the right singular subspace through the Gram matrix;
   * the reduced system of the low-rank spike matrix S~ = I + U V
     (section 3.2, eqs. 'per-partition_1/2' and 'red_sys_prec_mid_1'), in
     compressed unknowns zeta_i = P_i x_{i+1,t}, omega_{i+1} = Q_{i+1} x_{i,b}
@@ -178,6 +181,95 @@ def coupling_C(ab: np.ndarray, k: int, s: int) -> np.ndarray:
     return np.array([[band_entry(ab, k, s + a, s - k + b) for b in range(k)] for a in range(k)])
 
 
+# --------------------------------------------------------------------------
+# Randomized truncation for wide bands (section 3.1: the randomized SVD of
+# Halko, Martinsson and Tropp, "proto-algorithm", few passes, oversampling)
+# --------------------------------------------------------------------------
+_GOLDEN = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, i: int) -> int:
+    """Output i (0-based) of the SplitMix64 generator started at `seed`
+    (Steele, Lea and Flood, 2014): state_i = seed + (i+1)*0x9E3779B97F4A7C15,
+    then the mixing function of the published definition."""
+    z = (seed + (i + 1) * _GOLDEN) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def gaussian_sketch(rows: int, cols: int, seed: int) -> np.ndarray:
+    """Omega (rows x cols): entry (a, j) is the Box-Muller normal of the
+    SplitMix64 outputs 2c and 2c+1, c = a*cols + j, with
+    u1 = ((o_2c >> 11) + 0.5) 2^-53 in (0, 1), u2 = (o_2c+1 >> 11) 2^-53:
+    omega = sqrt(-2 ln u1) cos(2 pi u2).  A counter-based generator, so the
+    CUDA side draws the same numbers from the same definition."""
+    om = np.empty((rows, cols))
+    for a in range(rows):
+        for j in range(cols):
+            c = a * cols + j
+            u1 = ((splitmix64(seed, 2 * c) >> 11) + 0.5) * 2.0 ** -53
+            u2 = (splitmix64(seed, 2 * c + 1) >> 11) * 2.0 ** -53
+            om[a, j] = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return om
+
+
+def _orth_by_gram(Y: np.ndarray, tol: float) -> np.ndarray:
+    """Orthonormal basis of range(Y) from the eigendecomposition of Y^T Y:
+    Q = Y V Lambda^{-1/2}; directions with sqrt(lambda_j) <= tol sqrt(lambda_max)
+    are dropped (zero columns)."""
+    C = Y.T @ Y
+    lam, V = np.linalg.eigh(C)
+    Q = np.zeros_like(Y)
+    top = np.sqrt(max(lam.max(), 0.0))
+    for j in range(lam.size):
+        sj = np.sqrt(max(lam[j], 0.0))
+        if top > 0.0 and sj > tol * top:
+            Q[:, j] = (Y @ V[:, j]) / sj
+    return Q
+
+
+def randomized_truncation(X: np.ndarray, r: int, ell: int, q: int, seed: int, rank_tol: float,
+                          orth_tol: float = 1e-7):
+    """Rank-r truncation of X (n_i x k) by randomized subspace iteration on
+    its right singular subspace (the HMT proto-algorithm with q power passes
+    and ell = r + oversampling columns, applied to G = X^T X):
+      Y = G Omega;  q times: Q = orth(Y), Y = G Q;  Q = orth(Y);
+      H = Q^T G Q = W Theta W^T (Rayleigh-Ritz);  V_r = Q W[:, top r];
+      sigma_j = sqrt(theta_j).
+    With ell = k the basis Q spans everything and the result is the exact
+    truncated SVD.  Returns (U, sig, Vt, all Ritz values) like truncated_svd,
+    with U = X V_r / sigma (the left factor) and the rank guard of
+    truncated_svd."""
+    k = X.shape[1]
+    G = X.T @ X
+    Y = G @ gaussian_sketch(k, ell, seed)
+    for _ in range(q):
+        Y = G @ _orth_by_gram(Y, orth_tol)
+    Q = _orth_by_gram(Y, orth_tol)
+    th, Wm = np.linalg.eigh(Q.T @ G @ Q)
+    order = np.argsort(-th, kind="stable")
+    th = np.maximum(th[order], 0.0)
+    sv = np.sqrt(th)
+    U, sig, V = np.zeros((X.shape[0], r)), np.zeros(r), np.zeros((r, k))
+    for j in range(min(r, sv.size)):
+        if sv[0] > 0.0 and sv[j] > rank_tol * sv[0]:
+            v = Q @ Wm[:, order[j]]
+            U[:, j], sig[j], V[j, :] = (X @ v) / sv[j], sv[j], v
+    return U, sig, V, sv
+
+
+def sketch_seed(base: int, part: int, side: int) -> int:
+    """Seed of the sketch of partition `part`'s right (side 0) or left
+    (side 1) spike."""
+    return (base + 2 * part + side) & _M64
+
+
+SKETCH_SEED = 0x4C52535049
+WIDE_K = 64   # bands with k > WIDE_K are truncated by the randomized SVD
+
+
 def truncated_svd(X: np.ndarray, r: int, rank_tol: float):
     """Rank-r truncated SVD X ~ U diag(sig) Vt, the 'low-rank SVD' of section 3.1.
 
@@ -225,7 +317,8 @@ class Factor:
 
 def factor(ab: np.ndarray, k: int, p: int, r: int, compress: str = "spike",
            reduced: str = "full", pivoting: bool = False, rank_tol: float = 1e-13,
-           threads: int = 1) -> Factor:
+           threads: int = 1, randomized: Optional[bool] = None, oversample: Optional[int] = None,
+           power_iters: int = 2, seed: int = SKETCH_SEED, orth_tol: float = 1e-7) -> Factor:
     """LR-SPIKE factorisation of the banded A (FP64).
 
     compress: "spike" (truncated SVD of the explicit spikes, section 3.1) or
@@ -235,6 +328,10 @@ def factor(ab: np.ndarray, k: int, p: int, r: int, compress: str = "spike",
               per-interface diagonal blocks only, LR-SPIKE-T).
     pivoting: partial pivoting inside each partition (rows never cross
               partitions); B_i and C_i are taken from the unpivoted A.
+    randomized: truncate the explicit spikes with randomized_truncation
+              (default: when k > WIDE_K), ell = min(k, r + oversample)
+              (oversample defaults to r), power_iters passes, sketch seeds
+              sketch_seed(seed, i, side).
     """
     ab = np.ascontiguousarray(ab, dtype=np.float64)
     n = ab.shape[1]
@@ -248,6 +345,16 @@ def factor(ab: np.ndarray, k: int, p: int, r: int, compress: str = "spike",
     if compress not in ("spike", "coupling") or reduced not in ("full", "truncated"):
         raise ValueError("bad mode")
 
+    if randomized is None:
+        randomized = k > WIDE_K
+    ell = min(k, r + (r if oversample is None else oversample))
+
+    def trunc(X, i, side):
+        if randomized and compress == "spike":
+            return randomized_truncation(X, r, ell, power_iters, sketch_seed(seed, i, side), rank_tol,
+                                         orth_tol)
+        return truncated_svd(X, r, rank_tol)
+
     def one(i):
         s, m = int(offs[i]), int(sizes[i])
         lu = BandLU(partition_band(ab, k, s, m), k, pivoting)
@@ -257,7 +364,7 @@ def factor(ab: np.ndarray, k: int, p: int, r: int, compress: str = "spike",
             rhs = np.zeros((m, k))
             if compress == "spike":
                 rhs[m - k:, :] = B
-                U, sig, Vt, sv = truncated_svd(lu.solve(rhs), r, rank_tol)
+                U, sig, Vt, sv = trunc(lu.solve(rhs), i, 0)
                 out[1], out[2], out[5] = U, sig[:, None] * Vt, sv
             else:
                 Ub, sig, Vt, sv = truncated_svd(B, r, rank_tol)
@@ -269,7 +376,7 @@ def factor(ab: np.ndarray, k: int, p: int, r: int, compress: str = "spike",
             if compress == "spike":
                 rhs = np.zeros((m, k))
                 rhs[:k, :] = C
-                U, sig, Vt, sv = truncated_svd(lu.solve(rhs), r, rank_tol)
+                U, sig, Vt, sv = trunc(lu.solve(rhs), i, 1)
                 out[3], out[4], out[6] = U, sig[:, None] * Vt, sv
             else:
                 Uc, sig, Vt, sv = truncated_svd(C, r, rank_tol)
