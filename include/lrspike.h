@@ -91,6 +91,14 @@ typedef struct {
                              (default 1e-13 FP64, 1e-6 mixed)                        */
     int32_t max_nrhs;     /* largest nrhs a solve may pass (default 16)              */
     int32_t profile;      /* 1 = time every kernel with CUDA events (see below)     */
+    /* Wide bands (k > 64) truncate the spikes with the randomized SVD the paper
+     * uses (section 3.1, Halko-Martinsson-Tropp): ell = min(k, r + oversample)
+     * sketch columns (ell <= 64), power_iters passes, Gaussian sketches from
+     * SplitMix64 + Box-Muller at counter a*ell + j with seed + 2 i + side
+     * (partition i, side 0 = T_i, 1 = W_i).  Ignored for k <= 64 (exact SVD). */
+    int32_t oversample;   /* default r                                               */
+    int32_t power_iters;  /* default 2                                               */
+    uint64_t seed;        /* default 0x4C52535049                                    */
 } lrspike_options;
 
 typedef struct {
@@ -108,7 +116,11 @@ lrspike_status lrspike_options_default(lrspike_options *opt, int64_t n, int32_t 
 /* Validates *opt, allocates every device workspace the handle needs (sized by
  * n, k, p, r, precision and max_nrhs) and returns the handle in *out.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream), borrowed.
- * Errors: INVALID_ARG (n < 1, k < 0 or k > 64, r < 0 or r > k, p < 1,
+ * k <= 64 uses blocks of KB in {8, 16, 32, 64} >= k and the hand-written
+ * block kernels; 64 < k <= 1024 (wide bands) uses blocks of W = 64 ceil(k/64)
+ * whose products are batched GEMMs (cuBLAS: FP64, FP32, or TF32 tensor cores
+ * with LRSPIKE_MIXED_TF32), SPIKE compression, no pivoting, r <= 32.
+ * Errors: INVALID_ARG (n < 1, k < 0 or k > 1024, r < 0 or r > k, p < 1,
  * n_i <= k with p > 1, max_nrhs < 1, unknown enum), UNSUPPORTED, OOM, CUDA. */
 lrspike_status lrspike_create(const lrspike_options *opt, void *cuda_stream, lrspike_handle *out);
 

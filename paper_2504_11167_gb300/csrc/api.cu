@@ -15,7 +15,8 @@ const char *const kKernelNames[KID_COUNT] = {
     "band_lu",      "spike_rhs",   "spike_sweep", "gram",
     "gram_reduce",  "coupling_gram", "jacobi",      "make_u",      "reduced_build",
     "reduced_factor", "norm",        "residual",    "dstage",      "reduced_solve",
-    "retrieve",     "project_t",     "dstage_t",    "bicgstab_vector", "matvec"};
+    "retrieve",     "project_t",     "dstage_t",    "bicgstab_vector", "matvec",
+    "wide_gather",  "wide_gemm",     "wide_lu64",   "wide_vector", "nonzero_diagonals"};
 
 static cudaEvent_t take_event(Ctx *c) {
     if (!c->free_events.empty()) {
@@ -105,6 +106,7 @@ static void free_all(Ctx *c) {
         if (p) cudaFree(p);
     for (double *p : c->bv)
         if (p) cudaFree(p);
+    wide_free(c);
     if (c->host) cudaFreeHost(c->host);
     for (auto &pd : c->pending) {
         cudaEventDestroy(pd.a);
@@ -131,6 +133,9 @@ extern "C" lrspike_status lrspike_options_default(lrspike_options *o, int64_t n,
     o->rank_tol = 1e-13;
     o->max_nrhs = 16;
     o->profile = 0;
+    o->oversample = r;
+    o->power_iters = 2;
+    o->seed = 0x4C52535049ull;
     return LRSPIKE_OK;
 }
 
@@ -139,7 +144,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     *out = nullptr;
     const lrspike_options &o = *opt;
     if (o.n < 1) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "n must be >= 1");
-    if (o.k < 0 || o.k > 64) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "k must be in 0..64");
+    if (o.k < 0 || o.k > 1024) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "k must be in 0..1024");
     if (o.p < 1 || o.p > o.n) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "p must be in 1..n");
     if (o.r < 0 || o.r > o.k) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "r must be in 0..k");
     if (o.max_nrhs < 1 || o.max_nrhs > 16)
@@ -149,8 +154,15 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "unknown enum value in options");
     if (o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rank_tol >= 0.0))
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "max_iter, tol and rank_tol must be >= 0");
-    if (o.precision == LRSPIKE_MIXED_TF32)
-        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "TF32 tensor-core factorisation is not built yet");
+    const bool wide = o.k > 64;
+    if (o.precision == LRSPIKE_MIXED_TF32 && !wide)
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "TF32 tensor-core updates are built for k > 64 only");
+    if (wide && (o.pivoting || o.compress != LRSPIKE_COMPRESS_SPIKE))
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "k > 64 supports SPIKE compression without pivoting");
+    if (wide && (o.oversample < 0 || o.power_iters < 0))
+        return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "oversample and power_iters must be >= 0");
+    if (wide && o.p > 1 && o.r > 0 && std::min(o.k, o.r + o.oversample) > 64)
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "min(k, r + oversample) > 64 sketch columns is not built");
     if (o.r > 32) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "r > 32 is not built yet");
 
     Ctx *c = new (std::nothrow) Ctx();
@@ -164,6 +176,8 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     c->r = (o.p > 1) ? o.r : 0;  // one partition has no spikes and no reduced system
     c->KB = 8;
     while (c->KB < o.k) c->KB *= 2;
+    c->wide = wide;
+    if (wide) c->KB = 64 * ((o.k + 63) / 64);  // W, the wide-band block size
     c->fp64 = (o.precision == LRSPIKE_FP64);
     c->tsize = c->fp64 ? 8 : 4;
     c->profile = o.profile != 0;
@@ -191,6 +205,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     // spike panel columns: a multiple of 16 (the register-tiled sweep's column
     // groups); T_i in the first half, W_i in the second half
     c->m = spikes ? (o.compress == LRSPIKE_COMPRESS_COUPLING ? 16 * ((2 * c->r + 15) / 16) : 2 * c->KB) : 0;
+    if (wide) c->m = 0;
     if (c->m == 48) c->m = 64;  // column groups of 1, 2, 4 or 8
     c->gram_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(32, minnb));
     const size_t T = c->tsize, KB = c->KB, NB = c->NB, mx = o.max_nrhs;
@@ -198,17 +213,18 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     const int64_t rb = (c->n + 255) / 256;
     const bool piv = o.pivoting != 0;
     bool ok = dalloc(&c->off_d, (c->p + 1) * 8) && dalloc(&c->boff_d, (c->p + 1) * 8) &&
-              (piv ? dalloc(&c->PF, NB * 5 * KB * KB * T) && dalloc(&c->PIVP, NB * 2 * KB)
-                   : dalloc(&c->LT, NB * KB * KB * T) && dalloc(&c->UT, NB * KB * KB * T) &&
-                         dalloc(&c->DI, NB * KB * T)) &&
+              (wide ? true
+               : piv ? dalloc(&c->PF, NB * 5 * KB * KB * T) && dalloc(&c->PIVP, NB * 2 * KB)
+                     : dalloc(&c->LT, NB * KB * KB * T) && dalloc(&c->UT, NB * KB * KB * T) &&
+                           dalloc(&c->DI, NB * KB * T)) &&
               dalloc(&c->rv, (size_t)c->n * mx * 8) && dalloc(&c->Yv, (size_t)c->n * mx * T) &&
               dalloc(&c->Gv, (size_t)c->n * mx * T) && dalloc(&c->nrm, 4 * mx * 8) &&
               dalloc(&c->partial, (size_t)rb * mx * 8) && dalloc(&c->counter, 64) && dalloc(&c->status, 64);
     if (ok && spikes) {
-        ok = dalloc(&c->X, NB * KB * c->m * T) && dalloc(&c->Ucat, (size_t)c->n * n2 * T) &&
-             dalloc(&c->PQ, (size_t)c->p * 2 * c->r * KB * T) &&
-             dalloc(&c->Gram, (size_t)c->p * 2 * KB * KB * 8) &&
-             dalloc(&c->Gpart, (size_t)c->p * c->gram_chunks * 2 * KB * KB * 8) &&
+        ok = (wide ? true
+                   : dalloc(&c->X, NB * KB * c->m * T) && dalloc(&c->Gram, (size_t)c->p * 2 * KB * KB * 8) &&
+                         dalloc(&c->Gpart, (size_t)c->p * c->gram_chunks * 2 * KB * KB * 8)) &&
+             dalloc(&c->Ucat, (size_t)c->n * n2 * T) && dalloc(&c->PQ, (size_t)c->p * 2 * c->r * KB * T) &&
              dalloc(&c->sigma, (size_t)c->p * 2 * c->r * 8) && dalloc(&c->E, ni * n2 * n2 * 8) &&
              dalloc(&c->F, ni * n2 * n2 * 8) && dalloc(&c->Gs, ni * n2 * n2 * 8) &&
              dalloc(&c->Rinv, ni * n2 * n2 * 8) && dalloc(&c->Gam, ni * n2 * n2 * 8) &&
@@ -216,6 +232,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
              dalloc(&c->wr, ni * n2 * mx * 8);
     }
     if (ok && o.outer == LRSPIKE_OUTER_BICGSTAB) ok = bicgstab_alloc(c);
+    if (ok && wide) ok = wide_setup(c);
     if (ok) ok = cudaMallocHost((void **)&c->host, (8 * mx + 8) * 8) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -271,8 +288,8 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
     if (cudaMemcpyAsync(c->status, c->host, 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return cuda_fail(c, "status reset");
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "stream sync");
-    bool ok = run_band_lu(c);
-    if (ok && c->p > 1 && c->r > 0) {
+    bool ok = c->wide ? run_wide_factor(c) : run_band_lu(c);
+    if (ok && !c->wide && c->p > 1 && c->r > 0) {
         if (c->opt.compress == LRSPIKE_COMPRESS_COUPLING)
             ok = run_coupling_gram(c) && run_jacobi(c) && run_spike_rhs(c) && run_sweep(c) && run_make_u(c);
         else

@@ -169,7 +169,7 @@ template <int NR, int MODE>
 __global__ void __launch_bounds__(VBS)
     k_bicg_mv(const double *__restrict__ band, int64_t ldb, int k, int64_t n, int trans,
               const double *__restrict__ u, double *__restrict__ y, const double *__restrict__ w, int nrhs,
-              int mx, double *sc, double *partial, unsigned *counter) {
+              int mx, double *sc, double *partial, unsigned *counter, const int *__restrict__ dlist, int ndl) {
     constexpr int NV = (MODE == 0) ? NR : 2 * NR;
     double dv[NV];
 #pragma unroll
@@ -179,7 +179,11 @@ __global__ void __launch_bounds__(VBS)
 #pragma unroll
         for (int q = 0; q < NR; ++q) acc[q] = 0.0;
         const int t0 = (int)max((int64_t)0, k - i), t1 = (int)min((int64_t)2 * k, n - 1 - i + k);
-        for (int t = t0; t <= t1; ++t) {
+        // with a list of the band rows that hold nonzeros only those are visited
+        const int nt = dlist ? ndl : t1 - t0 + 1;
+        for (int it = 0; it < nt; ++it) {
+            const int t = dlist ? (trans ? dlist[it] : 2 * k - dlist[it]) : t0 + it;
+            if (t < t0 || t > t1) continue;
             const int64_t j = i - k + t;
             // A[i][j] = band[(k+i-j) ldb + j];  A^T[i][j] = A[j][i] = band[(k+j-i) ldb + i]
             const double a = trans ? band[(int64_t)t * ldb + i] : band[(int64_t)(2 * k - t) * ldb + j];
@@ -325,7 +329,7 @@ static bool bicg_iteration(Ctx *c, unsigned g, int nrhs, bool trans, double *xd,
     if (!apply_precond(c, pv, ph, n, nrhs, trans, false)) return false;
     if (!launch(c, KID_MATVEC, [&] {
             k_bicg_mv<NR, 0><<<g, VBS, 0, c->stream>>>(c->band, c->ld, c->k, n, tr, ph, vv, rh, nrhs, mx, sc, part,
-                                                       c->counter);
+                                                       c->counter, c->diag_list, c->ndiag);
         }))
         return false;
     if (!launch(c, KID_VEC, [&] {
@@ -335,7 +339,7 @@ static bool bicg_iteration(Ctx *c, unsigned g, int nrhs, bool trans, double *xd,
     if (!apply_precond(c, sv, sh, n, nrhs, trans, false)) return false;
     if (!launch(c, KID_MATVEC, [&] {
             k_bicg_mv<NR, 1><<<g, VBS, 0, c->stream>>>(c->band, c->ld, c->k, n, tr, sh, tv, sv, nrhs, mx, sc, part,
-                                                       c->counter);
+                                                       c->counter, c->diag_list, c->ndiag);
         }))
         return false;
     return launch(c, KID_VEC, [&] {

@@ -418,6 +418,54 @@ static bool lu_kb(Ctx *c) {
     }
 }
 
+// Wide bands: batched LU with both triangular inverses of one 64 x 64
+// diagonal sub-block per partition (the base case of the recursive block
+// factorisation).  A, Li, Ui are column-major views (leading dimension lda /
+// ldo, one matrix per partition at stride sA / sO); A is overwritten.
+// grow0 of partition i = P.off[i] + row0 (the global row of the sub-block).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_lu_inv64(T *A, int lda, int64_t sA, T *Li, T *Ui, int ldo, int64_t sO, Parts P, int64_t row0,
+               int64_t *status) {
+    constexpr int N = 64, NT = 256, LD = N + Pad<T>::v;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Sb = reinterpret_cast<T *>(smem_raw), *Ls = Sb + N * LD, *Us = Ls + N * LD;
+    const int part = blockIdx.x;
+    T *a = A + part * sA;
+    for (int e = threadIdx.x; e < N * N; e += NT) {
+        const int r = e % N, c = e / N;  // column-major source: consecutive threads, consecutive rows
+        Sb[r * LD + c] = a[(int64_t)c * lda + r];
+    }
+    __syncthreads();
+    lu_inv<T, N, NT>(Sb, Ls, Us, LD, P.off[part] + row0, status);
+    T *li = Li + part * sO, *ui = Ui + part * sO;
+    for (int e = threadIdx.x; e < N * N; e += NT) {
+        const int r = e % N, c = e / N;
+        li[(int64_t)c * ldo + r] = Ls[r * LD + c];
+        ui[(int64_t)c * ldo + r] = Us[r * LD + c];
+    }
+}
+
+bool run_lu_inv64(Ctx *c, void *A, int lda, int64_t sA, void *Li, void *Ui, int ldo, int64_t sO, int64_t row0) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    if (c->fp64) {
+        constexpr int LD = 64 + Pad<double>::v;
+        const size_t smem = 3 * 64 * LD * sizeof(double);
+        cudaFuncSetAttribute(k_lu_inv64<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return launch(c, KID_WIDE_LU64, [&] {
+            k_lu_inv64<double><<<c->p, 256, smem, c->stream>>>((double *)A, lda, sA, (double *)Li, (double *)Ui,
+                                                              ldo, sO, P, row0, c->status);
+        });
+    }
+    constexpr int LD = 64 + Pad<float>::v;
+    const size_t smem = 3 * 64 * LD * sizeof(float);
+    cudaFuncSetAttribute(k_lu_inv64<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch(c, KID_WIDE_LU64, [&] {
+        k_lu_inv64<float><<<c->p, 256, smem, c->stream>>>((float *)A, lda, sA, (float *)Li, (float *)Ui, ldo, sO,
+                                                         P, row0, c->status);
+    });
+}
+
 bool run_band_lu(Ctx *c) {
     if (c->opt.pivoting) return run_band_lu_piv(c);
     return c->fp64 ? lu_kb<double>(c) : lu_kb<float>(c);

@@ -544,6 +544,31 @@ static bool jacobi_impl(Ctx *c) {
     });
 }
 
+// Eigendecompositions of nmat symmetric n x n FP64 matrices (n in {16, 32,
+// 64}; G row-major, one per CTA): the rout leading eigenvectors as rows of
+// `out` (stride n), sqrt(eigenvalue) in sigma, the rank guard of k_jacobi.
+template <typename T, int KB>
+static bool jacobi_batch_kb(Ctx *c, const double *G, int nmat, int rout, double rank_tol, void *out, double *sigma) {
+    const size_t smem = 2 * KB * (KB + 1) * sizeof(T);
+    auto kern = k_jacobi<T, KB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch(c, KID_JACOBI, [&] {
+        kern<<<nmat, Geo<KB>::NT, smem, c->stream>>>(G, rout, rank_tol, c->fp64 ? 30 : 20, (T *)out, sigma);
+    });
+}
+
+bool run_jacobi_batch(Ctx *c, int n, const double *G, int nmat, int rout, double rank_tol, void *out,
+                      double *sigma) {
+    if (c->fp64) {
+        if (n == 16) return jacobi_batch_kb<double, 16>(c, G, nmat, rout, rank_tol, out, sigma);
+        if (n == 32) return jacobi_batch_kb<double, 32>(c, G, nmat, rout, rank_tol, out, sigma);
+        return jacobi_batch_kb<double, 64>(c, G, nmat, rout, rank_tol, out, sigma);
+    }
+    if (n == 16) return jacobi_batch_kb<float, 16>(c, G, nmat, rout, rank_tol, out, sigma);
+    if (n == 32) return jacobi_batch_kb<float, 32>(c, G, nmat, rout, rank_tol, out, sigma);
+    return jacobi_batch_kb<float, 64>(c, G, nmat, rout, rank_tol, out, sigma);
+}
+
 template <typename T, int KB, int UC>
 static bool make_u_uc(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};

@@ -30,6 +30,11 @@ enum KernelId {
     KID_DSTAGE_T,
     KID_VEC,
     KID_MATVEC,
+    KID_WIDE_GATHER,
+    KID_WIDE_GEMM,
+    KID_WIDE_LU64,
+    KID_WIDE_VEC,
+    KID_DIAGS,
     KID_COUNT
 };
 
@@ -93,6 +98,24 @@ struct Ctx {
     double *dots = nullptr;
     double *bpartial = nullptr;
 
+    // wide bands (k > 64): blocks of W = 64 ceil(k/64), block products as
+    // batched GEMMs; every partition padded to NBW blocks (PS = NBW W rows)
+    bool wide = false;
+    int W = 0, NBW = 0, ell = 0, lp = 0;
+    int64_t PS = 0;
+    void *blas = nullptr;                                                 // cublasHandle_t
+    void *WLi = nullptr, *WUi = nullptr, *WZ = nullptr, *WY = nullptr;   // [p][NBW][W x W]
+    void *WS = nullptr, *WB = nullptr, *WC = nullptr, *WT = nullptr;     // [p][W x W] work
+    void *WX1 = nullptr, *WX2 = nullptr;   // spike panels [p][PS x 2W]
+    void *WG = nullptr;                    // [2p][W x W] Gram matrices of the spikes
+    void *WOm = nullptr, *WYk = nullptr, *WQk = nullptr, *WTk = nullptr;  // [2p][W x lp]
+    void *WH = nullptr, *WE = nullptr;     // [2p][lp x lp]
+    double *WHd = nullptr, *Wsg = nullptr; // [2p][lp x lp] FP64 copy, [2p][lp]
+    void *WV1 = nullptr, *WV2 = nullptr;   // vector panels [p][PS x 16]
+    void **Wptr = nullptr;                 // device pointer arrays of the grouped GEMMs
+    int *diag_list = nullptr;              // band rows holding a nonzero (residual), or NULL
+    int ndiag = 0;
+
     const double *band = nullptr;
     int64_t ld = 0;
     double *band_own = nullptr;
@@ -144,6 +167,16 @@ bool run_reduced_solve(Ctx *c, int nrhs, bool trans);
 bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs, bool accumulate);
 bool run_project_t(Ctx *c, const double *hin, int64_t ld, int nrhs);
 bool run_dstage_t(Ctx *c, const double *hin, int64_t ldh, double *x, int64_t ldx, int nrhs, bool accumulate);
+// wide bands (wide.cu)
+bool wide_setup(Ctx *c);
+void wide_free(Ctx *c);
+bool run_wide_factor(Ctx *c);
+bool run_wide_dstage(Ctx *c, const double *rin, int nrhs);
+bool run_wide_dstage_t(Ctx *c, const double *hin, double *x, int64_t ldx, int nrhs, bool accumulate);
+bool run_lu_inv64(Ctx *c, void *A, int lda, int64_t sA, void *Li, void *Ui, int ldo, int64_t sO, int64_t row0);
+bool run_jacobi_batch(Ctx *c, int n, const double *G, int nmat, int rout, double rank_tol, void *out,
+                      double *sigma);
+bool run_reduced_build_ld(Ctx *c, int ldpq);
 // partial pivoting inside the partitions (pivot.cu)
 bool run_band_lu_piv(Ctx *c);
 bool run_sweep_piv(Ctx *c);

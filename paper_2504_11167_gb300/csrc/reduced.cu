@@ -18,8 +18,8 @@
 
 namespace lrs {
 
-template <typename T, int KB>
-__global__ void k_red_build(const T *__restrict__ PQ, const T *__restrict__ Ucat, Parts P, int k,
+template <typename T>
+__global__ void k_red_build(const T *__restrict__ PQ, int KB, const T *__restrict__ Ucat, Parts P, int k,
                             int r, double *__restrict__ E, double *__restrict__ F,
                             double *__restrict__ Gs) {
     const int i = blockIdx.x;
@@ -246,32 +246,22 @@ __global__ void k_red_solve_full(const double *__restrict__ Rinv, const double *
     }
 }
 
-template <typename T, int KB>
-static bool build_impl(Ctx *c) {
+// ldpq: row stride of the projections P_i, Q_i (the block size)
+template <typename T>
+static bool build_impl(Ctx *c, int ldpq) {
     Parts P{c->off_d, c->boff_d, c->p};
     return launch(c, KID_RED_BUILD, [&] {
-        k_red_build<T, KB><<<c->p - 1, 256, 0, c->stream>>>((const T *)c->PQ, (const T *)c->Ucat, P,
-                                                             c->k, c->r, c->E, c->F, c->Gs);
+        k_red_build<T><<<c->p - 1, 256, 0, c->stream>>>((const T *)c->PQ, ldpq, (const T *)c->Ucat, P, c->k,
+                                                        c->r, c->E, c->F, c->Gs);
     });
 }
 
-bool run_reduced_build(Ctx *c) {
+bool run_reduced_build_ld(Ctx *c, int ldpq) {
     if (c->p < 2 || c->r == 0) return true;
-    if (c->fp64) {
-        switch (c->KB) {
-            case 8: return build_impl<double, 8>(c);
-            case 16: return build_impl<double, 16>(c);
-            case 32: return build_impl<double, 32>(c);
-            default: return build_impl<double, 64>(c);
-        }
-    }
-    switch (c->KB) {
-        case 8: return build_impl<float, 8>(c);
-        case 16: return build_impl<float, 16>(c);
-        case 32: return build_impl<float, 32>(c);
-        default: return build_impl<float, 64>(c);
-    }
+    return c->fp64 ? build_impl<double>(c, ldpq) : build_impl<float>(c, ldpq);
 }
+
+bool run_reduced_build(Ctx *c) { return run_reduced_build_ld(c, c->KB); }
 
 bool run_reduced_factor(Ctx *c) {
     if (c->p < 2 || c->r == 0) return true;

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(RBS)
     k_residual(const double *__restrict__ band, int64_t ldb, int k, int64_t n,
                const double *__restrict__ f, const double *__restrict__ x, int64_t ld, int nrhs,
                int trans, int xzero, double *__restrict__ r, double *partial, unsigned *counter,
-               double *nrm_out, double *inv_out) {
+               double *nrm_out, double *inv_out, const int *__restrict__ dlist, int ndl) {
     const int64_t i = blockIdx.x * (int64_t)RBS + threadIdx.x;
     double acc[NR], ss[NR];
 #pragma unroll
@@ -81,7 +81,11 @@ __global__ void __launch_bounds__(RBS)
         for (int c = 0; c < NR; ++c)
             if (c < nrhs) acc[c] = f[c * ld + i];
         if (!xzero) {
-            for (int t = 0; t <= 2 * k; ++t) {
+            // t = j - i + k; with a list of the band rows that hold nonzeros
+            // (row d = 2k - t of A, row t of A^T) only those are visited
+            const int nt = dlist ? ndl : 2 * k + 1;
+            for (int u = 0; u < nt; ++u) {
+                const int t = dlist ? (trans ? dlist[u] : 2 * k - dlist[u]) : u;
                 const int64_t j = i - k + t;
                 if (j < 0 || j >= n) continue;
                 // A[i][j] = band[(k+i-j) ld + j];  A^T[i][j] = A[j][i] = band[(k+j-i) ld + i]
@@ -419,7 +423,7 @@ static bool residual_nr(Ctx *c, const double *f, const double *x, int64_t ld, in
     return launch(c, KID_RESIDUAL, [&] {
         k_residual<NR><<<row_blocks(c->n), RBS, 0, c->stream>>>(
             c->band, c->ld, c->k, c->n, f, x, ld, nrhs, trans, xz, c->rv, c->partial, c->counter,
-            c->nrm + c->opt.max_nrhs, c->nrm + 2 * c->opt.max_nrhs);
+            c->nrm + c->opt.max_nrhs, c->nrm + 2 * c->opt.max_nrhs, c->diag_list, c->ndiag);
     });
 }
 
@@ -430,11 +434,11 @@ bool launch_residual_raw(const double *band, int64_t ldb, int k, int64_t n, cons
                          unsigned *counter, double *nrm, cudaStream_t st) {
     const unsigned g = row_blocks(n);
     switch (nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16) {
-        case 1: k_residual<1><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
-        case 2: k_residual<2><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
-        case 4: k_residual<4><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
-        case 8: k_residual<8><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
-        default: k_residual<16><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr); break;
+        case 1: k_residual<1><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
+        case 2: k_residual<2><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
+        case 4: k_residual<4><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
+        case 8: k_residual<8><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
+        default: k_residual<16><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
     }
     return cudaGetLastError() == cudaSuccess;
 }
@@ -514,6 +518,7 @@ static bool project_t_impl(Ctx *c, const double *hin, int nrhs) {
 }
 
 bool run_dstage(Ctx *c, const double *rin, int64_t, int nrhs) {
+    if (c->wide) return run_wide_dstage(c, rin, nrhs);
     if (c->opt.pivoting) return run_dstage_piv(c, rin, nrhs);
     if (c->fp64) {
         switch (c->KB) {
@@ -532,6 +537,7 @@ bool run_dstage(Ctx *c, const double *rin, int64_t, int nrhs) {
 }
 
 bool run_dstage_t(Ctx *c, const double *hin, int64_t, double *x, int64_t ldx, int nrhs, bool accumulate) {
+    if (c->wide) return run_wide_dstage_t(c, hin, x, ldx, nrhs, accumulate);
     if (c->opt.pivoting) return run_dstage_t_piv(c, hin, x, ldx, nrhs, accumulate);
     const int acc = accumulate ? 1 : 0;
     if (c->fp64) {

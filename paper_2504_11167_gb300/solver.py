@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("r", ctypes.c_int32), ("precision", ctypes.c_int32), ("pivoting", ctypes.c_int32),
                 ("compress", ctypes.c_int32), ("reduced", ctypes.c_int32), ("outer", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double),
-                ("max_nrhs", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("max_nrhs", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("oversample", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 class Info(ctypes.Structure):

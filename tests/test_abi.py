@@ -43,9 +43,26 @@ def test_defaults(lib):
     assert o.precision == 0 and o.compress == 0 and o.reduced == 0 and o.outer == 0
     assert o.tol == 1e-12 and o.max_iter == 50 and o.max_nrhs == 16
     assert lib.lrspike_options_default(None, 1, 1, 1, 1) == 1
+    assert (o.oversample, o.power_iters, o.seed) == (2, 2, 0x4C52535049)
 
 
-@pytest.mark.parametrize("field,value", [("k", 65), ("k", -1), ("r", 9), ("r", -1), ("p", 0),
+@pytest.mark.parametrize("changes", [
+    dict(precision=2),                                     # TF32 needs the wide-band path (k > 64)
+    dict(n=20000, k=100, r=8, pivoting=1),                 # wide bands: no pivoting
+    dict(n=20000, k=100, r=8, compress=1),                 # wide bands: SPIKE compression only
+    dict(n=20000, k=100, r=8, oversample=60),              # more than 64 sketch columns
+    dict(n=20000, k=100, r=33),                            # r > 32
+])
+def test_create_reports_unbuilt_combinations(lib, changes):
+    o = _opts(lib, n=changes.pop("n", 1000), k=changes.pop("k", 8), p=4, r=changes.pop("r", 2))
+    for f, v in changes.items():
+        setattr(o, f, v)
+    h = ctypes.c_void_p()
+    assert lib.lrspike_create(ctypes.byref(o), None, ctypes.byref(h)) == 7
+    assert not h.value
+
+
+@pytest.mark.parametrize("field,value", [("k", 1025), ("k", -1), ("r", 9), ("r", -1), ("p", 0),
                                          ("n", 0), ("max_nrhs", 0), ("max_nrhs", 17),
                                          ("precision", 7), ("outer", 5), ("compress", 2)])
 def test_create_rejects_bad_options(lib, field, value):
