@@ -16,7 +16,10 @@ dominant kernel, and the CPU oracle timed on a bounded sample.
 
 Also on the same band: the weakly dominant variant (diagonal rescaled to
 dominance 0.6) with partial pivoting inside the partitions, reported under
-"variants".
+"variants"; and the sparse-in-band PDE configuration: 2-D convection-diffusion
+on a 1024 x 1024 grid (n = 1,048,576, half-bandwidth 1024, cell Peclet number
+0.5), p = 64, r = 16, 4 right-hand sides, TF32 tensor-core factors with FP64
+BiCGStab to 1e-10 (iterative refinement stalls on it).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        python bench.py --profile-case   (one factor + solve at n = 1,048,576,
@@ -181,6 +184,64 @@ def kernel_work(name: str, prof: dict, precision_bytes: int):
     return None, None
 
 
+def cd_band_device(nx: int, peclet: float, dev):
+    """The convection-diffusion band of inputs.convection_diffusion_band,
+    built on the device (the FP64 band of the 1024^2 grid is 17 GB)."""
+    import torch
+    n, k = nx * nx, nx
+    ab = torch.zeros(2 * k + 1, n, dtype=torch.float64, device=dev)
+    i = torch.arange(n, device=dev)
+    x, y = i % nx, i // nx
+    ab[k, :] = 4.0
+    w = i[x > 0]
+    ab[k + 1, w - 1] = -(1.0 + peclet)
+    e = i[x < nx - 1]
+    ab[k - 1, e + 1] = -(1.0 - peclet)
+    s = i[y > 0]
+    ab[2 * k, s - nx] = -(1.0 + peclet)
+    nn = i[y < nx - 1]
+    ab[0, nn + nx] = -(1.0 - peclet)
+    return ab
+
+
+def cd_variant(steps: int, warmup: int, dev):
+    """Steps of factor + BiCGStab solve on the convection-diffusion workload."""
+    import torch
+    from paper_2504_11167_gb300 import inputs
+    from paper_2504_11167_gb300.solver import LRSpike
+    small = cd_band_device(12, 0.5, dev).cpu().numpy()
+    assert np.array_equal(small, inputs.convection_diffusion_band(12, 0.5))
+    nx, p, r, nrhs = 1024, 64, 16, 4
+    n, k = nx * nx, nx
+    band = cd_band_device(nx, 0.5, dev)
+    f = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, nrhs, inputs.SEED_BASE + 3).T)).to(dev)
+    s = LRSpike(n, k, p, r, precision="tf32", reduced="truncated", outer="bicgstab", tol=TOL, max_iter=200,
+                max_nrhs=nrhs, profile=True)
+    for _ in range(warmup):
+        s.factor(band)
+        s.solve(f)
+    s.profile_reset()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        s.factor(band)
+        x, info = s.solve(f)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    prof = s.profile()
+    s.close()
+    del band, f
+    torch.cuda.empty_cache()
+    return {"value": n * nrhs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "iterations": info["iterations"],
+            "rel_residual": info["max_rel_residual"],
+            "config": {"workload": "2-D convection-diffusion 1024x1024, Pe 0.5", "n": n, "k": k, "p": p, "r": r,
+                       "nrhs": nrhs, "precision": "tf32", "outer": "bicgstab", "reduced": "truncated", "tol": TOL},
+            "kernels": {k_: {"launches": c_, "ms_total": round(t_, 3)} for k_, (c_, t_) in prof.items() if c_}}
+
+
 def profile_case():
     """One factor + solve on a quarter-size case (n = 1,048,576, p = 64, same
     k, r, dominance and n_i): small enough for ncu replays, inputs still larger
@@ -328,6 +389,7 @@ def main():
             "pivoting": "partial, inside each partition",
             "kernels": {k_: {"launches": c_, "ms_total": round(t_, 4)} for k_, (c_, t_) in profv.items() if c_}}}
         torch.cuda.empty_cache()
+        variants["convection_diffusion_k1024"] = cd_variant(2, 1, dev)
 
     # end to end through the C ABI with host buffers
     e2e = None
