@@ -209,6 +209,23 @@ lrspike_status lrspike_residual_noalloc(const double *band, int64_t ld_band, int
                                         const double *f, const double *x, double *r, int32_t nrhs,
                                         int64_t ld, double *norms, void *cuda_stream);
 
+/* ---- gradient of the band ------------------------------------------------
+ * For x = A^{-1} f and a loss L(x), the adjoint solve A^T lambda = dL/dx
+ * (lrspike_solve_transpose with the stored factors) gives dL/df = lambda and
+ * dL/dA = -lambda x^T; only the entries inside the band are parameters of A.
+ * This entry point writes that band-restricted outer product:
+ *   grad_band[(k + i - j) ld_band + j] = alpha * sum_q lam_q[i] x_q[j]
+ * for every |i - j| <= k inside the matrix (alpha = -1 gives dL/dA), and 0 at
+ * the band positions outside the matrix.  lam, x: device, n x nrhs
+ * column-major, leading dimension ld >= n; grad_band: device, (2k+1) x
+ * ld_band, ld_band >= n.  1 <= nrhs <= 16, 0 <= k <= 1024.  Enqueued on
+ * cuda_stream (NULL = legacy default stream); no allocation, no handle.
+ * Errors (INVALID_ARG for NULL, host pointers or bad sizes, CUDA) are
+ * described by lrspike_last_error(NULL). */
+lrspike_status lrspike_band_outer(const double *lam, const double *x, int32_t nrhs, int64_t ld, int64_t n,
+                                  int32_t k, double alpha, double *grad_band, int64_t ld_band,
+                                  void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

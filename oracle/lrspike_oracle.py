@@ -600,3 +600,32 @@ def bicgstab(ab, k, fac: Factor, f: np.ndarray, tol: float = 1e-12, max_iter: in
         its = max(its, it)
         ok = ok and rel <= tol
     return SolveResult(X.reshape(f.shape), its, np.array(rels), [], ok)
+
+
+# --------------------------------------------------------------------------
+# Gradient of a solve (the adjoint): x = A^{-1} f, L(x);  A^T lambda = dL/dx,
+# dL/df = lambda, dL/dA = -lambda x^T (band entries only)
+# --------------------------------------------------------------------------
+def solve_gradients(ab: np.ndarray, k: int, f: np.ndarray, gx_of_x):
+    """Exact x = A^{-1} f (LAPACK banded solve), lambda = A^{-T} gx_of_x(x),
+    and the band gradient G[k + i - j, j] = -sum_q lambda[i, q] x[j, q]
+    (zero outside the matrix).  f: (n,) or (n, nrhs)."""
+    n = ab.shape[1]
+    F = f.reshape(n, -1)
+    x = scipy.linalg.solve_banded((k, k), ab, F)
+    abT = np.zeros_like(ab)                 # band of A^T: A^T[i][j] = A[j][i]
+    for d in range(2 * k + 1):
+        off = d - k                         # A[j + off, j] = ab[d, j]  ->  A^T[j, j + off]
+        for j in range(n):
+            i = j + off
+            if 0 <= i < n:
+                abT[k + j - i, i] = ab[d, j]
+    lam = scipy.linalg.solve_banded((k, k), abT, np.asarray(gx_of_x(x.reshape(f.shape))).reshape(n, -1))
+    G = np.zeros_like(ab)
+    for d in range(2 * k + 1):
+        for j in range(n):
+            i = j + d - k
+            if 0 <= i < n:
+                G[d, j] = -np.dot(lam[i, :], x[j, :])
+    return x.reshape(f.shape), lam.reshape(f.shape), G
+

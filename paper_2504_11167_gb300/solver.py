@@ -54,7 +54,7 @@ _lib = None
 EXPORTS = ["lrspike_options_default", "lrspike_create", "lrspike_factor", "lrspike_solve",
            "lrspike_solve_transpose", "lrspike_destroy", "lrspike_last_error",
            "lrspike_launch_count", "lrspike_profile_get", "lrspike_profile_reset",
-           "lrspike_get_reduced", "lrspike_residual_noalloc"]
+           "lrspike_get_reduced", "lrspike_residual_noalloc", "lrspike_band_outer"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -87,6 +87,9 @@ def load_library(path: str = LIB_PATH):
                                              ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                                              ctypes.c_void_p, ctypes.c_void_p]
+    lib.lrspike_band_outer.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_void_p]
     for name in EXPORTS:
         if name not in ("lrspike_last_error", "lrspike_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
@@ -116,6 +119,26 @@ def residual_noalloc(band, k: int, f, x, r, norms, stream=None) -> None:
                                       ctypes.c_void_p(_ptr(r)), nrhs, ld,
                                       ctypes.c_void_p(_ptr(norms)),
                                       ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise LRSpikeError(st, lib.lrspike_last_error(None).decode(errors="replace"))
+
+
+def band_outer(lam, x, k: int, alpha: float, grad_band, stream=None) -> None:
+    """grad_band[k + i - j, j] = alpha * sum_q lam[q, i] x[q, j] on the band
+    (0 outside the matrix): with alpha = -1 the band part of dL/dA = -lam x^T.
+    lam, x: device (nrhs, ld) or (n,); grad_band: device (2k+1, ld_band)."""
+    import torch
+    lib = load_library()
+    L = lam.unsqueeze(0) if lam.dim() == 1 else lam
+    X = x.unsqueeze(0) if x.dim() == 1 else x
+    assert L.shape == X.shape and L.is_contiguous() and X.is_contiguous() and grad_band.is_contiguous()
+    nrhs, ld = L.shape
+    n = grad_band.shape[1] if grad_band.shape[1] <= ld else ld
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = lib.lrspike_band_outer(ctypes.c_void_p(_ptr(L)), ctypes.c_void_p(_ptr(X)), nrhs, ld, n, k, alpha,
+                                ctypes.c_void_p(_ptr(grad_band)), grad_band.shape[1],
+                                ctypes.c_void_p(stream.cuda_stream))
     if st != 0:
         raise LRSpikeError(st, lib.lrspike_last_error(None).decode(errors="replace"))
 
