@@ -99,6 +99,16 @@ typedef struct {
     int32_t oversample;   /* default r                                               */
     int32_t power_iters;  /* default 2                                               */
     uint64_t seed;        /* default 0x4C52535049                                    */
+    /* graph_safe = 1: factor and solve only enqueue work on the handle's stream
+     * (no host synchronisation, no host reads, no allocation), so a caller can
+     * capture them in a CUDA graph and replay it.  The solve then runs exactly
+     * max_iter refinement steps (IR; NONE is one application) and leaves the
+     * final residual on the device; lrspike_finish reports the outcome.
+     * Requires device buffers, outer IR or NONE, profile 0, k <= 64. */
+    int32_t graph_safe;
+    /* block: the block size KB (8, 16, 32 or 64, >= the smallest block that
+     * holds k; 0 = that smallest block).  A tuning knob for k <= 64. */
+    int32_t block;
 } lrspike_options;
 
 typedef struct {
@@ -148,6 +158,13 @@ lrspike_status lrspike_solve(lrspike_handle h, const double *f, double *x, int32
  * transpose of M^{-1} = (I - U R^{-1} V) D^{-1}.  Arguments as lrspike_solve. */
 lrspike_status lrspike_solve_transpose(lrspike_handle hd, const double *h, double *lambda,
                                        int32_t nrhs, int64_t ld, lrspike_info *info);
+
+/* For a graph_safe handle: waits for the handle's stream and reports the last
+ * factorisation (SINGULAR as lrspike_factor would) and the last solve (info as
+ * lrspike_solve fills it: iterations = max_iter, the per-column relative
+ * residual of the final iterate; NOT_CONVERGED if a column is above tol).
+ * STATE if nothing was solved since the last factor. */
+lrspike_status lrspike_finish(lrspike_handle h, lrspike_info *info);
 
 /* Releases the handle and every buffer it owns.  NULL is accepted. */
 lrspike_status lrspike_destroy(lrspike_handle h);

@@ -136,6 +136,8 @@ extern "C" lrspike_status lrspike_options_default(lrspike_options *o, int64_t n,
     o->oversample = r;
     o->power_iters = 2;
     o->seed = 0x4C52535049ull;
+    o->graph_safe = 0;
+    o->block = 0;
     return LRSPIKE_OK;
 }
 
@@ -155,6 +157,12 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     if (o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rank_tol >= 0.0))
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "max_iter, tol and rank_tol must be >= 0");
     const bool wide = o.k > 64;
+    if (o.graph_safe && (o.outer == LRSPIKE_OUTER_BICGSTAB || wide))
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "graph_safe supports outer IR or NONE with k <= 64");
+    if (o.graph_safe && o.profile)
+        return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "graph_safe handles cannot profile (no host reads)");
+    if (o.block != 0 && (wide || (o.block != 8 && o.block != 16 && o.block != 32 && o.block != 64) || o.block < o.k))
+        return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "block must be 8, 16, 32 or 64 and >= k (k <= 64)");
     if (o.precision == LRSPIKE_MIXED_TF32 && !wide)
         return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "TF32 tensor-core updates are built for k > 64 only");
     if (wide && (o.pivoting || o.compress != LRSPIKE_COMPRESS_SPIKE))
@@ -178,6 +186,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     while (c->KB < o.k) c->KB *= 2;
     c->wide = wide;
     if (wide) c->KB = 64 * ((o.k + 63) / 64);  // W, the wide-band block size
+    if (o.block > c->KB) c->KB = o.block;
     c->fp64 = (o.precision == LRSPIKE_FP64);
     c->tsize = c->fp64 ? 8 : 4;
     c->profile = o.profile != 0;
@@ -261,6 +270,8 @@ static lrspike_status cuda_fail(Ctx *c, const char *what) {
     return fail(c, LRSPIKE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+__global__ void k_set_status(int64_t *s, int64_t v) { *s = v; }
+
 extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, int64_t ld) {
     Ctx *c = ctx(h);
     if (!c) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "NULL handle");
@@ -268,7 +279,8 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
     if (!band || ld < c->n) return fail(c, LRSPIKE_ERR_INVALID_ARG, "band is NULL or ld < n");
     cudaSetDevice(c->device);
     c->factored = false;
-    if (is_device_ptr(band)) {
+    const bool gs = c->opt.graph_safe != 0;  // enqueue only: no host reads, no synchronisation
+    if (gs || is_device_ptr(band)) {
         c->band = band;
     } else {
         const size_t bytes = (size_t)(2 * c->k + 1) * ld * 8;
@@ -284,10 +296,15 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
         c->band = c->band_own;
     }
     c->ld = ld;
-    *(int64_t *)c->host = kNoStatus;
-    if (cudaMemcpyAsync(c->status, c->host, 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
-        return cuda_fail(c, "status reset");
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "stream sync");
+    if (gs) {
+        k_set_status<<<1, 1, 0, c->stream>>>(c->status, kNoStatus);
+        if (cudaGetLastError() != cudaSuccess) return cuda_fail(c, "status reset");
+    } else {
+        *(int64_t *)c->host = kNoStatus;
+        if (cudaMemcpyAsync(c->status, c->host, 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return cuda_fail(c, "status reset");
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "stream sync");
+    }
     bool ok = c->wide ? run_wide_factor(c) : run_band_lu(c);
     if (ok && !c->wide && c->p > 1 && c->r > 0) {
         if (c->opt.compress == LRSPIKE_COMPRESS_COUPLING)
@@ -297,6 +314,11 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
         ok = ok && run_reduced_build(c) && run_reduced_factor(c);
     }
     if (!ok) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+    if (gs) {  // the status is read by lrspike_finish
+        c->factored = true;
+        c->last_nrhs = 0;
+        return LRSPIKE_OK;
+    }
     if (cudaMemcpyAsync(c->host, c->status, 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return cuda_fail(c, "factorisation");
@@ -322,6 +344,26 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
     if ((const char *)x < (const char *)f + span && (const char *)f < (const char *)x + span)
         return fail(c, LRSPIKE_ERR_INVALID_ARG, "x must not alias f");
     cudaSetDevice(c->device);
+    if (c->opt.graph_safe) {
+        // device buffers; exactly max_iter refinement steps (NONE: one application);
+        // the final residual stays on the device for lrspike_finish
+        const bool none = c->opt.outer == LRSPIKE_OUTER_NONE;
+        const int steps = none ? 1 : c->opt.max_iter;
+        if (cudaMemset2DAsync(x, ld * 8, 0, c->n * 8, nrhs, c->stream) != cudaSuccess) return cuda_fail(c, "x reset");
+        if (!run_norms(c, f, ld, nrhs, c->nrm)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        for (int it = 0; it < steps; ++it)
+            if (!run_residual(c, f, x, ld, nrhs, trans, it == 0) ||
+                !apply_precond(c, c->rv, x, ld, nrhs, trans, true))
+                return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        if (!run_residual(c, f, x, ld, nrhs, trans, false)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        c->last_nrhs = nrhs;
+        if (info) {
+            info->iterations = steps;
+            info->converged = 0;
+            info->max_rel_residual = NAN;
+        }
+        return LRSPIKE_OK;
+    }
     const bool fdev = is_device_ptr(f), xdev = is_device_ptr(x);
     if (fdev != xdev) return fail(c, LRSPIKE_ERR_INVALID_ARG, "f and x must both be device or both host");
     const double *fd = f;
@@ -435,6 +477,50 @@ extern "C" lrspike_status lrspike_solve(lrspike_handle h, const double *f, doubl
 extern "C" lrspike_status lrspike_solve_transpose(lrspike_handle h, const double *hv, double *lam, int32_t nrhs,
                                                   int64_t ld, lrspike_info *info) {
     return solve_common(ctx(h), hv, lam, nrhs, ld, info, true);
+}
+
+extern "C" lrspike_status lrspike_finish(lrspike_handle h, lrspike_info *info) {
+    Ctx *c = ctx(h);
+    if (!c) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "NULL handle");
+    c->err.clear();
+    if (!c->opt.graph_safe) return fail(c, LRSPIKE_ERR_STATE, "lrspike_finish is for graph_safe handles");
+    cudaSetDevice(c->device);
+    int64_t st = kNoStatus;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+        cudaMemcpy(&st, c->status, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(c, "finish");
+    if (st == kReducedSingular) return fail(c, LRSPIKE_ERR_SINGULAR, "singular reduced system block");
+    if (st != kNoStatus) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "zero or non-finite pivot at global row %lld", (long long)st);
+        return fail(c, LRSPIKE_ERR_SINGULAR, buf);
+    }
+    const int nrhs = c->last_nrhs, mx = c->opt.max_nrhs;
+    if (nrhs == 0) return fail(c, LRSPIKE_ERR_STATE, "no solve since the last factor");
+    std::vector<double> nf(nrhs), nr(nrhs);
+    if (cudaMemcpy(nf.data(), c->nrm, nrhs * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nr.data(), c->nrm + mx, nrhs * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(c, "residual read");
+    double worst = 0.0;
+    bool ok = true;
+    for (int q = 0; q < nrhs; ++q) {
+        const double rel = (nf[q] > 0.0) ? nr[q] / nf[q] : 0.0;
+        if (info && info->rel_residual) info->rel_residual[q] = rel;
+        ok = ok && rel <= c->opt.tol;
+        worst = std::max(worst, (rel == rel) ? rel : INFINITY);
+    }
+    const int steps = c->opt.outer == LRSPIKE_OUTER_NONE ? 1 : c->opt.max_iter;
+    if (info) {
+        info->iterations = steps;
+        info->converged = ok ? 1 : 0;
+        info->max_rel_residual = worst;
+    }
+    if (!ok) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "worst relative residual %.3e after %d steps", worst, steps);
+        return fail(c, LRSPIKE_ERR_NOT_CONVERGED, buf);
+    }
+    return LRSPIKE_OK;
 }
 
 extern "C" lrspike_status lrspike_destroy(lrspike_handle h) {

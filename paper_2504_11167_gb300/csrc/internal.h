@@ -123,6 +123,7 @@ struct Ctx {
     double *io_f = nullptr, *io_x = nullptr;  // device copies for host-pointer solves
     size_t io_bytes = 0;
     bool factored = false;
+    int last_nrhs = 0;        // graph_safe: columns of the last enqueued solve
 
     std::string err;
     int64_t launches = 0;

@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("compress", ctypes.c_int32), ("reduced", ctypes.c_int32), ("outer", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double),
                 ("max_nrhs", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("oversample", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("oversample", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("graph_safe", ctypes.c_int32), ("block", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -54,7 +55,7 @@ _lib = None
 EXPORTS = ["lrspike_options_default", "lrspike_create", "lrspike_factor", "lrspike_solve",
            "lrspike_solve_transpose", "lrspike_destroy", "lrspike_last_error",
            "lrspike_launch_count", "lrspike_profile_get", "lrspike_profile_reset",
-           "lrspike_get_reduced", "lrspike_residual_noalloc", "lrspike_band_outer"]
+           "lrspike_get_reduced", "lrspike_residual_noalloc", "lrspike_band_outer", "lrspike_finish"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -74,6 +75,7 @@ def load_library(path: str = LIB_PATH):
     lib.lrspike_solve.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                                   ctypes.POINTER(Info)]
     lib.lrspike_solve_transpose.argtypes = lib.lrspike_solve.argtypes
+    lib.lrspike_finish.argtypes = [H, ctypes.POINTER(Info)]
     lib.lrspike_destroy.argtypes = [H]
     lib.lrspike_last_error.argtypes = [H]
     lib.lrspike_last_error.restype = ctypes.c_char_p
@@ -150,7 +152,8 @@ class LRSpike:
                  compress: str = "spike", reduced: str = "full", outer: str = "ir",
                  pivoting: bool = False, tol: Optional[float] = None, max_iter: int = 50,
                  rank_tol: Optional[float] = None, max_nrhs: int = 16, profile: bool = False,
-                 stream=None):
+                 stream=None, graph_safe: bool = False, block: int = 0, oversample: Optional[int] = None,
+                 power_iters: int = 2):
         import torch
         self._lib = load_library()
         o = Options()
@@ -165,6 +168,11 @@ class LRSpike:
         o.rank_tol = rank_tol if rank_tol is not None else (1e-13 if precision == "fp64" else 1e-6)
         o.max_nrhs = max_nrhs
         o.profile = int(bool(profile))
+        o.graph_safe = int(bool(graph_safe))
+        o.block = block
+        if oversample is not None:
+            o.oversample = oversample
+        o.power_iters = power_iters
         self.opt = o
         self.n, self.k, self.p, self.r = n, k, p, r
         if stream is None and torch.cuda.is_available():
@@ -235,6 +243,18 @@ class LRSpike:
     def solve_transpose(self, h, x=None, allow_unconverged=False):
         """lambda = A^{-T} h (or M^{-T} h with outer='none'); returns (lambda, info)."""
         return self._solve(self._lib.lrspike_solve_transpose, h, x, allow_unconverged)
+
+    def finish(self, nrhs: int = 16, allow_unconverged: bool = False) -> dict:
+        """graph_safe handles: wait for the enqueued work and report the last
+        factorisation and solve (raises on SINGULAR, and on NOT_CONVERGED
+        unless allowed)."""
+        rel = (ctypes.c_double * nrhs)()
+        info = Info(0, 0, 0.0, ctypes.cast(rel, ctypes.POINTER(ctypes.c_double)))
+        st = self._lib.lrspike_finish(self._h, ctypes.byref(info))
+        if st != 0 and not (allow_unconverged and st == 6):
+            self._check(st, self._h)
+        return {"iterations": info.iterations, "converged": bool(info.converged),
+                "max_rel_residual": info.max_rel_residual, "rel_residual": list(rel)}
 
     def launch_count(self) -> int:
         return int(self._lib.lrspike_launch_count(self._h))
