@@ -19,7 +19,10 @@ dominance 0.6) with partial pivoting inside the partitions, reported under
 "variants"; and the sparse-in-band PDE configuration: 2-D convection-diffusion
 on a 1024 x 1024 grid (n = 1,048,576, half-bandwidth 1024, cell Peclet number
 0.5), p = 64, r = 16, 4 right-hand sides, TF32 tensor-core factors with FP64
-BiCGStab to 1e-10 (iterative refinement stalls on it).
+BiCGStab to 1e-10 (iterative refinement stalls on it); and 512 independent
+systems of uneven n (log-uniform in [4096, 262144]) and k (8, 16, 32, 64),
+r = k/4, dominance 1.5, solved by one CUDA-graph launch with default and with
+autotuned partition / block shapes.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        python bench.py --profile-case   (one factor + solve at n = 1,048,576,
@@ -242,6 +245,68 @@ def cd_variant(steps: int, warmup: int, dev):
             "kernels": {k_: {"launches": c_, "ms_total": round(t_, 3)} for k_, (c_, t_) in prof.items() if c_}}
 
 
+def batch_variant(dev, systems_count=512, steps=3, iterations=10):
+    """One CUDA-graph launch over `systems_count` uneven systems; default
+    shapes versus autotuned shapes (throughput = all systems' unknowns / replay
+    time, CUDA events around the replays)."""
+    import torch
+    from paper_2504_11167_gb300 import batch, inputs
+    rng = np.random.default_rng(inputs.SEED_BASE + 4)
+    systems = []
+    for i in range(systems_count):
+        n = int(round(np.exp(rng.uniform(np.log(4096), np.log(262144)))))
+        k = int(rng.choice([8, 16, 32, 64]))
+        band = inputs.dominant_band_torch(n, k, 1.5, inputs.SEED_BASE + 5000 + i, device=dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(inputs.SEED_BASE + 9000 + i)
+        f = torch.rand(1, n, generator=g, dtype=torch.float64, device=dev) * 2.0 - 1.0
+        systems.append((band, f, k))
+    total = sum(b.shape[1] for b, _, _ in systems)
+
+    def timed(shapes):
+        b = batch.BatchSolver(systems, shapes=shapes, iterations=iterations, streams=32)
+        b.capture()
+        b.replay()
+        b.finish(allow_unconverged=True)                # warm replay
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize(dev)
+        e0.record(cur)
+        for _ in range(steps):
+            b.replay()
+        e1.record(cur)
+        torch.cuda.synchronize(dev)
+        infos = b.finish(allow_unconverged=True)
+        ms = e0.elapsed_time(e1) / steps
+        worst = max(x["max_rel_residual"] for x in infos)
+        unconverged = sum(1 for x in infos if not x["converged"])
+        used = list(b.shapes)
+        b.close()
+        return ms, (worst, unconverged), used
+
+    ms_def, worst_def, shapes_def = timed(None)
+    classes = {}
+    for band, f, k in systems:
+        classes.setdefault((k, batch.size_class(band.shape[1])), (band, f))
+    best = batch.autotune(classes, iterations=iterations, reps=2)
+    tuned = [best[(k, batch.size_class(b.shape[1]))] for b, _, k in systems]
+    ms_tun, worst_tun, _ = timed(tuned)
+    changed = sum(1 for a, b_ in zip(shapes_def, tuned) if a != b_)
+    del systems
+    torch.cuda.empty_cache()
+    return {"value": total / (ms_tun * 1e-3), "unit": UNIT, "ms_per_step": ms_tun,
+            "default_shapes": {"value": total / (ms_def * 1e-3), "ms_per_step": ms_def,
+                               "max_rel_residual": worst_def[0], "unconverged_systems": worst_def[1]},
+            "autotuned_shapes": {"value": total / (ms_tun * 1e-3), "ms_per_step": ms_tun,
+                                 "max_rel_residual": worst_tun[0], "unconverged_systems": worst_tun[1],
+                                 "classes": len(best),
+                                 "systems_with_changed_shape": changed},
+            "config": {"workload": f"{systems_count} banded systems, n log-uniform [4096, 262144], "
+                                   "k in {8,16,32,64}, r = k/4, dominance 1.5",
+                       "unknowns": total, "precision": "fp32", "refinement_steps": iterations,
+                       "graph": "one CUDA graph per batch (factor + solve of every system)"}}
+
+
 def profile_case():
     """One factor + solve on a quarter-size case (n = 1,048,576, p = 64, same
     k, r, dominance and n_i): small enough for ncu replays, inputs still larger
@@ -390,6 +455,7 @@ def main():
             "kernels": {k_: {"launches": c_, "ms_total": round(t_, 4)} for k_, (c_, t_) in profv.items() if c_}}}
         torch.cuda.empty_cache()
         variants["convection_diffusion_k1024"] = cd_variant(2, 1, dev)
+        variants["batched_512_uneven_systems"] = batch_variant(dev)
 
     # end to end through the C ABI with host buffers
     e2e = None

@@ -53,6 +53,28 @@ def dominant_band(n: int, k: int, dom: float, seed: int) -> np.ndarray:
     return ab
 
 
+def dominant_band_torch(n: int, k: int, dom: float, seed: int, device="cuda"):
+    """The recipe of dominant_band drawn with torch's generator on `device`
+    (for workloads whose bands are too large to build on the host): entries
+    uniform[-1, 1] inside the matrix, 0 outside, diagonal dom * (sum of
+    |off-diagonals| of its row).  Not the same numbers as dominant_band."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    ab = torch.rand(2 * k + 1, n, generator=g, dtype=torch.float64, device=device) * 2.0 - 1.0
+    j = torch.arange(n, device=device)
+    rows = torch.zeros(n, dtype=torch.float64, device=device)
+    for d in range(2 * k + 1):
+        i = j + d - k                        # A[i, j] = ab[d, j]
+        inside = (i >= 0) & (i < n)
+        ab[d] = torch.where(inside, ab[d], torch.zeros_like(ab[d]))
+        if d != k:
+            lo, hi = max(0, k - d), min(n, n + k - d)
+            rows[lo + d - k:hi + d - k] += ab[d, lo:hi].abs()
+    ab[k] = dom * rows
+    return ab
+
+
 def rhs(n: int, nrhs: int, seed: int) -> np.ndarray:
     """Right-hand sides uniform[-1, 1], drawn from stream seed + 1; returned
     column-major (n x nrhs, Fortran order) so column q starts at q * n."""

@@ -24,3 +24,22 @@ def test_candidates_respect_partition_and_block_rules():
 def test_size_classes_are_power_of_two_intervals():
     assert batch.size_class(4096) == batch.size_class(8191) == 12
     assert batch.size_class(8192) == 13
+
+
+def test_device_band_generator_follows_the_recipe():
+    import numpy as np
+    import torch
+    from paper_2504_11167_gb300 import inputs
+    n, k, dom = 300, 7, 1.5
+    ab = inputs.dominant_band_torch(n, k, dom, 3, device="cpu").numpy()
+    for d in range(2 * k + 1):
+        for j in (0, 1, n - 2, n - 1, 150):
+            i = j + d - k
+            if not 0 <= i < n:
+                assert ab[d, j] == 0.0
+            elif d != k:
+                assert -1.0 <= ab[d, j] <= 1.0
+    off = inputs.off_diagonal_row_sums(np.where(np.arange(2 * k + 1)[:, None] == k, 0.0, ab), k)
+    assert np.allclose(ab[k], dom * off, rtol=1e-14, atol=0)
+    b2 = inputs.dominant_band_torch(n, k, dom, 3, device="cpu").numpy()
+    assert np.array_equal(ab, b2)
