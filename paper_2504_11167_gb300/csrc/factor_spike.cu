@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(4 * KB)
     k_gram(const T *__restrict__ X, Parts P, int chunks, double *__restrict__ Gpart) {
     constexpr int NT = 4 * KB, M = 2 * KB, GC = (KB >= 8) ? KB / 8 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Xs = reinterpret_cast<T *>(smem_raw);  // KB x M
+    T *Xs = reinterpret_cast<T *>(smem_raw);  // [2][KB x M]
     const int part = blockIdx.y, ch = blockIdx.x;
     const int64_t b0 = P.boff[part];
     const int nb = (int)(P.boff[part + 1] - b0);
@@ -224,14 +224,24 @@ __global__ void __launch_bounds__(4 * KB)
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < GC; ++j) acc[i][j] = T(0);
-    for (int J = J0; J < J1; ++J) {
+    // double buffer: block J+1 is copied (cp.async) while block J is multiplied
+    constexpr int CH = 16 / (int)sizeof(T);
+    auto stage = [&](int J, T *dst) {
         const T *src = X + (b0 + J) * (int64_t)KB * M;
-        for (int e = threadIdx.x; e < KB * M; e += NT) Xs[e] = src[e];
+        for (int e = threadIdx.x; e < KB * M / CH; e += NT) cp_async16(dst + e * CH, src + e * CH);
+    };
+    if (J0 < J1) stage(J0, Xs);
+    cp_async_commit();
+    for (int J = J0; J < J1; ++J) {
+        T *cur = Xs + ((J - J0) & 1) * KB * M;
+        if (J + 1 < J1) stage(J + 1, Xs + ((J + 1 - J0) & 1) * KB * M);
+        cp_async_commit();
+        cp_async_wait1();
         __syncthreads();
         for (int q = 0; q < KB; ++q) {
             T av[4], bv[GC];
-            ld_row<T, 4>(Xs + q * M + off + a0, av);
-            ld_row<T, GC>(Xs + q * M + off + b0c, bv);
+            ld_row<T, 4>(cur + q * M + off + a0, av);
+            ld_row<T, GC>(cur + q * M + off + b0c, bv);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -422,9 +432,21 @@ __global__ void __launch_bounds__(4 * KB)
         for (int e = threadIdx.x; e < n2 * KB; e += NT)
             Ps[(e % KB) * n2 + e / KB] = PQ[(int64_t)part * n2 * KB + e];
     const int a0 = 4 * (threadIdx.x / 16), cb = UC * (threadIdx.x % 16);
-    for (int J = J0; J < J1; ++J) {
+    // the halves of the panel this thread's columns read (T for col < r, W after)
+    const bool needT = cb < r, needW = cb + UC > r && cb < n2;
+    constexpr int CH = 16 / (int)sizeof(T);
+    T *Xs1 = Ps + KB * n2;  // second staged block (after the projections)
+    auto stage = [&](int J, T *dst) {
         const T *src = X + (b0 + J) * (int64_t)KB * m;
-        for (int e = threadIdx.x; e < KB * m; e += NT) Xs[e] = src[e];
+        for (int e = threadIdx.x; e < KB * m / CH; e += NT) cp_async16(dst + e * CH, src + e * CH);
+    };
+    if (J0 < J1) stage(J0, Xs);
+    cp_async_commit();
+    for (int J = J0; J < J1; ++J) {
+        T *cur = ((J - J0) & 1) ? Xs1 : Xs;
+        if (J + 1 < J1) stage(J + 1, ((J + 1 - J0) & 1) ? Xs1 : Xs);
+        cp_async_commit();
+        cp_async_wait1();
         __syncthreads();
         T acc[4][UC];
 #pragma unroll
@@ -433,23 +455,26 @@ __global__ void __launch_bounds__(4 * KB)
             for (int u = 0; u < UC; ++u) {
                 const int col = cb + u;
                 const int xcol = (col < r) ? col : half + (col - r);   // coupling: panel column
-                acc[i][u] = (coupling && col < n2) ? Xs[(a0 + i) * m + xcol] : T(0);
+                acc[i][u] = (coupling && col < n2) ? cur[(a0 + i) * m + xcol] : T(0);
             }
         if (!coupling) {
-            for (int j = 0; j < KB; ++j) {
-                T xv[4], xw[4];
+            for (int j = 0; j < KB; j += 4) {
+                T xv[4][4], xw[4][4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    xv[i] = Xs[(a0 + i) * m + j];
-                    xw[i] = Xs[(a0 + i) * m + KB + j];
+                    if (needT) ld_row<T, 4>(cur + (a0 + i) * m + j, xv[i]);
+                    if (needW) ld_row<T, 4>(cur + (a0 + i) * m + KB + j, xw[i]);
                 }
 #pragma unroll
                 for (int u = 0; u < UC; ++u) {
                     const int col = cb + u;
                     if (col < n2) {
-                        const T pv = Ps[j * n2 + col];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) acc[i][u] += ((col < r) ? xv[i] : xw[i]) * pv;
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const T pv = Ps[(j + jj) * n2 + col];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) acc[i][u] += ((col < r) ? xv[i][jj] : xw[i][jj]) * pv;
+                        }
                     }
                 }
             }
@@ -511,7 +536,7 @@ template <typename T, int KB>
 static bool gram_impl(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
     dim3 grid(c->gram_chunks, c->p);
-    const size_t smem = (size_t)KB * 2 * KB * sizeof(T);
+    const size_t smem = (size_t)2 * KB * 2 * KB * sizeof(T);  // two staged blocks
     auto kern = k_gram<T, KB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (!launch(c, KID_GRAM, [&] {
@@ -572,7 +597,7 @@ bool run_jacobi_batch(Ctx *c, int n, const double *G, int nmat, int rout, double
 template <typename T, int KB, int UC>
 static bool make_u_uc(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
-    const size_t smem = (KB * c->m + 2 * c->r * KB) * sizeof(T);
+    const size_t smem = (2 * KB * c->m + 2 * c->r * KB) * sizeof(T);  // two staged blocks + projections
     auto kern = k_make_u<T, KB, UC>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(c->gram_chunks, c->p);

@@ -276,6 +276,47 @@ __global__ void __launch_bounds__(RBS)
     }
 }
 
+// One right-hand side: zeta and omega of the partition (2r <= NQ values) sit
+// in registers and every thread streams RPT rows (the shared-memory reads of
+// the general kernel made it issue-bound).  Same arithmetic order.
+template <typename T, int NQ>
+__global__ void __launch_bounds__(RBS)
+    k_retrieve1(const T *__restrict__ Gv, const T *__restrict__ Ucat, const double *__restrict__ zr, Parts P,
+                int r, int64_t n, const double *__restrict__ nrm, double *__restrict__ x, int accumulate) {
+    const int part = blockIdx.y;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int n2 = 2 * r;
+    T z[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        double v = 0.0;
+        if (j < r) { if (part <= P.p - 2) v = zr[(int64_t)part * n2 + j]; }
+        else if (j < n2 && part >= 1) v = zr[(int64_t)(part - 1) * n2 + j];
+        z[j] = (T)v;
+    }
+    const double sc = nrm[0];
+    const bool vec = (sizeof(T) == 4) && (n2 % 4 == 0);
+    for (int64_t row = blockIdx.x * (int64_t)RBS + threadIdx.x; row < ni; row += (int64_t)gridDim.x * RBS) {
+        const int64_t gi = s + row;
+        T d = Gv[gi];
+        const T *u = Ucat + gi * n2;
+        if (vec) {
+#pragma unroll
+            for (int j = 0; j < NQ; j += 4)
+                if (j < n2) {
+                    const float4 v = *reinterpret_cast<const float4 *>(u + j);
+                    d -= v.x * z[j] + v.y * z[j + 1] + v.z * z[j + 2] + v.w * z[j + 3];
+                }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NQ; ++j)
+                if (j < n2) d -= u[j] * z[j];
+        }
+        const double upd = sc * (double)d;
+        x[gi] = accumulate ? x[gi] + upd : upd;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a = U^T h per partition: alpha_i = u_{T,i}^T h_i -> interface i, rows 0..r-1;
 // beta_i = u_{W,i}^T h_i -> interface i-1, rows r..2r-1.
@@ -496,8 +537,26 @@ static bool dstage_t_impl(Ctx *c, const double *hin, double *x, int64_t ldx, int
     });
 }
 
+template <typename T, int NQ>
+static bool retrieve1_nq(Ctx *c, double *x, int acc) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    constexpr int RPT = 8;  // rows per thread
+    dim3 grid((unsigned)((c->maxni + RBS * RPT - 1) / (RBS * RPT)), c->p);
+    return launch(c, KID_RETRIEVE, [&] {
+        k_retrieve1<T, NQ><<<grid, RBS, 0, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r, c->n,
+                                                        c->nrm + c->opt.max_nrhs, x, acc);
+    });
+}
+
 template <typename T>
 static bool retrieve_impl(Ctx *c, double *x, int64_t ld, int nrhs, int acc) {
+    if (nrhs == 1) {
+        const int n2 = 2 * c->r;
+        if (n2 <= 8) return retrieve1_nq<T, 8>(c, x, acc);
+        if (n2 <= 16) return retrieve1_nq<T, 16>(c, x, acc);
+        if (n2 <= 32) return retrieve1_nq<T, 32>(c, x, acc);
+        return retrieve1_nq<T, 64>(c, x, acc);
+    }
     Parts P{c->off_d, c->boff_d, c->p};
     dim3 grid(row_blocks(c->maxni), c->p);
     const size_t smem = (size_t)(2 * c->r * nrhs + 1) * sizeof(double);
