@@ -68,6 +68,8 @@ CASES = [
     (70, 16, 4, 3, 1.5, "spike", "full", 1),            # n_i = 17/18 just above k
     (260, 33, 3, 5, 1.4, "coupling", "full", 2),        # k not a block size
     (50000, 8, 16, 4, 1.5, "spike", "truncated", 16),   # many blocks, widest nrhs
+    (5000, 24, 4, 6, 1.3, "coupling", "full", 1),       # KB = 32, one column: warp D-stage
+    (9000, 40, 3, 10, 1.2, "spike", "truncated", 1),    # KB = 64, one column: warp D-stage
 ]
 
 
@@ -193,3 +195,20 @@ def test_config1_full_size_fp64(torch_cuda):
         x, info, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced=reduced, tol=1e-12)
         res = np.asarray(f) - O.band_matvec(ab, k, x)
         assert np.linalg.norm(res) / np.linalg.norm(f) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-10)])
+@pytest.mark.parametrize("compress", ["spike", "coupling"])
+def test_single_column_solves_k64(torch_cuda, precision, tol, compress):
+    """One right-hand side with 64-row blocks (the one-warp-per-partition
+    D-stage): the IR solve reaches tol and matches LAPACK's banded solve."""
+    n, k, p, r = 40000, 64, 8, 16
+    ab = inputs.dominant_band(n, k, 1.1, 19)
+    f = inputs.rhs(n, 1, 19)[:, 0]
+    x, info, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced="truncated", precision=precision, tol=tol,
+                           compress=compress)
+    assert info["converged"]
+    res = f - O.band_matvec(ab, k, x)
+    assert np.linalg.norm(res) / np.linalg.norm(f) <= tol * 1.01
+    xs = scipy.linalg.solve_banded((k, k), ab, f)
+    assert rel(x, xs) <= 1e3 * tol
