@@ -53,7 +53,9 @@ typedef enum {
 
 /* Working precision of the preconditioner (factors, spikes, D-stage,
  * retrieval).  The residual f - A x, the reduced system and the solution
- * update are always FP64. */
+ * update are always FP64.  MIXED_TF32: as MIXED_FP32 with the block products
+ * of the band LU on the tensor cores (TF32 operands, FP32 accumulation; the
+ * triangular base blocks stay FP32); for k > 64 every block GEMM. */
 enum { LRSPIKE_FP64 = 0, LRSPIKE_MIXED_FP32 = 1, LRSPIKE_MIXED_TF32 = 2 };
 /* Compression of the spikes (section 3.1): SPIKE = truncated SVD of the
  * explicit spikes T_i, W_i (the paper's choice, optimal by Eckart-Young);

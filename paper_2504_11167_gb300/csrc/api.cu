@@ -163,8 +163,6 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "graph_safe handles cannot profile (no host reads)");
     if (o.block != 0 && (wide || (o.block != 8 && o.block != 16 && o.block != 32 && o.block != 64) || o.block < o.k))
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "block must be 8, 16, 32 or 64 and >= k (k <= 64)");
-    if (o.precision == LRSPIKE_MIXED_TF32 && !wide)
-        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "TF32 tensor-core updates are built for k > 64 only");
     if (wide && (o.pivoting || o.compress != LRSPIKE_COMPRESS_SPIKE))
         return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "k > 64 supports SPIKE compression without pivoting");
     if (wide && (o.oversample < 0 || o.power_iters < 0))

@@ -21,6 +21,8 @@
 //   UT[J] = [ (D^{-1}U_JJ)^{-1} strictly upper | D^{-1}U_{J,J+1} lower incl. diagonal ]
 //   DI[J] = D^{-1},  D = diag(U_JJ)
 // so the solve kernels need only matrix-vector products per block step.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "tile_ops.cuh"
@@ -186,6 +188,82 @@ struct TileGemm {
     }
 };
 
+// The same product on the tensor cores (TF32 operands rounded to nearest,
+// FP32 accumulation): the S x S output in m16n8 tiles spread over the warps,
+// mma.sync m16n8k8 over k-blocks of 8.  k-blocks outside the operands'
+// triangles are skipped; inside a straddling k-block the masked elements are
+// zeroed in the fragments (the unused triangles may hold temporaries).
+// Fragments (m16n8k8, .tf32): lane = 4g + t; A: (g, t) (g+8, t) (g, t+4)
+// (g+8, t+4); B: (t, g) (t+4, g); C: (g, 2t) (g, 2t+1) (g+8, 2t) (g+8, 2t+1).
+__device__ __forceinline__ unsigned to_tf32(float x) {
+    unsigned u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return u;
+}
+
+template <int S, int NT, int SA, int SB>
+struct TileGemmTC {
+    static constexpr int NTL = S / 8, TILES = (S / 16) * NTL, WARPS = NT / 32;
+    static constexpr int PER = (TILES + WARPS - 1) / WARPS;
+    float c[PER][4];
+    static __device__ __forceinline__ bool inA(int i, int q) {
+        return SA == LOWER ? q <= i : SA == UPPER ? q >= i : true;
+    }
+    static __device__ __forceinline__ bool inB(int q, int j) {
+        return SB == LOWER ? q >= j : SB == UPPER ? q <= j : true;
+    }
+    __device__ __forceinline__ void compute(const float *A, const float *B, int ld) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+        for (int w = 0; w < PER; ++w) {
+            c[w][0] = c[w][1] = c[w][2] = c[w][3] = 0.f;
+            const int tile = warp + w * WARPS;
+            if (tile >= TILES) continue;
+            const int m0 = (tile / NTL) * 16, n0 = (tile % NTL) * 8;
+#pragma unroll
+            for (int q0 = 0; q0 < S; q0 += 8) {
+                if (SA == LOWER && q0 > m0 + 15) continue;
+                if (SA == UPPER && q0 + 7 < m0) continue;
+                if (SB == LOWER && q0 + 7 < n0) continue;
+                if (SB == UPPER && q0 > n0 + 7) continue;
+                const int r0 = m0 + g, r1 = m0 + g + 8, k0 = q0 + t, k1 = q0 + t + 4, cn = n0 + g;
+                const unsigned a0 = to_tf32(inA(r0, k0) ? A[r0 * ld + k0] : 0.f);
+                const unsigned a1 = to_tf32(inA(r1, k0) ? A[r1 * ld + k0] : 0.f);
+                const unsigned a2 = to_tf32(inA(r0, k1) ? A[r0 * ld + k1] : 0.f);
+                const unsigned a3 = to_tf32(inA(r1, k1) ? A[r1 * ld + k1] : 0.f);
+                const unsigned b0 = to_tf32(inB(k0, cn) ? B[k0 * ld + cn] : 0.f);
+                const unsigned b1 = to_tf32(inB(k1, cn) ? B[k1 * ld + cn] : 0.f);
+                asm volatile(
+                    "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                    "{%0,%1,%2,%3};\n"
+                    : "+f"(c[w][0]), "+f"(c[w][1]), "+f"(c[w][2]), "+f"(c[w][3])
+                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+            }
+        }
+    }
+    // mode 0: C = A B; 1: C = -A B; 2: C = C - A B
+    __device__ __forceinline__ void store(float *C, int ld, int mode) const {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+        for (int w = 0; w < PER; ++w) {
+            const int tile = warp + w * WARPS;
+            if (tile >= TILES) continue;
+            const int m0 = (tile / NTL) * 16, n0 = (tile % NTL) * 8;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int row = m0 + g + (e >> 1) * 8, col = n0 + 2 * t + (e & 1);
+                float *p = C + row * ld + col;
+                *p = (mode == 0) ? c[w][e] : (mode == 1) ? -c[w][e] : *p - c[w][e];
+            }
+        }
+    }
+};
+
+// SIMT tiles, or tensor-core tiles for FP32 with TC (blocks of 16 and more)
+template <typename T, bool TC, int S, int NT, int SA, int SB>
+using Gemm = typename std::conditional<TC && std::is_same<T, float>::value && (S >= 16),
+                                       TileGemmTC<S, NT, SA, SB>, TileGemm<T, S, NT, SA, SB>>::type;
+
 // Base case: N x N block S (row stride ld) factorised in place into L\U while
 // the row operations turn an identity into L^{-1} and the column multipliers
 // of an identity block appended below S turn into U^{-1}.  One warp does it
@@ -274,7 +352,7 @@ __device__ void base_lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *
 // S22 -= L21 U12; S22 = L22 U22 (recursively);
 // (L^{-1})_21 = -L22^{-1} L21 L11^{-1},  (U^{-1})_12 = -U11^{-1} U12 U22^{-1}.
 // The two temporaries live in the unused triangles Li_12 and Ui_21.
-template <typename T, int N, int NT>
+template <typename T, int N, int NT, bool TC = false>
 __device__ void lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *status) {
     if constexpr (N <= 16) {
         base_lu_inv<T, N, NT>(S, Li, Ui, ld, grow0, status);
@@ -283,10 +361,10 @@ __device__ void lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *statu
         T *S12 = S + h, *S21 = S + h * ld, *S22 = S + h * ld + h;
         T *Li12 = Li + h, *Li21 = Li + h * ld, *Li22 = Li + h * ld + h;
         T *Ui12 = Ui + h, *Ui21 = Ui + h * ld, *Ui22 = Ui + h * ld + h;
-        lu_inv<T, h, NT>(S, Li, Ui, ld, grow0, status);
+        lu_inv<T, h, NT, TC>(S, Li, Ui, ld, grow0, status);
         {
-            TileGemm<T, h, NT, LOWER, FULL> g1;
-            TileGemm<T, h, NT, FULL, UPPER> g2;
+            Gemm<T, TC, h, NT, LOWER, FULL> g1;
+            Gemm<T, TC, h, NT, FULL, UPPER> g2;
             g1.compute(Li, S12, ld);   // U12 = L11^{-1} S12
             g2.compute(S21, Ui, ld);   // L21 = S21 U11^{-1}
             __syncthreads();
@@ -295,15 +373,15 @@ __device__ void lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *statu
             __syncthreads();
         }
         {
-            TileGemm<T, h, NT, FULL, FULL> g;
+            Gemm<T, TC, h, NT, FULL, FULL> g;
             g.compute(S21, S12, ld);
             g.store(S22, ld, 2);       // S22 -= L21 U12
             __syncthreads();
         }
-        lu_inv<T, h, NT>(S22, Li22, Ui22, ld, grow0 + h, status);
+        lu_inv<T, h, NT, TC>(S22, Li22, Ui22, ld, grow0 + h, status);
         {
-            TileGemm<T, h, NT, FULL, LOWER> g1;
-            TileGemm<T, h, NT, FULL, UPPER> g2;
+            Gemm<T, TC, h, NT, FULL, LOWER> g1;
+            Gemm<T, TC, h, NT, FULL, UPPER> g2;
             g1.compute(S21, Li, ld);   // L21 L11^{-1}
             g2.compute(S12, Ui22, ld); // U12 U22^{-1}
             g1.store(Li12, ld, 0);
@@ -311,8 +389,8 @@ __device__ void lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *statu
             __syncthreads();
         }
         {
-            TileGemm<T, h, NT, LOWER, FULL> g1;
-            TileGemm<T, h, NT, UPPER, FULL> g2;
+            Gemm<T, TC, h, NT, LOWER, FULL> g1;
+            Gemm<T, TC, h, NT, UPPER, FULL> g2;
             g1.compute(Li22, Li12, ld);
             g2.compute(Ui, Ui21, ld);
             g1.store(Li21, ld, 1);     // (L^{-1})_21
@@ -327,7 +405,7 @@ __device__ void lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *statu
     }
 }
 
-template <typename T, int KB>
+template <typename T, int KB, bool TC>
 __global__ void __launch_bounds__(4 * KB)
     k_band_lu(const double *__restrict__ band, int64_t ld, int k, Parts P, T *__restrict__ LT,
               T *__restrict__ UT, T *__restrict__ DI, int64_t *__restrict__ status) {
@@ -356,7 +434,7 @@ __global__ void __launch_bounds__(4 * KB)
         T *lt = LT + gJ * KB * KB;
         T *ut = UT + gJ * KB * KB;
 
-        lu_inv<T, KB, NT>(Sb, Li, Ui, LD, s + (int64_t)J * KB, status);
+        lu_inv<T, KB, NT, TC>(Sb, Li, Ui, LD, s + (int64_t)J * KB, status);
         if (t < KB) dU[t] = Sb[t * LD + t];
         __syncthreads();
         for (int e = t; e < KB * KB; e += NT) {
@@ -371,8 +449,8 @@ __global__ void __launch_bounds__(4 * KB)
 
         load_colblock<T, KB>(band, ld, k, s, ni, J + 1, Bu, Sb, Bln, LD);
         {
-            TileGemm<T, KB, NT, LOWER, LOWER> gz;
-            TileGemm<T, KB, NT, UPPER, UPPER> gy;
+            Gemm<T, TC, KB, NT, LOWER, LOWER> gz;
+            Gemm<T, TC, KB, NT, UPPER, UPPER> gy;
             gz.compute(Li, Bu, LD);    // U_{J,J+1} = L^{-1} A_{J,J+1}
             gy.compute(Blc, Ui, LD);   // L_{J+1,J} = A_{J+1,J} U^{-1}
             __syncthreads();
@@ -381,7 +459,7 @@ __global__ void __launch_bounds__(4 * KB)
             __syncthreads();
         }
         {
-            TileGemm<T, KB, NT, UPPER, LOWER> gs;
+            Gemm<T, TC, KB, NT, UPPER, LOWER> gs;
             gs.compute(Blc, Bu, LD);
             gs.store(Sb, LD, 2);       // S_{J+1} = A_{J+1,J+1} - L_{J+1,J} U_{J,J+1}
         }
@@ -400,7 +478,8 @@ static bool lu_impl(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
     constexpr int LD = KB + Pad<T>::v;
     const size_t smem = (6 * KB * LD + KB) * sizeof(T);
-    auto kern = k_band_lu<T, KB>;
+    // TF32: the block products on the tensor cores (FP32 factors otherwise)
+    auto kern = (c->opt.precision == LRSPIKE_MIXED_TF32) ? k_band_lu<T, KB, true> : k_band_lu<T, KB, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_LU, [&] {
         kern<<<c->p, 4 * KB, smem, c->stream>>>(c->band, c->ld, c->k, P, (T *)c->LT, (T *)c->UT, (T *)c->DI,

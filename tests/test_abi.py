@@ -47,7 +47,6 @@ def test_defaults(lib):
 
 
 @pytest.mark.parametrize("changes", [
-    dict(precision=2),                                     # TF32 needs the wide-band path (k > 64)
     dict(n=20000, k=100, r=8, pivoting=1),                 # wide bands: no pivoting
     dict(n=20000, k=100, r=8, compress=1),                 # wide bands: SPIKE compression only
     dict(n=20000, k=100, r=8, oversample=60),              # more than 64 sketch columns

@@ -212,3 +212,24 @@ def test_single_column_solves_k64(torch_cuda, precision, tol, compress):
     assert np.linalg.norm(res) / np.linalg.norm(f) <= tol * 1.01
     xs = scipy.linalg.solve_banded((k, k), ab, f)
     assert rel(x, xs) <= 1e3 * tol
+
+
+@pytest.mark.parametrize("compress", ["spike", "coupling"])
+def test_tf32_band_lu(torch_cuda, compress):
+    """MIXED_TF32 with k <= 64: the band LU's block products on the tensor
+    cores.  One application: TF32 operands carry a relative rounding of
+    2^-11 = 4.9e-4 into the products; through a well-conditioned chain that
+    stays well below 1e-3 of |M^{-1} f| (the FP32 bound is 5e-5).  The FP64
+    refinement still reaches 1e-10."""
+    n, k, p, r = 6000, 64, 6, 16
+    ab = inputs.dominant_band(n, k, 1.1, 5)
+    f = inputs.rhs(n, 2, 5)
+    fac = O.factor(ab, k, p, r, compress=compress, reduced="truncated")
+    got, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced="truncated", outer="none",
+                          precision="tf32")
+    assert rel(got, O.apply(fac, np.asarray(f))) <= 1e-3
+    x, info, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced="truncated", precision="tf32",
+                           tol=1e-10)
+    assert info["converged"]
+    res = np.asarray(f) - O.band_matvec(ab, k, x)
+    assert (np.linalg.norm(res, axis=0) / np.linalg.norm(f, axis=0)).max() <= 1.01e-10
