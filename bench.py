@@ -169,7 +169,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per launch at this workload, from one ncu capture of
 # the quarter-size case (python bench.py --profile-case: n/4 rows, p/4
 # partitions, same n_i) scaled by 4 (both grow with n).  None = not captured.
-NCU_TRAFFIC = {"band_lu": 4 * (1.083490e9 + 0.512573e9)}
+NCU_TRAFFIC = {"band_lu": 4 * (1.080680e9 + 0.511967e9), "band_lu_inv": 4 * (0.394333e9 + 0.249154e9)}
 
 
 def kernel_work(name: str, prof: dict, precision_bytes: int):
@@ -185,6 +185,8 @@ def kernel_work(name: str, prof: dict, precision_bytes: int):
         return "hbm", n * 2 * r * tb + n * nrhs * (tb + 16)
     if name == "band_lu":           # 2 n k^2 flops: the textbook band LU count
         return "alu", 2.0 * n * k * k
+    if name == "band_lu_inv":       # both tiles read, their strict triangles written back
+        return "hbm", 3 * n * kb * tb
     if name == "spike_sweep":       # triangular block products, V fwd skipped? (counted as done)
         return "alu", 6.0 * n * k * k
     return None, None

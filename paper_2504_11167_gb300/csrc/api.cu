@@ -16,7 +16,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "gram_reduce",  "coupling_gram", "jacobi",      "make_u",      "reduced_build",
     "reduced_factor", "norm",        "residual",    "dstage",      "reduced_solve",
     "retrieve",     "project_t",     "dstage_t",    "bicgstab_vector", "matvec",
-    "wide_gather",  "wide_gemm",     "wide_lu64",   "wide_vector", "nonzero_diagonals"};
+    "wide_gather",  "wide_gemm",     "wide_lu64",   "wide_vector", "nonzero_diagonals", "band_lu_inv"};
 
 static cudaEvent_t take_event(Ctx *c) {
     if (!c->free_events.empty()) {

@@ -69,4 +69,49 @@ __device__ __forceinline__ double band_local(const double *__restrict__ band, in
     return band[d * ld + s + j];
 }
 
+// Pivot reciprocal: the hardware approximate reciprocal; in FP64 refined by
+// two Newton-Raphson steps r <- r (2 - v r) (each squares the relative error,
+// from about 2^-22 to below 2^-53).  A pivot below the smallest normal number
+// counts as singular.
+template <typename T> __device__ __forceinline__ T fast_rcp(T v);
+template <> __device__ __forceinline__ float fast_rcp<float>(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+template <> __device__ __forceinline__ double fast_rcp<double>(double v) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
+    r = r * (2.0 - v * r);
+    r = r * (2.0 - v * r);
+    return r;
+}
+template <typename T> __device__ __forceinline__ bool usable_pivot(T v);
+template <> __device__ __forceinline__ bool usable_pivot<float>(float v) { return fabsf(v) >= 1.17549435e-38f && isfinite(v); }
+template <> __device__ __forceinline__ bool usable_pivot<double>(double v) { return fabs(v) >= 2.2250738585072014e-308 && isfinite(v); }
+
+// FP64 -> FP32, round to nearest even, in integer arithmetic.  GB300 runs the
+// hardware conversion on its FP64 units, at a small fraction of the FP32
+// rate.  Derived from the IEEE 754 binary64 and binary32 layouts:
+//   - round the binary64 encoding at bit 29 (ties to even; a carry into the
+//     exponent is correct by construction);
+//   - keep the low 9 exponent bits and the top 23 mantissa bits;
+//   - rebias the exponent: for binary64 exponents of normal binary32 numbers
+//     (897..1150, i.e. 2^-126 <= |v| < 2^128), e - 896 equals the low 8 bits
+//     of e with the top bit flipped.
+// Magnitudes below 2^-126 become signed zero.  2^128 and above, Inf and NaN
+// take the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(b >> 32), mag = hi & 0x7FFFFFFFu;
+    if (mag >= 0x47F00000u) return (float)v;
+    if (mag < 0x38100000u) return __int_as_float((int)(hi & 0x80000000u));
+    b += 0x0FFFFFFFull + ((b >> 29) & 1ull);
+    const unsigned bits = __funnelshift_l((unsigned)b, (unsigned)(b >> 32), 3);
+    return __int_as_float((int)(((bits ^ 0x40000000u) & 0x7FFFFFFFu) | (hi & 0x80000000u)));
+}
+template <typename T> __device__ __forceinline__ T from_f64(double v);
+template <> __device__ __forceinline__ float from_f64<float>(double v) { return d2f_rn(v); }
+template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
+
 }  // namespace lrs

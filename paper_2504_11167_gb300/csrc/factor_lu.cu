@@ -270,27 +270,6 @@ using Gemm = typename std::conditional<TC && std::is_same<T, float>::value && (S
 // with the three blocks in registers: lane l owns row l % N and the CPL
 // columns (l / N) * CPL .. + CPL - 1 of S, L^{-1} and U^{-1}; the pivot row
 // and column move by shuffles, so no barrier is needed between pivots.
-// Pivot reciprocal: the hardware approximate reciprocal; in FP64 refined by
-// two Newton-Raphson steps r <- r (2 - v r) (each squares the relative error,
-// from about 2^-22 to below 2^-53).  A pivot below the smallest normal number
-// counts as singular.
-template <typename T> __device__ __forceinline__ T fast_rcp(T v);
-template <> __device__ __forceinline__ float fast_rcp<float>(float v) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-    return r;
-}
-template <> __device__ __forceinline__ double fast_rcp<double>(double v) {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
-    r = r * (2.0 - v * r);
-    r = r * (2.0 - v * r);
-    return r;
-}
-template <typename T> __device__ __forceinline__ bool usable_pivot(T v);
-template <> __device__ __forceinline__ bool usable_pivot<float>(float v) { return fabsf(v) >= 1.17549435e-38f && isfinite(v); }
-template <> __device__ __forceinline__ bool usable_pivot<double>(double v) { return fabs(v) >= 2.2250738585072014e-308 && isfinite(v); }
-
 template <typename T, int N, int NT>
 __device__ void base_lu_inv(T *S, T *Li, T *Ui, int ld, int64_t grow0, int64_t *status) {
     constexpr int CPL = N * N / 32;  // columns per lane
@@ -547,6 +526,8 @@ bool run_lu_inv64(Ctx *c, void *A, int lda, int64_t sA, void *Li, void *Ui, int 
 
 bool run_band_lu(Ctx *c) {
     if (c->opt.pivoting) return run_band_lu_piv(c);
+    // TF32 keeps the block-recursive kernel (its block products are what runs on the tensor cores)
+    if (c->opt.precision != LRSPIKE_MIXED_TF32) return run_band_lu_col(c);
     return c->fp64 ? lu_kb<double>(c) : lu_kb<float>(c);
 }
 

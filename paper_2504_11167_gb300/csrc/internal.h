@@ -35,6 +35,7 @@ enum KernelId {
     KID_WIDE_LU64,
     KID_WIDE_VEC,
     KID_DIAGS,
+    KID_LU_INV,
     KID_COUNT
 };
 
@@ -150,6 +151,8 @@ inline bool launch(Ctx *c, int kid, F &&f) {
 
 // ---- launchers (each dispatches on the working precision and KB) --------
 bool run_band_lu(Ctx *c);
+// column-by-column band LU + per-block triangular inverses (same tiles)
+bool run_band_lu_col(Ctx *c);
 bool run_spike_rhs(Ctx *c);
 bool run_sweep(Ctx *c);
 bool run_gram(Ctx *c);

@@ -216,6 +216,9 @@ __device__ __forceinline__ void cp_async_small(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Stages a KB x KB tile into shared memory rows of stride LDP = KB + 16/sizeof(T)
 // (one 16-byte pad per row), plus optionally KB diagonal values.
