@@ -120,28 +120,33 @@ __global__ void __launch_bounds__(RBS)
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, int KB, Split S>
+template <typename T, int KB, Split S, int NBUF>
 __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
                             const T *__restrict__ PQ, Parts P, int k, int r, int64_t n,
                             const double *__restrict__ rin, const double *__restrict__ inv,
                             int nrhs, T *__restrict__ Yv, T *__restrict__ Gv, double *__restrict__ psi,
                             unsigned char *smem_raw) {
     constexpr int NT = Geo<KB>::NT, LDP = KB + 16 / (int)sizeof(T);
+    constexpr int PDS = NBUF - 1;  // steps staged ahead (the factor tile of a step is 16 KB from HBM)
     const int pm = KB * nrhs;
-    double *ib = reinterpret_cast<double *>(smem_raw);  // [2][KB x nrhs] staged input rows
-    T *tb = reinterpret_cast<T *>(ib + 2 * pm);          // [2][KB x LDP] staged factor tiles
-    T *db = tb + 2 * KB * LDP;                            // [2][KB] staged D^{-1}
-    T *Tt = db + 2 * KB;
+    double *ib = reinterpret_cast<double *>(smem_raw);  // [NBUF][KB x nrhs] staged input rows
+    T *tb = reinterpret_cast<T *>(ib + NBUF * pm);       // [NBUF][KB x LDP] staged factor tiles
+    T *db = tb + NBUF * KB * LDP;                         // [NBUF][KB] staged D^{-1}
+    T *Tt = db + NBUF * KB;
     T *Yp = Tt + pm;
+    T *Yk = Yp + pm;  // forward output of block nb-2, kept for the backward sweep
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int64_t b0 = P.boff[part];
     const int nb = (int)(P.boff[part + 1] - b0);
     const int steps = 2 * nb;
     // step t < nb: forward block t (LT, input rows of r); step t >= nb:
-    // backward block 2nb-1-t (UT, DI, input rows of y written by the forward sweep)
+    // backward block 2nb-1-t (UT, DI, input rows of y written by the forward
+    // sweep).  A backward input is staged PDS steps ahead from global memory
+    // only for blocks J <= nb-3, whose forward writes are at least two steps
+    // (and barriers) older; blocks nb-1 and nb-2 take it from Yp and Yk.
     auto stage = [&](int t) {
-        const int buf = t & 1;
+        const int buf = t % NBUF;
         double *in = ib + buf * pm;
         if (t < nb) {
             stage_tile<T, KB>(LT + (b0 + t) * KB * KB, tb + buf * KB * LDP, nullptr, nullptr);
@@ -154,7 +159,7 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
             const int J = steps - 1 - t;
             const int64_t g = b0 + J;
             stage_tile<T, KB>(UT + g * KB * KB, tb + buf * KB * LDP, DI + g * KB, db + buf * KB);
-            if (J < nb - 1) {  // the last forward step's output is still in Yp
+            if (J < nb - 2) {
                 T *inT = reinterpret_cast<T *>(in);
                 for (int e = threadIdx.x; e < pm; e += NT) {
                     const int c = e / KB, a = e % KB;
@@ -164,15 +169,71 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
             }
         }
     };
-    stage(0);
-    cp_async_commit();
-    for (int t = 0; t < steps; ++t) {
-        if (t + 1 < steps) stage(t + 1);
+    for (int t = 0; t < PDS; ++t) {
+        if (t < steps) stage(t);
         cp_async_commit();
-        cp_async_wait1();
+    }
+    if (nrhs == 1 && sizeof(T) == 4) {
+        // One right-hand side in FP32 (FP64 keeps the bounded triangular
+        // loops below, its multiply-adds being scarce): two barriers per block step.  The loop-top
+        // barrier publishes the staged step and closes the previous one; the
+        // input scaling is fused into the first product, the output stores
+        // into the second.
+        const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
+        const double inv0 = inv[0];
+        for (int t = 0; t < steps; ++t) {
+            cp_async_wait<PDS - 1>();
+            __syncthreads();
+            // buffer (t + PDS) % NBUF last served step t-1, closed by the barrier above
+            if (t + PDS < steps) stage(t + PDS);
+            cp_async_commit();
+            const T *tile = tb + (t % NBUF) * KB * LDP + a * LDP;
+            const double *in = ib + (t % NBUF) * pm;
+            if (t < nb) {
+                const int J = t;
+                const int64_t row = (int64_t)J * KB + a;
+                // t = b_J - L_{J,J-1} y_{J-1}   (upper triangle incl. diagonal)
+                const T p1 = (J > 0) ? tri_dot1<T, KB, 0>(tile, Yp, a, q) : T(0);
+                if (q == 0) {
+                    const T b = (row >= ni) ? T(0) : (T)(in[a] * inv0);
+                    Tt[a] = b - p1;
+                }
+                __syncthreads();
+                // y_J = t + (L^{-1} strictly lower) t
+                const T y = Tt[a] + tri_dot1<T, KB, 1>(tile, Tt, a, q);
+                if (q == 0) {
+                    Yp[a] = y;
+                    if (row < ni) Yv[s + row] = y;
+                    if (J == nb - 2) Yk[a] = y;
+                }
+            } else {
+                const int J = steps - 1 - t;
+                const int64_t row = (int64_t)J * KB + a;
+                const T *inT = reinterpret_cast<const T *>(in);
+                const T yin = (row >= ni) ? T(0) : (J == nb - 1) ? Yp[a] : (J == nb - 2) ? Yk[a] : inT[a];
+                const T dsm = db[(t % NBUF) * KB + a];
+                // t = D^{-1} y_J - (D^{-1}U_{J,J+1}) x_{J+1}   (lower triangle incl. diagonal)
+                const T p1 = (J < nb - 1) ? tri_dot1<T, KB, 2>(tile, Yp, a, q) : T(0);
+                if (q == 0) Tt[a] = yin * dsm - p1;
+                __syncthreads();
+                // x_J = t + ((D^{-1}U_JJ)^{-1} strictly upper) t
+                const T x = Tt[a] + tri_dot1<T, KB, 3>(tile, Tt, a, q);
+                if (q == 0) {
+                    Yp[a] = x;
+                    if (row < ni) Gv[s + row] = x;
+                }
+            }
+        }
         __syncthreads();
-        const T *tile = tb + (t & 1) * KB * LDP;
-        const double *in = ib + (t & 1) * pm;
+    } else
+    for (int t = 0; t < steps; ++t) {
+        // buffer (t + PDS) % NBUF last served step t-1, closed by the barrier ending it
+        if (t + PDS < steps) stage(t + PDS);
+        cp_async_commit();
+        cp_async_wait<PDS>();
+        __syncthreads();
+        const T *tile = tb + (t % NBUF) * KB * LDP;
+        const double *in = ib + (t % NBUF) * pm;
         if (t < nb) {
             const int J = t;
             for (int e = threadIdx.x; e < pm; e += NT) {
@@ -186,6 +247,7 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
                 const int a = e / nrhs, c = e % nrhs;
                 const int64_t row = (int64_t)J * KB + a;
                 if (row < ni) Yv[c * n + s + row] = Yp[e];
+                if (J == nb - 2) Yk[e] = Yp[e];
             }
         } else {
             const int J = steps - 1 - t;
@@ -193,10 +255,10 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
             for (int e = threadIdx.x; e < pm; e += NT) {
                 const int a = e / nrhs;
                 const int64_t row = (int64_t)J * KB + a;
-                Tt[e] = (row >= ni) ? T(0) : (J == nb - 1) ? Yp[e] : inT[e];
+                Tt[e] = (row >= ni) ? T(0) : (J == nb - 1) ? Yp[e] : (J == nb - 2) ? Yk[e] : inT[e];
             }
             __syncthreads();
-            bwd_step<T, KB, S>(tile, LDP, db + (t & 1) * KB, Tt, Yp, nrhs, nrhs, J == nb - 1);
+            bwd_step<T, KB, S>(tile, LDP, db + (t % NBUF) * KB, Tt, Yp, nrhs, nrhs, J == nb - 1);
             for (int e = threadIdx.x; e < pm; e += NT) {
                 const int a = e / nrhs, c = e % nrhs;
                 const int64_t row = (int64_t)J * KB + a;
@@ -224,7 +286,7 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
     }
 }
 
-template <typename T, int KB>
+template <typename T, int KB, int NBUF>
 __global__ void __launch_bounds__(Geo<KB>::NT)
     k_dstage(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
              const T *__restrict__ PQ, Parts P, int k, int r, int64_t n, const double *__restrict__ rin,
@@ -232,9 +294,9 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
              double *__restrict__ psi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (nrhs < 4)
-        dstage_body<T, KB, Split::DOTS>(LT, UT, DI, PQ, P, k, r, n, rin, inv, nrhs, Yv, Gv, psi, smem_raw);
+        dstage_body<T, KB, Split::DOTS, NBUF>(LT, UT, DI, PQ, P, k, r, n, rin, inv, nrhs, Yv, Gv, psi, smem_raw);
     else
-        dstage_body<T, KB, Split::COLS>(LT, UT, DI, PQ, P, k, r, n, rin, inv, nrhs, Yv, Gv, psi, smem_raw);
+        dstage_body<T, KB, Split::COLS, NBUF>(LT, UT, DI, PQ, P, k, r, n, rin, inv, nrhs, Yv, Gv, psi, smem_raw);
 }
 
 // x (+)= nrm * (g - u_T zeta - u_W omega) for one partition's rows.
@@ -508,12 +570,17 @@ bool run_norms(Ctx *c, const double *v, int64_t ld, int nrhs, double *out) {
     return sumsq_nr<16>(c, v, ld, nrhs, out, nullptr);
 }
 
-template <typename T, int KB>
-static bool dstage_impl(Ctx *c, const double *rin, int nrhs) {
+template <typename T, int KB, int NBUF>
+static size_t dstage_smem(int nrhs) {
+    return (size_t)NBUF * KB * nrhs * sizeof(double) +
+           ((size_t)NBUF * KB * (KB + 16 / sizeof(T)) + NBUF * KB + 3 * KB * nrhs) * sizeof(T);
+}
+
+template <typename T, int KB, int NBUF>
+static bool dstage_launch(Ctx *c, const double *rin, int nrhs) {
     Parts P{c->off_d, c->boff_d, c->p};
-    const size_t smem = 2 * KB * nrhs * sizeof(double) +
-                        (2 * KB * (KB + 16 / sizeof(T)) + 2 * KB + 2 * KB * nrhs) * sizeof(T);
-    auto kern = k_dstage<T, KB>;
+    const size_t smem = dstage_smem<T, KB, NBUF>(nrhs);
+    auto kern = k_dstage<T, KB, NBUF>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_DSTAGE, [&] {
         kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT, (const T *)c->DI,
@@ -521,6 +588,14 @@ static bool dstage_impl(Ctx *c, const double *rin, int nrhs) {
                                                      c->nrm + 2 * c->opt.max_nrhs, nrhs, (T *)c->Yv,
                                                      (T *)c->Gv, c->psi);
     });
+}
+
+// Four stage buffers (three steps of factor tiles in flight) while two CTAs
+// still fit on an SM; two otherwise.
+template <typename T, int KB>
+static bool dstage_impl(Ctx *c, const double *rin, int nrhs) {
+    if (dstage_smem<T, KB, 4>(nrhs) <= 110 * 1024) return dstage_launch<T, KB, 4>(c, rin, nrhs);
+    return dstage_launch<T, KB, 2>(c, rin, nrhs);
 }
 
 template <typename T, int KB>
