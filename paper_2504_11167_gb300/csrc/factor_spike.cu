@@ -204,6 +204,185 @@ __global__ void __launch_bounds__((KB / 4) * CG, (KB >= 64 && sizeof(T) == 4) ? 
 }
 
 // ---------------------------------------------------------------------------
+// The same sweep, pipelined, for FP32 panels whose staging ring fits two CTAs
+// per SM (the COUPLING mode's 2r columns).  Per block step the raw factor tile,
+// the panel block and D^{-1} are staged with cp.async two steps ahead into a
+// ring of three buffers.  The triangular products read the raw tile and mask
+// only the thread's 4-row diagonal chunk (compile-time masks: row a0+i,
+// column a0+u).  Two barriers per step: the loop-top barrier publishes the
+// staged step and closes the previous one.  The backward sweep's first block
+// (J = nb-1) takes its input from Yp, the forward output that is still in
+// shared memory; every other backward input was written to X at least one
+// step (and a barrier) before its staging.
+template <typename T, int KB, int MT, int CG> struct SweepPipe {
+    static constexpr int NT = (KB / 4) * CG, M = MT * CG, NBUF = 3, PDS = 2;
+    static constexpr int LDT = KB + 16 / (int)sizeof(T), LDM = M + 16 / (int)sizeof(T);
+    static constexpr size_t bytes =
+        ((size_t)NBUF * (KB * LDT + KB * LDM + KB) + (size_t)2 * KB * LDM) * sizeof(T);
+};
+
+template <typename T, int KB, int MT, int CG>
+__global__ void __launch_bounds__((KB / 4) * CG)
+    k_sweep_pipe(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI, Parts P, int k,
+                 T *__restrict__ X) {
+    using SP = SweepPipe<T, KB, MT, CG>;
+    constexpr int NT = SP::NT, M = SP::M, HALFM = M / 2, NBUF = SP::NBUF, PDS = SP::PDS;
+    constexpr int LDT = SP::LDT, LDM = SP::LDM, CH = 16 / (int)sizeof(T);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tiles = reinterpret_cast<T *>(smem_raw);  // [NBUF][KB x LDT] raw factor tiles
+    T *pans = tiles + NBUF * KB * LDT;           // [NBUF][KB x LDM] panel blocks
+    T *dis = pans + NBUF * KB * LDM;             // [NBUF][KB] D^{-1}
+    T *Tt = dis + NBUF * KB;                     // KB x LDM
+    T *Yp = Tt + KB * LDM;                       // KB x LDM
+    const int part = blockIdx.x;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int64_t b0 = P.boff[part];
+    const int nb = (int)(P.boff[part + 1] - b0), steps = 2 * nb;
+    const bool hasV = part < P.p - 1, hasW = part > 0;
+    const int Jv0 = (int)((ni - k) / KB);
+    int ty, tx;
+    PanelMap<KB, CG>::get(threadIdx.x, ty, tx);
+    const int a0 = 4 * ty, c0 = MT * tx;
+    const bool isV = c0 < HALFM;
+
+    auto stage = [&](int t) {
+        const int buf = t % NBUF;
+        const bool fwd = t < nb;
+        const int J = fwd ? t : steps - 1 - t;
+        const int64_t g = b0 + J;
+        const T *tsrc = (fwd ? LT : UT) + g * KB * KB;
+        T *tdst = tiles + buf * KB * LDT;
+        for (int e = threadIdx.x; e < KB * (KB / CH); e += NT) {
+            const int row = e / (KB / CH), ch = e % (KB / CH);
+            cp_async16(tdst + row * LDT + ch * CH, tsrc + row * KB + ch * CH);
+        }
+        if (fwd || J < nb - 1) {
+            const T *psrc = X + g * KB * M;
+            T *pdst = pans + buf * KB * LDM;
+            for (int e = threadIdx.x; e < KB * (M / CH); e += NT) {
+                const int row = e / (M / CH), ch = e % (M / CH);
+                cp_async16(pdst + row * LDM + ch * CH, psrc + row * M + ch * CH);
+            }
+        }
+        if (!fwd && threadIdx.x < KB / CH) cp_async16(dis + buf * KB + threadIdx.x * CH, DI + g * KB + threadIdx.x * CH);
+    };
+    // acc (+/-)= tile rows a0..a0+3 x B over q in [a0, a0+4), masked per (row, column)
+    auto chunk = [&](T (&acc)[4][MT], const T *tile, const T *B, int mode, bool sub) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            T bv[MT];
+            ld_row<T, MT>(B + (a0 + u) * LDM + c0, bv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                // column a0+u against row a0+i: 0: q >= a, 1: q < a, 2: q <= a, 3: q > a
+                const bool in = mode == 0 ? u >= i : mode == 1 ? u < i : mode == 2 ? u <= i : u > i;
+                if (!in) continue;
+                const T av = tile[(a0 + i) * LDT + a0 + u];
+#pragma unroll
+                for (int j = 0; j < MT; ++j) acc[i][j] = sub ? acc[i][j] - av * bv[j] : acc[i][j] + av * bv[j];
+            }
+        }
+    };
+
+    // acc (+/-)= tile rows a0..a0+3 x B over q in [q0, q1) (multiples of 4):
+    // four inner indices per 16-byte load of each tile row
+    auto mac4 = [&](T (&acc)[4][MT], const T *tile, const T *B, int q0, int q1, bool sub) {
+        for (int q = q0; q < q1; q += 4) {
+            T av[4][4], bv[4][MT];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ld_row<T, 4>(tile + (a0 + i) * LDT + q, av[i]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ld_row<T, MT>(B + (q + u) * LDM + c0, bv[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < MT; ++j)
+                        acc[i][j] = sub ? acc[i][j] - av[i][u] * bv[u][j] : acc[i][j] + av[i][u] * bv[u][j];
+        }
+    };
+    for (int t = 0; t < PDS; ++t) {
+        if (t < steps) stage(t);
+        cp_async_commit();
+    }
+    T acc[4][MT];
+    for (int t = 0; t < steps; ++t) {
+        cp_async_wait<PDS - 1>();
+        __syncthreads();
+        // buffer (t + PDS) % NBUF last served step t-1, closed by the barrier above
+        if (t + PDS < steps) stage(t + PDS);
+        cp_async_commit();
+        const int buf = t % NBUF;
+        const T *tile = tiles + buf * KB * LDT, *pan = pans + buf * KB * LDM;
+        if (t < nb) {
+            const int J = t;
+            const bool active = isV ? (hasV && J >= Jv0) : hasW;
+            const bool first = (J == 0) || (isV && J == Jv0);
+            if (active) {
+                // t = b_J - L_{J,J-1} y_{J-1}   (L_{J,J-1} upper incl. diagonal: q >= a)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ld_row<T, MT>(pan + (a0 + i) * LDM + c0, acc[i]);
+                if (!first) {
+                    chunk(acc, tile, Yp, 0, true);
+                    mac4(acc, tile, Yp, a0 + 4, KB, true);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) st_row<T, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+            }
+            __syncthreads();
+            if (active) {
+                // y_J = t + (L_JJ^{-1} strictly lower) t
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ld_row<T, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+                mac4(acc, tile, Tt, 0, a0, false);
+                chunk(acc, tile, Tt, 1, false);
+                T *xg = X + (b0 + J) * KB * M;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    st_row<T, MT>(Yp + (a0 + i) * LDM + c0, acc[i]);
+                    st_row<T, MT>(xg + (a0 + i) * M + c0, acc[i]);
+                }
+            }
+        } else {
+            const int J = steps - 1 - t;
+            const bool active = isV ? hasV : hasW;
+            const T *dsm = dis + buf * KB;
+            if (active) {
+                // t = D^{-1} y_J - (D^{-1}U_{J,J+1}) x_{J+1}   (lower incl. diagonal: q <= a)
+                const T *src = (J == nb - 1) ? Yp : pan;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ld_row<T, MT>(src + (a0 + i) * LDM + c0, acc[i]);
+#pragma unroll
+                    for (int j = 0; j < MT; ++j) acc[i][j] *= dsm[a0 + i];
+                }
+                if (J < nb - 1) {
+                    mac4(acc, tile, Yp, 0, a0, true);
+                    chunk(acc, tile, Yp, 2, true);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) st_row<T, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+            }
+            __syncthreads();
+            if (active) {
+                // x_J = t + ((D^{-1}U_JJ)^{-1} strictly upper) t
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ld_row<T, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+                chunk(acc, tile, Tt, 3, false);
+                mac4(acc, tile, Tt, a0 + 4, KB, false);
+                T *xg = X + (b0 + J) * KB * M;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    st_row<T, MT>(Yp + (a0 + i) * LDM + c0, acc[i]);
+                    st_row<T, MT>(xg + (a0 + i) * M + c0, acc[i]);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Gram matrices of the two spike panels, partial sums over a chunk of blocks.
 // Thread tile: 4 rows x GC columns of one Gram matrix (GC = KB/8).
 template <typename T, int KB>
@@ -341,9 +520,10 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
                 // rotate while the pair is not yet diagonal to working precision:
                 // relative to the pair, with an absolute floor of eps * (largest
                 // initial diagonal entry) below which off-diagonals are rounding noise
-                const double thr = fmax((double)Eps<T>::v * sqrt(fabs((double)app * (double)aqq)),
-                                        2.0 * (double)Eps<T>::v * (double)amax);
-                if (apq != T(0) && fabs((double)apq) > thr) {
+                // (in the working precision: GB300's FP64 units are scarce, and
+                // sqrt|a_pp| sqrt|a_qq| cannot overflow)
+                const T thr = fmax(Eps<T>::v * (sqrt(fabs(app)) * sqrt(fabs(aqq))), T(2) * Eps<T>::v * amax);
+                if (apq != T(0) && fabs(apq) > thr) {
                     const T tau = (aqq - app) / (T(2) * apq);
                     const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
                     c = T(1) / sqrt(T(1) + t * t);
@@ -402,7 +582,7 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
         const bool keep = (s1 > 0.0) && (sg > rank_tol * s1);
         int imax = 0;
         for (int q = 1; q < KB; ++q)
-            if (fabs((double)V[q * LD + j]) > fabs((double)V[imax * LD + j])) imax = q;
+            if (fabs(V[q * LD + j]) > fabs(V[imax * LD + j])) imax = q;
         const T sgn = (V[imax * LD + j] < T(0)) ? T(-1) : T(1);
         for (int q = threadIdx.x % 4; q < KB; q += 4) out[c * KB + q] = keep ? sgn * V[q * LD + j] : T(0);
         if (threadIdx.x % 4 == 0) sigma[(int64_t)id * r + c] = keep ? sg : 0.0;
@@ -510,6 +690,17 @@ template <typename T, int KB, int MT, int CG>
 static bool sweep_mt(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
     constexpr int M = MT * CG, LDM = M + 16 / (int)sizeof(T), NT = (KB / 4) * CG;
+    if constexpr (sizeof(T) == 4) {
+        using SP = SweepPipe<T, KB, MT, CG>;
+        if (SP::bytes <= 110 * 1024) {
+            auto kp = k_sweep_pipe<T, KB, MT, CG>;
+            cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP::bytes);
+            return launch(c, KID_SWEEP, [&] {
+                kp<<<c->p, NT, SP::bytes, c->stream>>>((const T *)c->LT, (const T *)c->UT, (const T *)c->DI, P,
+                                                       c->k, (T *)c->X);
+            });
+        }
+    }
     const size_t smem = (2 * KB * (KB + 1) + 2 * KB * LDM + KB) * sizeof(T);
     auto kern = k_sweep<T, KB, MT, CG>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
