@@ -7,37 +7,35 @@
 //   DI[J] = D^{-1},  D = diag(U_JJ)
 // in two kernels.
 //
-// k_band_lu_col: one CTA per partition eliminates its columns one at a time.
+// k_band_lu_col: one CTA per partition eliminates its columns, TR at a time.
 //   Without pivoting, eliminating column j changes only rows and columns
 //   j+1..j+k, so the live part of the matrix is a KB x KB window (KB >= k)
 //   that slides down the diagonal.  The window stays in registers, indexed
-//   modulo KB: the entry (i, l) sits with the thread owning row residue
-//   i mod KB and column residue l mod KB (a GRID x GRID thread grid, TR x TR
-//   residues per thread: 64 threads with 8 x 8 entries at KB = 64, few threads
-//   with many entries, so the per-column bookkeeping is paid by few threads).
-//   After column j is eliminated, row j and column j leave the window and
-//   row j+KB and column j+KB enter it in the same residue slots.  Both come
-//   straight from the band, because no earlier column touches them.  Each
-//   column costs one barrier:
-//     - the owners of pivot row j and column j have published them in shared
-//       memory (double-buffered by column parity);
-//     - every thread forms its multipliers a_ij / a_jj;
-//     - every thread swaps in the entering row and column, then applies the
-//       rank-1 update to its entries;
-//     - the owners of row and column j+1 publish them for the next column.
-//   Staging is spread evenly over all threads and done per group of TR
-//   columns.  The 2KB+2 values that enter per column are:
-//     - the entering row (band diagonals k..k+KB-1);
-//     - the entering column (diagonals k..k-KB+1);
-//     - the far ends of the next pivot row and column.
-//   Each thread owns the same few (column-in-group, value) slots in every
-//   group, with precomputed band pointers.  Per group it:
-//     - issues 8-byte cp.async for the group PD groups ahead (32 columns);
-//     - converts its own values of the next group into buffers indexed by
-//       residue, in integer arithmetic (d2f_rn: GB300's hardware FP64
-//       conversion runs on the slow FP64 units);
+//   modulo KB: entry (i, l) sits with the thread owning row residue i mod KB
+//   and column residue l mod KB (a GRID x GRID thread grid, TR x TR residues
+//   per thread).  One step eliminates the TR columns j..j+TR-1 of one residue
+//   group (one barrier per step):
+//     - the pivot block a_{j+u, j+v}, the pivot rows and the pivot columns
+//       were published by their owners in shared memory (double-buffered);
+//     - every thread factors the TR x TR pivot block itself (P = L_p U_p);
+//     - every thread forms the pivot-row entries L_p^{-1} R of its columns and
+//       the multipliers C U_p^{-1} of its rows;
+//     - the thread row / column owning the group's residues swaps in the
+//       entering rows and columns j+KB..j+KB+TR-1 (straight from the band: no
+//       earlier column touches them);
+//     - every thread applies the rank-TR update to its TR x TR entries;
+//     - the owners of the next group publish it.
+//   The leaving residue slots stand for the entering columns in the pivot
+//   rows and for the entering rows in the pivot columns.  Those "far" entries
+//   come from the band as well.
+//   Staging is spread evenly over all threads.  Each thread owns the same few
+//   values in every group, each a fixed band diagonal with a precomputed
+//   pointer.  Per step it:
+//     - issues 8-byte cp.async for the group PD steps ahead (32 columns);
+//     - converts its own values of the next group to the working precision,
+//       in integer arithmetic (d2f_rn: GB300's hardware FP64 conversion runs
+//       on the slow FP64 units);
 //     - writes its share of the previous block's multipliers.
-//   The three tasks fall on different columns of the group.
 //   Outputs:
 //     - the multipliers of a block's KB columns are staged in shared memory
 //       and written during the next block;
@@ -60,6 +58,290 @@
 namespace lrs {
 
 template <typename T, int KB> struct ColGeo {
+    static constexpr int GRID = KB >= 16 ? 16 : 8;    // thread grid GRID x GRID
+    static constexpr int NT = GRID * GRID;
+    static constexpr int TR = KB / GRID;              // residues per thread and direction; columns per step
+    static constexpr int PD = (sizeof(T) == 8 ? 16 : 32) / TR;  // staging distance in steps
+    static constexpr int RING = PD + 1;               // raw ring slots (step Gs in slot Gs % RING)
+    static constexpr int SLOT = 2 * TR * KB + 2 * TR * TR;  // staged values per step
+    static constexpr int SLOTP = (SLOT + 3) / 4 * 4;  // converted stride (16-byte aligned vectors)
+    static constexpr int PUB = TR * TR + 2 * TR * KB; // published values per step
+    static constexpr int NU = (SLOT + NT - 1) / NT;   // staged values per thread and step
+};
+
+template <typename T, int KB> struct ColSmem {
+    using G = ColGeo<T, KB>;
+    static constexpr int LDL = KB + 16 / (int)sizeof(T);  // multiplier staging row stride
+    static constexpr size_t bytes = (size_t)G::RING * G::SLOT * 8 + (size_t)2 * G::SLOTP * sizeof(T) +
+                                    (size_t)2 * G::PUB * sizeof(T) + (size_t)2 * KB * LDL * sizeof(T);
+};
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(ColGeo<T, KB>::NT, sizeof(T) == 4 ? 2 : 1)
+    k_band_lu_col(const double *__restrict__ band, int64_t ld, int k, Parts P, T *__restrict__ LT,
+                  T *__restrict__ UT, T *__restrict__ DI, int64_t *__restrict__ status) {
+    using G = ColGeo<T, KB>;
+    constexpr int GRID = G::GRID, NT = G::NT, TR = G::TR, PD = G::PD, RING = G::RING, SLOT = G::SLOT,
+                  SLOTP = G::SLOTP, PUB = G::PUB, NU = G::NU;
+    constexpr int LDL = ColSmem<T, KB>::LDL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *raw = reinterpret_cast<double *>(smem_raw);  // [RING][SLOT] staged band values
+    T *cv_ = reinterpret_cast<T *>(raw + RING * SLOT);   // [2][SLOTP] converted, by step parity:
+    //   ER [TR][KB] entering rows by column residue, EC [TR][KB] entering columns by row residue,
+    //   FR [TR][TR] far pivot-row entries, FC [TR][TR] far pivot-column entries (of the next step)
+    T *pub = cv_ + 2 * SLOTP;                            // [2][PUB] published, by step parity:
+    //   PB [TR][TR] pivot block, RB [TR][KB] pivot rows by column residue, CB [TR][KB] pivot columns by row residue
+    T *LS = pub + 2 * PUB;                               // [2][KB][LDL] multipliers [column][row residue]
+
+    const int part = blockIdx.x;
+    const int64_t s0 = P.off[part], ni = P.off[part + 1] - s0, b0 = P.boff[part];
+    const int nb = (int)(P.boff[part + 1] - b0);
+    const int NP = nb * KB;  // padded columns of the partition
+    const int NG = nb * GRID;
+    const int t = threadIdx.x, ty = t / GRID, tx = t % GRID;
+
+    // partition-local entry, identity beyond the partition
+    auto entry = [&](int64_t i, int64_t l) -> double {
+        if (i >= ni || l >= ni) return (i == l) ? 1.0 : 0.0;
+        const int64_t d = k + i - l;
+        return (d < 0 || d > 2 * k) ? 0.0 : band[d * ld + s0 + l];
+    };
+    // Thread t stages slots e = t + u NT of every step; slot e of the step at
+    // column jb is entry(jb + iofs, jb + lofs), one band diagonal:
+    //   e < TR KB:    entering row jb+KB+v at column jb+KB+TR-1-o    (v = e / KB, o = e % KB)
+    //   e < 2 TR KB:  entering column jb+KB+v at row jb+KB+TR-1-o
+    //   next:         far pivot-row entry a_{jb+TR+u, jb+TR+KB+v}   (u, v < TR)
+    //   last:         far pivot-column entry a_{jb+TR+KB+v, jb+TR+u}
+    // The entering values go to the residue (jb + TR-1-o) mod KB.
+    const double *src[NU];
+    int so[NU], rofs[NU], hi_ofs[NU];
+    bool live[NU], inb[NU], idn[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int e = t + u * NT;
+        live[u] = e < SLOT;
+        so[u] = e;
+        int iofs, lofs;
+        rofs[u] = 0;
+        if (e < TR * KB) {
+            const int v = e / KB, o = e % KB;
+            iofs = KB + v; lofs = KB + TR - 1 - o; rofs[u] = TR - 1 - o;
+        } else if (e < 2 * TR * KB) {
+            const int v = (e - TR * KB) / KB, o = (e - TR * KB) % KB;
+            iofs = KB + TR - 1 - o; lofs = KB + v; rofs[u] = TR - 1 - o;
+        } else if (e < 2 * TR * KB + TR * TR) {
+            const int uu = (e - 2 * TR * KB) / TR, v = (e - 2 * TR * KB) % TR;
+            iofs = TR + uu; lofs = TR + KB + v;
+        } else {
+            const int uu = (e - 2 * TR * KB - TR * TR) / TR, v = (e - 2 * TR * KB - TR * TR) % TR;
+            iofs = TR + KB + v; lofs = TR + uu;
+        }
+        if (!live[u]) { iofs = 0; lofs = 0; }
+        const int dg = k + iofs - lofs;
+        inb[u] = live[u] && dg >= 0 && dg <= 2 * k;
+        src[u] = band + s0 + lofs + (inb[u] ? (int64_t)dg * ld : 0);
+        hi_ofs[u] = iofs > lofs ? iofs : lofs;  // beyond the partition once jb + hi_ofs >= ni
+        idn[u] = iofs == lofs;
+    }
+    auto stage = [&](int Gs) {
+        double *r = raw + (Gs % RING) * SLOT + t;
+        const int jb = Gs * TR;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            if (!live[u]) continue;
+            if (inb[u] && jb + hi_ofs[u] < ni) cp_async_small<8>(r + u * NT, src[u] + jb);
+            else r[u * NT] = (jb + hi_ofs[u] >= ni && idn[u]) ? 1.0 : 0.0;
+        }
+    };
+    auto convert = [&](int Gs) {
+        const double *r = raw + (Gs % RING) * SLOT + t;
+        T *c = cv_ + (Gs & 1) * SLOTP;
+        const int jb = Gs * TR;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            if (!live[u]) continue;
+            const int e = so[u];
+            int pos = e;  // far entries keep their slot
+            if (e < 2 * TR * KB) pos = (e / KB) * KB + ((jb + rofs[u]) & (KB - 1));
+            c[pos] = from_f64<T>(r[u * NT]);
+        }
+    };
+
+    // window of columns 0..KB-1; published pivot block, rows and columns of step 0
+    T w[TR][TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int c = 0; c < TR; ++c) w[r][c] = (T)entry(ty * TR + r, tx * TR + c);
+    for (int e = t; e < PUB; e += NT) {
+        T v;
+        if (e < TR * TR) v = (T)entry(e / TR, e % TR);
+        else if (e < TR * TR + TR * KB) {
+            const int u = (e - TR * TR) / KB, gm = (e - TR * TR) % KB;
+            v = (T)(gm < TR ? entry(u, KB + gm) : entry(u, gm));
+        } else {
+            const int u = (e - TR * TR - TR * KB) / KB, rh = (e - TR * TR - TR * KB) % KB;
+            v = (T)(rh < TR ? entry(KB + rh, u) : entry(rh, u));
+        }
+        pub[e] = v;
+    }
+    for (int e = t; e < KB * KB; e += NT)  // no L_{0,-1}
+        if (e / KB <= e % KB) LT[b0 * KB * KB + e] = T(0);
+    for (int Gs = 0; Gs < PD; ++Gs) {
+        if (Gs < NG) stage(Gs);
+        cp_async_commit();
+    }
+    cp_async_wait<PD - 1>();
+    convert(0);
+
+    for (int Gi = 0; Gi < NG; ++Gi) {
+        const int g = Gi % GRID, J = Gi / GRID, j = Gi * TR;
+        const bool rowg = (ty == g), colg = (tx == g);
+        __syncthreads();
+        // ring slot of step Gi-1 (converted during step Gi-2); step Gi+1 into the other parity
+        if (Gi + PD < NG) stage(Gi + PD);
+        cp_async_commit();
+        cp_async_wait<PD - 1>();
+        if (Gi + 1 < NG) convert(Gi + 1);
+        if (J > 0) {  // tile rows g*TR.. of the previous block's multipliers
+            const T *ls = LS + ((J - 1) & 1) * KB * LDL;
+            T *lt = LT + (b0 + J - 1) * KB * KB;
+            for (int e = t; e < TR * KB; e += NT) {
+                const int a2 = g * TR + e / KB, b = e % KB;
+                lt[(a2 > b ? 0 : KB * KB) + a2 * KB + b] = ls[b * LDL + a2];
+            }
+        }
+        const T *PB = pub + (Gi & 1) * PUB, *RB = PB + TR * TR, *CB = RB + TR * KB;
+        const T *cg = cv_ + (Gi & 1) * SLOTP;
+        // pivot block P = L_p U_p (every thread; U_p in place, unit L_p below it)
+        T pv[TR][TR], pinv[TR];
+#pragma unroll
+        for (int u = 0; u < TR; ++u) ld_row<T, TR>(PB + u * TR, pv[u]);
+#pragma unroll
+        for (int p = 0; p < TR; ++p) {
+            if (t == 0 && !usable_pivot<T>(pv[p][p]))
+                atomicMin((unsigned long long *)status, (unsigned long long)(s0 + j + p));
+            pinv[p] = fast_rcp<T>(pv[p][p]);
+#pragma unroll
+            for (int q = p + 1; q < TR; ++q) {
+                const T l = pv[q][p] * pinv[p];
+                pv[q][p] = l;
+#pragma unroll
+                for (int c = p + 1; c < TR; ++c) pv[q][c] -= l * pv[p][c];
+            }
+        }
+        // pivot-row entries of my columns: L_p^{-1} R;  multipliers of my rows: C U_p^{-1}
+        T ur[TR][TR], m[TR][TR];  // ur[u][c], m[r][u]
+#pragma unroll
+        for (int u = 0; u < TR; ++u) {
+            ld_row<T, TR>(RB + u * KB + tx * TR, ur[u]);
+#pragma unroll
+            for (int p = 0; p < u; ++p)
+#pragma unroll
+                for (int c = 0; c < TR; ++c) ur[u][c] -= pv[u][p] * ur[p][c];
+        }
+        {
+            T cb[TR][TR];  // cb[u][r]
+#pragma unroll
+            for (int u = 0; u < TR; ++u) ld_row<T, TR>(CB + u * KB + ty * TR, cb[u]);
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int u = 0; u < TR; ++u) {
+                    T y = cb[u][r];
+#pragma unroll
+                    for (int p = 0; p < u; ++p) y -= m[r][p] * pv[p][u];
+                    m[r][u] = y * pinv[u];
+                }
+        }
+        // rows and columns j..j+TR-1 leave; rows and columns j+KB.. enter
+        if (rowg) {
+#pragma unroll
+            for (int v = 0; v < TR; ++v) ld_row<T, TR>(cg + v * KB + tx * TR, w[v]);
+        }
+        if (colg) {
+#pragma unroll
+            for (int v = 0; v < TR; ++v) {
+                T ec[TR];
+                ld_row<T, TR>(cg + TR * KB + v * KB + ty * TR, ec);
+#pragma unroll
+                for (int r = 0; r < TR; ++r) w[r][v] = ec[r];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TR; ++u)
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int c = 0; c < TR; ++c) w[r][c] -= m[r][u] * ur[u][c];
+        // outputs: multipliers (staged), scaled pivot rows, 1/u_jj; in the leaving
+        // slots the pivot block's own L_p (below) and U_p (above) entries
+        if (tx == 0) {
+            T *ls = LS + (J & 1) * KB * LDL;
+#pragma unroll
+            for (int u = 0; u < TR; ++u) {
+                T v[TR];
+#pragma unroll
+                for (int r = 0; r < TR; ++r) v[r] = (rowg && r > u) ? pv[r][u] : m[r][u];
+                st_row<T, TR>(ls + (g * TR + u) * LDL + ty * TR, v);
+            }
+        }
+        if (ty == 0) {
+            T *ut = UT + ((b0 + J) * KB + g * TR) * KB + tx * TR;
+#pragma unroll
+            for (int u = 0; u < TR; ++u) {
+                T v[TR];
+#pragma unroll
+                for (int c = 0; c < TR; ++c) v[c] = ((colg && c > u) ? pv[u][c] : ur[u][c]) * pinv[u];
+                st_row<T, TR>(ut + u * KB, v);
+            }
+        }
+        if (t == 0) {
+#pragma unroll
+            for (int u = 0; u < TR; ++u) DI[b0 * KB + j + u] = pinv[u];
+        }
+        // publish the next step
+        if (j + TR < NP) {
+            const int g1 = (g + 1) % GRID;
+            T *PB1 = pub + ((Gi + 1) & 1) * PUB, *RB1 = PB1 + TR * TR, *CB1 = RB1 + TR * KB;
+            if (ty == g1 && tx == g1) {
+#pragma unroll
+                for (int u = 0; u < TR; ++u) {
+                    st_row<T, TR>(PB1 + u * TR, w[u]);
+                    T fr[TR], fc[TR];
+                    ld_row<T, TR>(cg + 2 * TR * KB + u * TR, fr);
+                    ld_row<T, TR>(cg + 2 * TR * KB + TR * TR + u * TR, fc);
+                    st_row<T, TR>(RB1 + u * KB + g1 * TR, fr);
+                    st_row<T, TR>(CB1 + u * KB + g1 * TR, fc);
+                }
+            } else if (ty == g1) {
+#pragma unroll
+                for (int u = 0; u < TR; ++u) st_row<T, TR>(RB1 + u * KB + tx * TR, w[u]);
+            } else if (tx == g1) {
+#pragma unroll
+                for (int u = 0; u < TR; ++u) {
+                    T v[TR];
+#pragma unroll
+                    for (int r = 0; r < TR; ++r) v[r] = w[r][u];
+                    st_row<T, TR>(CB1 + u * KB + ty * TR, v);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // multipliers of the last block (no block below it)
+    for (int e = t; e < KB * KB; e += NT) {
+        const int a = e / KB, b = e % KB;
+        if (a > b) LT[(b0 + nb - 1) * KB * KB + e] = LS[((nb - 1) & 1) * KB * LDL + b * LDL + a];
+    }
+}
+
+// The same factorisation one column per step (FP64: the TR-column step's
+// registers (pivot block, pivot-row entries and multipliers in doubles) would
+// leave room for only one CTA per SM).  Per column: one barrier; the owners of
+// pivot row and column j+1 publish them after the rank-1 update; staging,
+// conversion and flushing are spread over the columns of each group of TR.
+template <typename T, int KB> struct Col1Geo {
     static constexpr int GRID = KB >= 16 ? 16 : 8;   // thread grid GRID x GRID
     static constexpr int NT = GRID * GRID;
     static constexpr int TR = KB / GRID;             // residues per thread and direction; columns per group
@@ -71,8 +353,8 @@ template <typename T, int KB> struct ColGeo {
     static constexpr int NU = (SLOT + NT - 1) / NT;  // staged values per thread and group
 };
 
-template <typename T, int KB> struct ColSmem {
-    using G = ColGeo<T, KB>;
+template <typename T, int KB> struct Col1Smem {
+    using G = Col1Geo<T, KB>;
     static constexpr int LDL = KB + 16 / (int)sizeof(T);  // multiplier staging row stride
     static constexpr size_t raw = (size_t)G::RING * G::SLOT * 8;
     static constexpr size_t cvt = (size_t)2 * G::TR * G::CWP * sizeof(T);
@@ -80,13 +362,13 @@ template <typename T, int KB> struct ColSmem {
 };
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(ColGeo<T, KB>::NT)
-    k_band_lu_col(const double *__restrict__ band, int64_t ld, int k, Parts P, T *__restrict__ LT,
+__global__ void __launch_bounds__(Col1Geo<T, KB>::NT)
+    k_band_lu_col1(const double *__restrict__ band, int64_t ld, int k, Parts P, T *__restrict__ LT,
                   T *__restrict__ UT, T *__restrict__ DI, int64_t *__restrict__ status) {
-    using G = ColGeo<T, KB>;
+    using G = Col1Geo<T, KB>;
     constexpr int GRID = G::GRID, NT = G::NT, TR = G::TR, PD = G::PD, RING = G::RING, CW = G::CW,
                   CWP = G::CWP, SLOT = G::SLOT, NU = G::NU;
-    constexpr int LDL = ColSmem<T, KB>::LDL;
+    constexpr int LDL = Col1Smem<T, KB>::LDL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *raw = reinterpret_cast<double *>(smem_raw);  // [RING][SLOT] staged band values
     T *cv_ = reinterpret_cast<T *>(raw + RING * SLOT);   // [2][TR][CWP] converted, by group parity:
@@ -394,12 +676,21 @@ template <typename T, int KB>
 static bool col_impl(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
     const size_t sm1 = ColSmem<T, KB>::bytes, sm2 = InvGeo<T, KB>::bytes;
-    cudaFuncSetAttribute(k_band_lu_col<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if constexpr (sizeof(T) == 4)
+        cudaFuncSetAttribute(k_band_lu_col<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     cudaFuncSetAttribute(k_band_lu_inv<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-    if (!launch(c, KID_LU, [&] {
-            k_band_lu_col<T, KB><<<c->p, ColGeo<T, KB>::NT, sm1, c->stream>>>(
-                c->band, c->ld, c->k, P, (T *)c->LT, (T *)c->UT, (T *)c->DI, c->status);
-        }))
+    if constexpr (sizeof(T) == 8) {
+        const size_t smc = Col1Smem<T, KB>::bytes;
+        cudaFuncSetAttribute(k_band_lu_col1<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+        if (!launch(c, KID_LU, [&] {
+                k_band_lu_col1<T, KB><<<c->p, Col1Geo<T, KB>::NT, smc, c->stream>>>(
+                    c->band, c->ld, c->k, P, (T *)c->LT, (T *)c->UT, (T *)c->DI, c->status);
+            }))
+            return false;
+    } else if (!launch(c, KID_LU, [&] {
+                   k_band_lu_col<T, KB><<<c->p, ColGeo<T, KB>::NT, sm1, c->stream>>>(
+                       c->band, c->ld, c->k, P, (T *)c->LT, (T *)c->UT, (T *)c->DI, c->status);
+               }))
         return false;
     return launch(c, KID_LU_INV, [&] {
         k_band_lu_inv<T, KB><<<(unsigned)c->NB, InvGeo<T, KB>::NT, sm2, c->stream>>>((T *)c->LT, (T *)c->UT);

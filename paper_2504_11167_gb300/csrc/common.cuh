@@ -99,16 +99,18 @@ template <> __device__ __forceinline__ bool usable_pivot<double>(double v) { ret
 //   - rebias the exponent: for binary64 exponents of normal binary32 numbers
 //     (897..1150, i.e. 2^-126 <= |v| < 2^128), e - 896 equals the low 8 bits
 //     of e with the top bit flipped.
-// Magnitudes below 2^-126 become signed zero.  2^128 and above, Inf and NaN
-// take the hardware conversion.
+// Branch-free (selects only, so no predicated FP64 instruction is issued):
+// magnitudes below 2^-126 become signed zero, 2^128 and above (Inf, NaN
+// included) become signed infinity.
 __device__ __forceinline__ float d2f_rn(double v) {
     unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned hi = (unsigned)(b >> 32), mag = hi & 0x7FFFFFFFu;
-    if (mag >= 0x47F00000u) return (float)v;
-    if (mag < 0x38100000u) return __int_as_float((int)(hi & 0x80000000u));
+    const unsigned hi = (unsigned)(b >> 32), mag = hi & 0x7FFFFFFFu, sign = hi & 0x80000000u;
     b += 0x0FFFFFFFull + ((b >> 29) & 1ull);
     const unsigned bits = __funnelshift_l((unsigned)b, (unsigned)(b >> 32), 3);
-    return __int_as_float((int)(((bits ^ 0x40000000u) & 0x7FFFFFFFu) | (hi & 0x80000000u)));
+    unsigned r = ((bits ^ 0x40000000u) & 0x7FFFFFFFu) | sign;
+    r = (mag < 0x38100000u) ? sign : r;
+    r = (mag >= 0x47F00000u) ? (sign | 0x7F800000u) : r;
+    return __int_as_float((int)r);
 }
 template <typename T> __device__ __forceinline__ T from_f64(double v);
 template <> __device__ __forceinline__ float from_f64<float>(double v) { return d2f_rn(v); }
