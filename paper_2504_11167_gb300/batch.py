@@ -12,8 +12,9 @@ reports every system's final residual.
 Shapes: the number of partitions p and the block size KB of each system.  The
 default rule takes partitions of about 4096 rows (p = max(2, n // 4096), every
 partition longer than k) and the smallest block that holds k; `autotune`
-times candidate shapes on a representative system of each (k, size class) and
-keeps the fastest.
+times candidate shapes on copies of a representative system of each (k, size
+class) running together in one graph (enough to fill the GPU), and keeps the
+one with the highest throughput when it beats the default rule clearly.
 """
 from __future__ import annotations
 
@@ -139,6 +140,7 @@ class BatchSolver:
         return sum(b.shape[1] * (f.shape[0] if f.dim() == 2 else 1) for b, f, _ in self.systems)
 
     def close(self):
+        self.graph = None
         for s in self.handles:
             s.close()
         self.handles = []
@@ -146,35 +148,53 @@ class BatchSolver:
 
 def autotune(classes: Dict[Tuple[int, int], Tuple], precision: str = "fp32", iterations: int = 6,
              reps: int = 3, tol: float = 1e-10,
-             r_of_k: Callable[[int], int] = lambda k: max(1, k // 4)) -> Dict[Tuple[int, int], Shape]:
-    """classes: {(k, size class): (band, f) of a representative system}.  For
-    every class, times factor + graph-safe solve of each candidate shape with
-    CUDA events (median of `reps` after one warm-up) and returns the fastest
-    shape per class."""
+             r_of_k: Callable[[int], int] = lambda k: max(1, k // 4), max_copies: int = 8,
+             margin: float = 0.05) -> Dict[Tuple[int, int], Shape]:
+    """classes: {(k, size class): (band, f) of a representative system}.
+
+    A batch keeps the GPU full, so the objective is throughput, not one
+    system's latency: for every class and candidate shape (the default rule's
+    shape included), copies of the representative system are captured into
+    one graph the way a batch runs them (side streams, concurrently), enough
+    copies for about two partitions per SM (at most `max_copies`), and the
+    replays are timed with CUDA events (median of `reps` after one warm-up).
+    The shape with the least time per solved unknown wins; it replaces the
+    default rule only when it is at least `margin` faster."""
     import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     best = {}
     for (k, cls), (band, f) in classes.items():
         n = band.shape[1]
-        F = f.unsqueeze(0) if f.dim() == 1 else f
-        timings = []
-        for p, block in candidate_shapes(n, k):
-            r = min(r_of_k(k), k) if p > 1 else 0
-            s = LRSpike(n, k, p, r, precision=precision, reduced="truncated", outer="ir", tol=tol,
-                        max_iter=iterations, max_nrhs=F.shape[0], graph_safe=True, block=block)
-            x = torch.empty_like(F)
-            ts = []
-            for rep in range(reps + 1):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                s.factor(band)
-                s.solve(F, x)
-                e1.record()
-                torch.cuda.synchronize()
-                if rep:
-                    ts.append(e0.elapsed_time(e1))
-            info = s.finish(nrhs=F.shape[0], allow_unconverged=True)
-            s.close()
-            if info["converged"]:
-                timings.append((sorted(ts)[len(ts) // 2], (p, block)))
-        best[(k, cls)] = min(timings)[1] if timings else default_shape(n, k)
+        d = default_shape(n, k)
+        cands = candidate_shapes(n, k)
+        if d not in cands:
+            cands.append(d)
+        timings = {}
+        for p, block in cands:
+            copies = max(2, min(max_copies, -(-2 * sms // p)))
+            bs = BatchSolver([(band, f, k)] * copies, shapes=[(p, block)] * copies, precision=precision,
+                             iterations=iterations, tol=tol, r_of_k=r_of_k, streams=copies)
+            try:
+                bs.capture()
+                ts = []
+                for rep in range(reps + 1):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    bs.replay()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if rep:
+                        ts.append(e0.elapsed_time(e1))
+                infos = bs.finish(allow_unconverged=True)
+                if all(i["converged"] for i in infos):
+                    timings[(p, block)] = sorted(ts)[len(ts) // 2] / (copies * n)
+            finally:
+                bs.close()
+        if not timings:
+            best[(k, cls)] = d
+            continue
+        shape = min(timings, key=timings.get)
+        if d in timings and timings[shape] > (1.0 - margin) * timings[d]:
+            shape = d
+        best[(k, cls)] = shape
     return best

@@ -622,10 +622,21 @@ __global__ void __launch_bounds__(InvGeo<T, KB>::NT) k_band_lu_inv(T *__restrict
     T *Ms = reinterpret_cast<T *>(smem_raw);  // [2][KB][LDM]: L_JJ, P (D^{-1}U_JJ) P; inverted in place
     T *lt = LT + (int64_t)blockIdx.x * KB * KB, *ut = UT + (int64_t)blockIdx.x * KB * KB;
     const int t = threadIdx.x;
-    for (int e = t; e < KB * KB; e += NT) {
-        const int a = e / KB, b = e % KB;
-        Ms[a * LDM + b] = (a > b) ? lt[e] : T(0);
-        Ms[KB * LDM + (KB - 1 - a) * LDM + (KB - 1 - b)] = (a < b) ? ut[e] : T(0);
+    // 4-vectors of a tile row: (a, b..b+3); U is stored reversed, so its
+    // vector lands at columns KB-4-b.. in reverse order
+    constexpr int C4 = KB * KB / 4;
+    for (int e = t; e < C4; e += NT) {
+        const int a = (4 * e) / KB, b = (4 * e) % KB;
+        T lv[4], uv[4], lo[4], uo[4];
+        ld_row<T, 4>(lt + 4 * e, lv);
+        ld_row<T, 4>(ut + 4 * e, uv);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            lo[w] = (a > b + w) ? lv[w] : T(0);
+            uo[3 - w] = (a < b + w) ? uv[w] : T(0);
+        }
+        st_row<T, 4>(Ms + a * LDM + b, lo);
+        st_row<T, 4>(Ms + KB * LDM + (KB - 1 - a) * LDM + (KB - 4 - b), uo);
     }
     __syncthreads();
     // diagonal halves: thread t -> matrix t / 2H, half (t / H) % 2, column t % H
@@ -640,19 +651,22 @@ __global__ void __launch_bounds__(InvGeo<T, KB>::NT) k_band_lu_inv(T *__restrict
             if (i >= c) Md[i * LDM + c] = (i == c) ? T(1) : x[i];  // unit diagonal kept for the products
         __syncthreads();
     }
-    // off-diagonal half: T21 = M21 X11 (X11 lower: q >= j0), then X21 = -X22 T21 (X22 lower: q <= i0 + 3)
+    // off-diagonal half: T21 = M21 X11 (X11 lower: q >= j0), then X21 = -X22 T21 (X22 lower: q <= i0 + 3).
+    // The trip count of the first product depends on the tile column, of the second on
+    // the tile row: tiles go column-major, then row-major, so that a warp's tiles agree.
     const bool act = t < 2 * TILES;
     T *Mm = Ms + (t / TILES) * KB * LDM;
-    const int tile = t % TILES, i0 = (tile / (H / 4)) * 4, j0 = (tile % (H / 4)) * 4;
+    const int tile = t % TILES, ta = tile / (H / 4), tb = tile % (H / 4);
     T *X11 = Mm, *M21 = Mm + H * LDM, *X22 = Mm + H * LDM + H;
     T acc[4][4];
-    if (act) tile4_mac<T>(M21, X11, LDM, i0, j0, j0, H, acc);
+    if (act) tile4_mac<T>(M21, X11, LDM, tb * 4, ta * 4, ta * 4, H, acc);
     __syncthreads();
     if (act) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) st_row<T, 4>(M21 + (i0 + i) * LDM + j0, acc[i]);
+        for (int i = 0; i < 4; ++i) st_row<T, 4>(M21 + (tb * 4 + i) * LDM + ta * 4, acc[i]);
     }
     __syncthreads();
+    const int i0 = ta * 4, j0 = tb * 4;
     if (act) tile4_mac<T>(X22, M21, LDM, i0, j0, 0, i0 + 4, acc);
     __syncthreads();
     if (act) {
@@ -665,10 +679,23 @@ __global__ void __launch_bounds__(InvGeo<T, KB>::NT) k_band_lu_inv(T *__restrict
         }
     }
     __syncthreads();
-    for (int e = t; e < KB * KB; e += NT) {
-        const int a = e / KB, b = e % KB;
-        if (a > b) lt[e] = Ms[a * LDM + b];
-        else if (a < b) ut[e] = Ms[KB * LDM + (KB - 1 - a) * LDM + (KB - 1 - b)];
+    // strict triangles back: whole 4-vectors inside a triangle, single entries on its edge
+    for (int e = t; e < C4; e += NT) {
+        const int a = (4 * e) / KB, b = (4 * e) % KB;
+        T lv[4], uv[4], ur_[4];
+        ld_row<T, 4>(Ms + a * LDM + b, lv);
+        ld_row<T, 4>(Ms + KB * LDM + (KB - 1 - a) * LDM + (KB - 4 - b), ur_);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) uv[w] = ur_[3 - w];
+        if (b + 3 < a) st_row<T, 4>(lt + 4 * e, lv);
+        else if (b > a) st_row<T, 4>(ut + 4 * e, uv);
+        else {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                if (a > b + w) lt[4 * e + w] = lv[w];
+                else if (a < b + w) ut[4 * e + w] = uv[w];
+            }
+        }
     }
 }
 

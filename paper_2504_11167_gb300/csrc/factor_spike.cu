@@ -533,25 +533,38 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
                 pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
             }
             __syncthreads();
-            for (int it = threadIdx.x; it < NP * KB; it += NT) {  // rows p, q
-                const int i = it / KB, j = it % KB;
+            // warp w applies the rotations of pairs w*PPW.. in turn, its lanes over
+            // consecutive entries (conflict-free); a pair's indices and
+            // coefficients are read once per pass
+            constexpr int NWJ = NT / 32, PPW = (NP + NWJ - 1) / NWJ;  // warps, pairs per warp
+            const int wj = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+            for (int ii = 0; ii < PPW; ++ii) {  // rows p, q
+                const int i = wj * PPW + ii;
+                if (i >= NP) break;
                 const int p = pp[i], q = qq[i];
                 const T c = cs[i], s = sn[i];
-                const T ap = A[p * LD + j], aq = A[q * LD + j];
-                A[p * LD + j] = c * ap - s * aq;
-                A[q * LD + j] = s * ap + c * aq;
+                for (int j = lane; j < KB; j += 32) {
+                    const T ap = A[p * LD + j], aq = A[q * LD + j];
+                    A[p * LD + j] = c * ap - s * aq;
+                    A[q * LD + j] = s * ap + c * aq;
+                }
             }
             __syncthreads();
-            for (int it = threadIdx.x; it < NP * KB; it += NT) {  // columns p, q and V
-                const int i = it / KB, j = it % KB;
+#pragma unroll
+            for (int ii = 0; ii < PPW; ++ii) {  // columns p, q and V
+                const int i = wj * PPW + ii;
+                if (i >= NP) break;
                 const int p = pp[i], q = qq[i];
                 const T c = cs[i], s = sn[i];
-                const T ap = A[j * LD + p], aq = A[j * LD + q];
-                A[j * LD + p] = c * ap - s * aq;
-                A[j * LD + q] = s * ap + c * aq;
-                const T vp = V[j * LD + p], vq = V[j * LD + q];
-                V[j * LD + p] = c * vp - s * vq;
-                V[j * LD + q] = s * vp + c * vq;
+                for (int j = lane; j < KB; j += 32) {
+                    const T ap = A[j * LD + p], aq = A[j * LD + q];
+                    A[j * LD + p] = c * ap - s * aq;
+                    A[j * LD + q] = s * ap + c * aq;
+                    const T vp = V[j * LD + p], vq = V[j * LD + q];
+                    V[j * LD + p] = c * vp - s * vq;
+                    V[j * LD + q] = s * vp + c * vq;
+                }
             }
             __syncthreads();
         }
