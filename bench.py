@@ -169,7 +169,7 @@ class ClockSampler:
 # DRAM bytes (read + write) per launch at this workload, from one ncu capture of
 # the quarter-size case (python bench.py --profile-case: n/4 rows, p/4
 # partitions, same n_i) scaled by 4 (both grow with n).  None = not captured.
-NCU_TRAFFIC = {"band_lu": 4 * (1.080680e9 + 0.511967e9), "band_lu_inv": 4 * (0.394333e9 + 0.249154e9)}
+NCU_TRAFFIC = {"band_lu": 4 * (1.081185e9 + 0.512351e9), "band_lu_inv": 4 * (0.536948e9 + 0.251501e9)}
 
 
 def kernel_work(name: str, prof: dict, precision_bytes: int):
