@@ -603,6 +603,139 @@ def bicgstab(ab, k, fac: Factor, f: np.ndarray, tol: float = 1e-12, max_iter: in
 
 
 # --------------------------------------------------------------------------
+# LR-SPIKE-OTF (section 2.1, "SPIKE-on-the-fly", eqs. 'OTF-1' and 'OTF-2';
+# section 3.3: the truncated low-rank reduced system as its preconditioner).
+# The TRUE reduced system of the spike matrix S = D^{-1} A is solved
+# iteratively on the interface tips y_i = [x_{i,b} ; x_{i+1,t}] (2k per
+# interface i = 1..p-1).  A product with the spikes is never formed: the spike
+# terms of partition i act through one solve with A_i on the vector
+#     c_i = [C_i x_{i-1,b} ; 0 ; B_i x_{i+1,t}]
+# (eqs. OTF-1/OTF-2 applied right to left, both spikes at once by linearity):
+#     (S_red y)_i = y_i + tips(A^{-1} c(y))_i.
+# The preconditioner is S~~_r restricted to one interface,
+#     [[I, T~_{i,b}], [W~_{i+1,t}, I]],  T~_{i,b} = u_{T,i}^(b) P_i, W~_{i+1,t} = u_{W,i+1}^(t) Q_{i+1},
+# inverted by Woodbury through the 2r x 2r block E_i of the truncated reduced
+# matrix.  Reduced BiCGStab to a tolerance (1e-8 by default, as in the paper's
+# experiments), then the recovery x = g - A^{-1} c(y) with g = D^{-1} f.
+# --------------------------------------------------------------------------
+def otf_tips(fac: Factor, v: np.ndarray) -> np.ndarray:
+    """Interface tips of a full vector: y_i = [v(s_{i+1}-k : s_{i+1}) ; v(s_{i+1} : s_{i+1}+k)]."""
+    k, offs = fac.k, fac.offs
+    V = v.reshape(fac.n, -1)
+    y = np.zeros((fac.p - 1, 2 * k, V.shape[1]))
+    for i in range(fac.p - 1):
+        s = int(offs[i + 1])
+        y[i, :k] = V[s - k: s]
+        y[i, k:] = V[s: s + k]
+    return y
+
+
+def otf_coupling(fac: Factor, ab: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """c_i = [C_i x_{i-1,b} ; 0 ; B_i x_{i+1,t}] for all partitions (zero elsewhere)."""
+    k, offs = fac.k, fac.offs
+    c = np.zeros((fac.n, y.shape[2]))
+    for i in range(fac.p - 1):
+        s = int(offs[i + 1])
+        B = coupling_B(ab, k, s)          # rows s-k..s-1, columns s..s+k-1
+        C = coupling_C(ab, k, s)          # rows s..s+k-1, columns s-k..s-1
+        c[s - k: s] += B @ y[i, k:]       # B_i x_{i+1,t} on the bottom rows of partition i
+        c[s: s + k] += C @ y[i, :k]       # C_{i+1} x_{i,b} on the top rows of partition i+1
+    return c
+
+
+def otf_S(fac: Factor, ab: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """The true reduced operator applied on the fly: y + tips(D^{-1} c(y))."""
+    return y + otf_tips(fac, d_solve(fac, otf_coupling(fac, ab, y)))
+
+
+def otf_prec(fac: Factor, y: np.ndarray) -> np.ndarray:
+    """S~~_r^{-1} per interface (Woodbury): out = y - [u_T^(b) ; u_W^(t)] E_i^{-1} [P_i y_t ; Q_{i+1} y_b]."""
+    k, r, offs = fac.k, fac.r, fac.offs
+    out = y.copy()
+    for i in range(fac.p - 1):
+        s = int(offs[i + 1])
+        si = int(offs[i])
+        sl = slice(2 * r * i, 2 * r * (i + 1))
+        E = fac.R_full[sl, sl]
+        w = np.concatenate([fac.PV[i] @ y[i, k:], fac.QW[i + 1] @ y[i, :k]], axis=0)
+        z = np.linalg.solve(E, w)
+        out[i, :k] -= fac.UV[i][s - k - si: s - si] @ z[:r]          # u_T of partition i, bottom rows
+        out[i, k:] -= fac.UW[i + 1][0:k] @ z[r:]                      # u_W of partition i+1, top rows
+    return out
+
+
+def otf_bicgstab(fac: Factor, ab: np.ndarray, b: np.ndarray, tol: float, max_iter: int):
+    """Right-preconditioned BiCGStab on S_red y = b, column by column (the
+    reduced residual |b - S_red y| / |b| <= tol).  Returns y and the largest
+    iteration count."""
+    Y = np.zeros_like(b)
+    its = 0
+    for q in range(b.shape[2]):
+        bq = b[:, :, q:q + 1]
+        bn = np.linalg.norm(bq) or 1.0
+        y = np.zeros_like(bq)
+        r = bq.copy()
+        rh = r.copy()
+        rho = alpha = omega = 1.0
+        v = np.zeros_like(bq)
+        pv = np.zeros_like(bq)
+        it = 0
+        while np.linalg.norm(r) / bn > tol and it < max_iter:
+            it += 1
+            rho_new = float(np.sum(rh * r))
+            beta = (rho_new / rho) * (alpha / omega)
+            pv = r + beta * (pv - omega * v)
+            ph = otf_prec(fac, pv)
+            v = otf_S(fac, ab, ph)
+            alpha = rho_new / float(np.sum(rh * v))
+            s = r - alpha * v
+            sh = otf_prec(fac, s)
+            t = otf_S(fac, ab, sh)
+            tt = float(np.sum(t * t))
+            omega = float(np.sum(t * s)) / tt if tt > 0 else 0.0
+            y = y + alpha * ph + omega * sh
+            r = s - omega * t
+            rho = rho_new
+        Y[:, :, q:q + 1] = y
+        its = max(its, it)
+    return Y, its
+
+
+def otf_apply(fac: Factor, ab: np.ndarray, f: np.ndarray, otf_tol: float = 1e-8, max_iter: int = 100):
+    """One LR-SPIKE-OTF solve: g = D^{-1} f; BiCGStab on S_red y = tips(g);
+    x = g - D^{-1} c(y).  Returns x and the reduced iteration count."""
+    g = d_solve(fac, f).reshape(fac.n, -1)
+    if fac.p < 2:
+        return g.reshape(f.shape), 0
+    y, its = otf_bicgstab(fac, ab, otf_tips(fac, g), otf_tol, max_iter)
+    x = g - d_solve(fac, otf_coupling(fac, ab, y))
+    return x.reshape(f.shape), its
+
+
+def otf_solve(ab, k, fac: Factor, f: np.ndarray, tol: float = 1e-12, max_iter: int = 20,
+              otf_tol: float = 1e-8) -> SolveResult:
+    """Outer refinement around OTF solves (the paper lowers the reduced tolerance
+    and restarts when the solution is not accurate enough; here every extra
+    pass solves for the correction of the current residual)."""
+    F = f.reshape(fac.n, -1)
+    fn = np.linalg.norm(F, axis=0)
+    fn[fn == 0] = 1.0
+    x = np.zeros_like(F)
+    hist = []
+    for it in range(max_iter + 1):
+        res = F - band_matvec(ab, k, x)
+        rel = np.linalg.norm(res, axis=0) / fn
+        hist.append(rel.copy())
+        if np.all(rel <= tol):
+            return SolveResult(x.reshape(f.shape), it, rel, hist, True)
+        if it == max_iter:
+            break
+        d, _ = otf_apply(fac, ab, res, otf_tol)
+        x = x + d.reshape(x.shape)
+    return SolveResult(x.reshape(f.shape), max_iter, rel, hist, False)
+
+
+# --------------------------------------------------------------------------
 # Gradient of a solve (the adjoint): x = A^{-1} f, L(x);  A^T lambda = dL/dx,
 # dL/df = lambda, dL/dA = -lambda x^T (band entries only)
 # --------------------------------------------------------------------------
