@@ -64,8 +64,20 @@ enum { LRSPIKE_FP64 = 0, LRSPIKE_MIXED_FP32 = 1, LRSPIKE_MIXED_TF32 = 2 };
 enum { LRSPIKE_COMPRESS_SPIKE = 0, LRSPIKE_COMPRESS_COUPLING = 1 };
 /* Reduced system (section 3.3, table 'solver-list'): FULL = the low-rank
  * reduced system of LR-SPIKE-I, solved directly; TRUNCATED = its truncated
- * block-diagonal form S~~_r of LR-SPIKE-T (eq. 'red_sys_prec_mid_2'). */
-enum { LRSPIKE_REDUCED_FULL = 0, LRSPIKE_REDUCED_TRUNCATED = 1 };
+ * block-diagonal form S~~_r of LR-SPIKE-T (eq. 'red_sys_prec_mid_2');
+ * OTF = LR-SPIKE-OTF (section 2.1 "SPIKE-on-the-fly", eqs. OTF-1/OTF-2;
+ * section 3.3): the TRUE reduced system on the interface tips
+ * [x_{i,b}; x_{i+1,t}] (2k per interface), solved by right-preconditioned
+ * BiCGStab to otf_tol, its spike products formed on the fly by solves with
+ * the partitions (one D-stage per product), preconditioned by S~~_r; then
+ * x = g - D^{-1}[C_i x_{i-1,b}; 0; B_i x_{i+1,t}].  Each application of the
+ * solver (the outer loop's correction) is one such solve, so one outer step
+ * gives the solution to about otf_tol.  Factorised like TRUNCATED.  Built
+ * for k <= 64 without pivoting, outer IR or NONE, not graph_safe;
+ * solve_transpose uses the TRUNCATED preconditioner.  Extra device memory:
+ * FP64 n x max_nrhs, working precision n x max_nrhs, 10 x 2k(p-1) x max_nrhs
+ * FP64. */
+enum { LRSPIKE_REDUCED_FULL = 0, LRSPIKE_REDUCED_TRUNCATED = 1, LRSPIKE_REDUCED_OTF = 2 };
 /* Outer iteration: IR = iterative refinement x += M^{-1}(f - A x);
  * BICGSTAB = right-preconditioned BiCGStab (the paper's outer solver, section
  * 4), FP64 vectors and scalars, one iteration = two applications of M^{-1};
@@ -111,6 +123,11 @@ typedef struct {
     /* block: the block size KB (8, 16, 32 or 64, >= the smallest block that
      * holds k; 0 = that smallest block).  A tuning knob for k <= 64. */
     int32_t block;
+    /* reduced = OTF: relative residual target of the reduced BiCGStab in each
+     * solve (default 1e-8, the paper's default) and its iteration limit
+     * (default 100; the last iterate is used when it is reached). */
+    double otf_tol;
+    int32_t otf_max_iter;
 } lrspike_options;
 
 typedef struct {
@@ -118,6 +135,7 @@ typedef struct {
     int32_t converged;        /* 1 if every column met tol                             */
     double max_rel_residual;  /* worst column's final ||f - A x|| / ||f||              */
     double *rel_residual;     /* caller-owned host array of >= nrhs entries, or NULL   */
+    int32_t reduced_iterations; /* reduced = OTF: reduced BiCGStab iterations, all outer steps */
 } lrspike_info;
 
 /* Fills *opt with defaults for n, k, p, r (FP64, no pivoting, SPIKE

@@ -16,7 +16,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "gram_reduce",  "coupling_gram", "jacobi",      "make_u",      "reduced_build",
     "reduced_factor", "norm",        "residual",    "dstage",      "reduced_solve",
     "retrieve",     "project_t",     "dstage_t",    "bicgstab_vector", "matvec",
-    "wide_gather",  "wide_gemm",     "wide_lu64",   "wide_vector", "nonzero_diagonals", "band_lu_inv"};
+    "wide_gather",  "wide_gemm",     "wide_lu64",   "wide_vector", "nonzero_diagonals", "band_lu_inv", "otf"};
 
 static cudaEvent_t take_event(Ctx *c) {
     if (!c->free_events.empty()) {
@@ -101,7 +101,7 @@ static void free_all(Ctx *c) {
                     c->PQ,    c->Gram,   c->Gpart, c->sigma, c->E, c->F,    c->Gs,    c->Rinv,
                     c->Gam,   c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
                     c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots,
-                    c->bpartial, c->PF, c->PIVP};
+                    c->bpartial, c->PF, c->PIVP, c->ocv, c->og, c->orv, c->osc, c->oone};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (double *p : c->bv)
@@ -138,6 +138,8 @@ extern "C" lrspike_status lrspike_options_default(lrspike_options *o, int64_t n,
     o->seed = 0x4C52535049ull;
     o->graph_safe = 0;
     o->block = 0;
+    o->otf_tol = 1e-8;
+    o->otf_max_iter = 100;
     return LRSPIKE_OK;
 }
 
@@ -152,7 +154,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     if (o.max_nrhs < 1 || o.max_nrhs > 16)
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "max_nrhs must be in 1..16");
     if (o.precision < LRSPIKE_FP64 || o.precision > LRSPIKE_MIXED_TF32 || o.compress < 0 || o.compress > 1 ||
-        o.reduced < 0 || o.reduced > 1 || o.outer < 0 || o.outer > 2 || o.pivoting < 0 || o.pivoting > 1)
+        o.reduced < 0 || o.reduced > 2 || o.outer < 0 || o.outer > 2 || o.pivoting < 0 || o.pivoting > 1)
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "unknown enum value in options");
     if (o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rank_tol >= 0.0))
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "max_iter, tol and rank_tol must be >= 0");
@@ -170,10 +172,23 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     if (wide && o.p > 1 && o.r > 0 && std::min(o.k, o.r + o.oversample) > 64)
         return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "min(k, r + oversample) > 64 sketch columns is not built");
     if (o.r > 32) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "r > 32 is not built yet");
+    if (o.reduced == LRSPIKE_REDUCED_OTF) {
+        if (o.p < 2 || o.r < 1)
+            return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "the OTF reduced system needs p >= 2 and r >= 1");
+        if (wide || o.pivoting || o.graph_safe || o.outer == LRSPIKE_OUTER_BICGSTAB)
+            return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED,
+                        "OTF is built for k <= 64 without pivoting, outer IR or NONE, not graph_safe");
+    }
+    if (!(o.otf_tol > 0.0) || o.otf_max_iter < 1)
+        return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "otf_tol must be > 0 and otf_max_iter >= 1");
 
     Ctx *c = new (std::nothrow) Ctx();
     if (!c) return fail(nullptr, LRSPIKE_ERR_OOM, "host allocation failed");
     c->opt = o;
+    if (o.reduced == LRSPIKE_REDUCED_OTF) {  // factorised as TRUNCATED (its preconditioner)
+        c->otf = true;
+        c->opt.reduced = LRSPIKE_REDUCED_TRUNCATED;
+    }
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
     c->n = o.n;
@@ -239,6 +254,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
              dalloc(&c->wr, ni * n2 * mx * 8);
     }
     if (ok && o.outer == LRSPIKE_OUTER_BICGSTAB) ok = bicgstab_alloc(c);
+    if (ok && c->otf) ok = otf_alloc(c);
     if (ok && wide) ok = wide_setup(c);
     if (ok) ok = cudaMallocHost((void **)&c->host, (8 * mx + 8) * 8) == cudaSuccess;
     if (!ok) {
@@ -362,6 +378,7 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
         }
         return LRSPIKE_OK;
     }
+    c->otf_iters = 0;
     const bool fdev = is_device_ptr(f), xdev = is_device_ptr(x);
     if (fdev != xdev) return fail(c, LRSPIKE_ERR_INVALID_ARG, "f and x must both be device or both host");
     const double *fd = f;
@@ -451,6 +468,7 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
     if (info) {
         info->iterations = it;
         info->converged = converged ? 1 : 0;
+        info->reduced_iterations = c->otf_iters;
         info->max_rel_residual = hist.empty() ? NAN : hist.back();
         if (info->rel_residual)
             for (int q = 0; q < nrhs; ++q) info->rel_residual[q] = hist.empty() ? NAN : rel[q];

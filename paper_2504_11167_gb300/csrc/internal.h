@@ -36,6 +36,7 @@ enum KernelId {
     KID_WIDE_VEC,
     KID_DIAGS,
     KID_LU_INV,
+    KID_OTF,
     KID_COUNT
 };
 
@@ -125,6 +126,14 @@ struct Ctx {
     size_t io_bytes = 0;
     bool factored = false;
     int last_nrhs = 0;        // graph_safe: columns of the last enqueued solve
+    // LR-SPIKE-OTF (reduced = OTF; the factorisation is the TRUNCATED one)
+    bool otf = false;
+    int otf_iters = 0;        // reduced BiCGStab iterations of the last solve
+    double *ocv = nullptr;    // FP64 n x max_nrhs: coupling right-hand side c(y)
+    void *og = nullptr;       // T, n x max_nrhs: g = D^{-1} f kept for the recovery
+    double *orv = nullptr;    // kOtfVecs reduced vectors [p-1][2k] x max_nrhs
+    double *osc = nullptr;    // reduced BiCGStab scalars
+    double *oone = nullptr;   // max_nrhs ones (unscaled D-stage input)
 
     std::string err;
     int64_t launches = 0;
@@ -167,6 +176,8 @@ bool run_norms(Ctx *c, const double *v, int64_t ld, int nrhs, double *out);
 bool run_residual(Ctx *c, const double *f, const double *x, int64_t ld, int nrhs, bool trans,
                   bool x_zero);
 bool run_dstage(Ctx *c, const double *rin, int64_t ld, int nrhs);
+// the same with the column scale factors of the input given explicitly
+bool run_dstage_inv(Ctx *c, const double *rin, int nrhs, const double *inv);
 bool run_reduced_solve(Ctx *c, int nrhs, bool trans);
 bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs, bool accumulate);
 bool run_project_t(Ctx *c, const double *hin, int64_t ld, int nrhs);
@@ -195,6 +206,10 @@ void set_handleless_error(const std::string &msg);
 // dimension n) whose column norms |in| and 1/|in| are at nrm + max_nrhs and
 // nrm + 2 max_nrhs: out (+)= |in| * M^{-1}(in/|in|).  Used by the outer loops.
 bool apply_precond(Ctx *c, const double *in, double *out, int64_t ldo, int nrhs, bool trans, bool accumulate);
+// LR-SPIKE-OTF (otf.cu): out (+)= |in| * (OTF solve of in/|in|)
+constexpr int kOtfVecs = 10;
+bool otf_alloc(Ctx *c);
+bool apply_otf(Ctx *c, const double *in, double *out, int64_t ldo, int nrhs, bool accumulate);
 
 // BiCGStab outer iteration (right-preconditioned, FP64 vectors).
 struct BicgResult {

@@ -577,25 +577,24 @@ static size_t dstage_smem(int nrhs) {
 }
 
 template <typename T, int KB, int NBUF>
-static bool dstage_launch(Ctx *c, const double *rin, int nrhs) {
+static bool dstage_launch(Ctx *c, const double *rin, int nrhs, const double *inv) {
     Parts P{c->off_d, c->boff_d, c->p};
     const size_t smem = dstage_smem<T, KB, NBUF>(nrhs);
     auto kern = k_dstage<T, KB, NBUF>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_DSTAGE, [&] {
         kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT, (const T *)c->DI,
-                                                     (const T *)c->PQ, P, c->k, c->r, c->n, rin,
-                                                     c->nrm + 2 * c->opt.max_nrhs, nrhs, (T *)c->Yv,
-                                                     (T *)c->Gv, c->psi);
+                                                     (const T *)c->PQ, P, c->k, c->r, c->n, rin, inv, nrhs,
+                                                     (T *)c->Yv, (T *)c->Gv, c->psi);
     });
 }
 
 // Four stage buffers (three steps of factor tiles in flight) while two CTAs
 // still fit on an SM; two otherwise.
 template <typename T, int KB>
-static bool dstage_impl(Ctx *c, const double *rin, int nrhs) {
-    if (dstage_smem<T, KB, 4>(nrhs) <= 110 * 1024) return dstage_launch<T, KB, 4>(c, rin, nrhs);
-    return dstage_launch<T, KB, 2>(c, rin, nrhs);
+static bool dstage_impl(Ctx *c, const double *rin, int nrhs, const double *inv) {
+    if (dstage_smem<T, KB, 4>(nrhs) <= 110 * 1024) return dstage_launch<T, KB, 4>(c, rin, nrhs, inv);
+    return dstage_launch<T, KB, 2>(c, rin, nrhs, inv);
 }
 
 template <typename T, int KB>
@@ -651,23 +650,27 @@ static bool project_t_impl(Ctx *c, const double *hin, int nrhs) {
     });
 }
 
-bool run_dstage(Ctx *c, const double *rin, int64_t, int nrhs) {
-    if (c->wide) return run_wide_dstage(c, rin, nrhs);
-    if (c->opt.pivoting) return run_dstage_piv(c, rin, nrhs);
+bool run_dstage_inv(Ctx *c, const double *rin, int nrhs, const double *inv) {
     if (c->fp64) {
         switch (c->KB) {
-            case 8: return dstage_impl<double, 8>(c, rin, nrhs);
-            case 16: return dstage_impl<double, 16>(c, rin, nrhs);
-            case 32: return dstage_impl<double, 32>(c, rin, nrhs);
-            default: return dstage_impl<double, 64>(c, rin, nrhs);
+            case 8: return dstage_impl<double, 8>(c, rin, nrhs, inv);
+            case 16: return dstage_impl<double, 16>(c, rin, nrhs, inv);
+            case 32: return dstage_impl<double, 32>(c, rin, nrhs, inv);
+            default: return dstage_impl<double, 64>(c, rin, nrhs, inv);
         }
     }
     switch (c->KB) {
-        case 8: return dstage_impl<float, 8>(c, rin, nrhs);
-        case 16: return dstage_impl<float, 16>(c, rin, nrhs);
-        case 32: return dstage_impl<float, 32>(c, rin, nrhs);
-        default: return dstage_impl<float, 64>(c, rin, nrhs);
+        case 8: return dstage_impl<float, 8>(c, rin, nrhs, inv);
+        case 16: return dstage_impl<float, 16>(c, rin, nrhs, inv);
+        case 32: return dstage_impl<float, 32>(c, rin, nrhs, inv);
+        default: return dstage_impl<float, 64>(c, rin, nrhs, inv);
     }
+}
+
+bool run_dstage(Ctx *c, const double *rin, int64_t, int nrhs) {
+    if (c->wide) return run_wide_dstage(c, rin, nrhs);
+    if (c->opt.pivoting) return run_dstage_piv(c, rin, nrhs);
+    return run_dstage_inv(c, rin, nrhs, c->nrm + 2 * c->opt.max_nrhs);
 }
 
 bool run_dstage_t(Ctx *c, const double *hin, int64_t, double *x, int64_t ldx, int nrhs, bool accumulate) {
@@ -701,6 +704,7 @@ bool run_project_t(Ctx *c, const double *hin, int64_t, int nrhs) {
 }
 
 bool apply_precond(Ctx *c, const double *in, double *out, int64_t ldo, int nrhs, bool trans, bool accumulate) {
+    if (c->otf && !trans) return apply_otf(c, in, out, ldo, nrhs, accumulate);
     if (!trans) {
         if (!run_dstage(c, in, c->n, nrhs)) return false;
         if (!run_reduced_solve(c, nrhs, false)) return false;

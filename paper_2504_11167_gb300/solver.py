@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "OOM", 4: "CUDA", 5: "SINGUL
           6: "NOT_CONVERGED", 7: "UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2}
 COMPRESS = {"spike": 0, "coupling": 1}
-REDUCED = {"full": 0, "truncated": 1}
+REDUCED = {"full": 0, "truncated": 1, "otf": 2}
 OUTER = {"ir": 0, "bicgstab": 1, "none": 2}
 
 
@@ -42,13 +42,14 @@ class Options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double),
                 ("max_nrhs", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("oversample", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("graph_safe", ctypes.c_int32), ("block", ctypes.c_int32)]
+                ("graph_safe", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("otf_tol", ctypes.c_double), ("otf_max_iter", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("max_rel_residual", ctypes.c_double),
-                ("rel_residual", ctypes.POINTER(ctypes.c_double))]
+                ("rel_residual", ctypes.POINTER(ctypes.c_double)), ("reduced_iterations", ctypes.c_int32)]
 
 
 _lib = None
@@ -153,7 +154,7 @@ class LRSpike:
                  pivoting: bool = False, tol: Optional[float] = None, max_iter: int = 50,
                  rank_tol: Optional[float] = None, max_nrhs: int = 16, profile: bool = False,
                  stream=None, graph_safe: bool = False, block: int = 0, oversample: Optional[int] = None,
-                 power_iters: int = 2):
+                 power_iters: int = 2, otf_tol: float = 1e-8, otf_max_iter: int = 100):
         import torch
         self._lib = load_library()
         o = Options()
@@ -173,6 +174,8 @@ class LRSpike:
         if oversample is not None:
             o.oversample = oversample
         o.power_iters = power_iters
+        o.otf_tol = otf_tol
+        o.otf_max_iter = otf_max_iter
         self.opt = o
         self.n, self.k, self.p, self.r = n, k, p, r
         if stream is None and torch.cuda.is_available():
@@ -233,7 +236,8 @@ class LRSpike:
         if st != 0 and not (allow_unconverged and st == 6):
             self._check(st, self._h)
         out = {"iterations": info.iterations, "converged": bool(info.converged),
-               "max_rel_residual": info.max_rel_residual, "rel_residual": list(rel)}
+               "max_rel_residual": info.max_rel_residual, "rel_residual": list(rel),
+               "reduced_iterations": info.reduced_iterations}
         return (X[0] if squeeze else X), out
 
     def solve(self, f, x=None, allow_unconverged=False):

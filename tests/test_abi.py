@@ -44,6 +44,7 @@ def test_defaults(lib):
     assert o.tol == 1e-12 and o.max_iter == 50 and o.max_nrhs == 16
     assert lib.lrspike_options_default(None, 1, 1, 1, 1) == 1
     assert (o.oversample, o.power_iters, o.seed) == (2, 2, 0x4C52535049)
+    assert (o.otf_tol, o.otf_max_iter) == (1e-8, 100)
 
 
 @pytest.mark.parametrize("changes", [
@@ -51,6 +52,10 @@ def test_defaults(lib):
     dict(n=20000, k=100, r=8, compress=1),                 # wide bands: SPIKE compression only
     dict(n=20000, k=100, r=8, oversample=60),              # more than 64 sketch columns
     dict(n=20000, k=100, r=33),                            # r > 32
+    dict(reduced=2, pivoting=1),                           # OTF: no pivoting
+    dict(reduced=2, outer=1),                              # OTF: outer IR or NONE
+    dict(reduced=2, graph_safe=1),                         # OTF: not graph_safe
+    dict(n=20000, k=100, r=8, reduced=2),                  # OTF: k <= 64
 ])
 def test_create_reports_unbuilt_combinations(lib, changes):
     o = _opts(lib, n=changes.pop("n", 1000), k=changes.pop("k", 8), p=4, r=changes.pop("r", 2))
@@ -63,7 +68,8 @@ def test_create_reports_unbuilt_combinations(lib, changes):
 
 @pytest.mark.parametrize("field,value", [("k", 1025), ("k", -1), ("r", 9), ("r", -1), ("p", 0),
                                          ("n", 0), ("max_nrhs", 0), ("max_nrhs", 17),
-                                         ("precision", 7), ("outer", 5), ("compress", 2)])
+                                         ("precision", 7), ("outer", 5), ("compress", 2), ("reduced", 3),
+                                         ("otf_tol", 0.0), ("otf_max_iter", 0)])
 def test_create_rejects_bad_options(lib, field, value):
     o = _opts(lib)
     setattr(o, field, value)
@@ -72,6 +78,15 @@ def test_create_rejects_bad_options(lib, field, value):
     assert st == 1, (field, value, st)
     assert not h.value
     assert len(lib.lrspike_last_error(None)) > 0
+
+
+def test_otf_needs_partitions_and_rank(lib):
+    for p, r in ((1, 2), (4, 0)):
+        o = _opts(lib, p=p, r=r)
+        o.reduced = 2
+        h = ctypes.c_void_p()
+        assert lib.lrspike_create(ctypes.byref(o), None, ctypes.byref(h)) == 1
+        assert b"OTF" in lib.lrspike_last_error(None)
 
 
 def test_create_rejects_partitions_not_wider_than_k(lib):
