@@ -119,6 +119,46 @@ __global__ void __launch_bounds__(RBS)
     reduce_columns<NR>(ss, nrhs, partial, counter, nrm_out, inv_out);
 }
 
+// Row stride of the staged factor tiles of the D-stage.  FP32 KB = 64 uses 80
+// (= 16 mod 32 words): the two rows a quarter-warp reads then fall on
+// disjoint bank halves, and with the rotated chunk order of ds_row64 the four
+// lanes of a row on disjoint quarters, so the 16-byte tile loads are free of
+// bank conflicts.  Otherwise one 16-byte pad per row.
+template <typename T, int KB>
+__host__ __device__ constexpr int ds_ldp() {
+    return (sizeof(T) == 4 && KB == 64) ? 80 : KB + 16 / (int)sizeof(T);
+}
+
+// FP32, KB = 64, one right-hand side: lane q of row a owns the quarter row
+// [16q, 16q+16), visited in four 4-entry chunks in the rotated order
+// (u + q) mod 4 (chunk offsets co[u]).  mv holds the quarter of the tile row
+// (loaded once per block step, used by both triangular products); masks m
+// select the product's entries (INV: the complement).
+template <bool INV>
+__device__ __forceinline__ float ds_dot64(const float (&mv)[16], const float *v, const int (&co)[4],
+                                         const unsigned (&m)[16]) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float4 f = *reinterpret_cast<const float4 *>(v + co[u]);
+        const float vv[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const unsigned mk = INV ? ~m[4 * u + w] : m[4 * u + w];
+            acc[w] = fmaf(__uint_as_float(__float_as_uint(mv[4 * u + w]) & mk), vv[w], acc[w]);
+        }
+    }
+    return quad_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+}
+
+__device__ __forceinline__ void ds_row64(const float *row, const int (&co)[4], float (&mv)[16]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float4 f = *reinterpret_cast<const float4 *>(row + co[u]);
+        mv[4 * u] = f.x; mv[4 * u + 1] = f.y; mv[4 * u + 2] = f.z; mv[4 * u + 3] = f.w;
+    }
+}
+
 // ---------------------------------------------------------------------------
 template <typename T, int KB, Split S, int NBUF>
 __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
@@ -126,7 +166,7 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
                             const double *__restrict__ rin, const double *__restrict__ inv,
                             int nrhs, T *__restrict__ Yv, T *__restrict__ Gv, double *__restrict__ psi,
                             unsigned char *smem_raw) {
-    constexpr int NT = Geo<KB>::NT, LDP = KB + 16 / (int)sizeof(T);
+    constexpr int NT = Geo<KB>::NT, LDP = ds_ldp<T, KB>();
     constexpr int PDS = NBUF - 1;  // steps staged ahead (the factor tile of a step is 16 KB from HBM)
     const int pm = KB * nrhs;
     double *ib = reinterpret_cast<double *>(smem_raw);  // [NBUF][KB x nrhs] staged input rows
@@ -149,7 +189,7 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
         const int buf = t % NBUF;
         double *in = ib + buf * pm;
         if (t < nb) {
-            stage_tile<T, KB>(LT + (b0 + t) * KB * KB, tb + buf * KB * LDP, nullptr, nullptr);
+            stage_tile<T, KB, LDP>(LT + (b0 + t) * KB * KB, tb + buf * KB * LDP, nullptr, nullptr);
             for (int e = threadIdx.x; e < pm; e += NT) {
                 const int c = e / KB, a = e % KB;
                 const int64_t row = (int64_t)t * KB + a;
@@ -158,7 +198,7 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
         } else {
             const int J = steps - 1 - t;
             const int64_t g = b0 + J;
-            stage_tile<T, KB>(UT + g * KB * KB, tb + buf * KB * LDP, DI + g * KB, db + buf * KB);
+            stage_tile<T, KB, LDP>(UT + g * KB * KB, tb + buf * KB * LDP, DI + g * KB, db + buf * KB);
             if (J < nb - 2) {
                 T *inT = reinterpret_cast<T *>(in);
                 for (int e = threadIdx.x; e < pm; e += NT) {
@@ -173,59 +213,140 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
         if (t < steps) stage(t);
         cp_async_commit();
     }
-    if (nrhs == 1 && sizeof(T) == 4) {
-        // One right-hand side in FP32 (FP64 keeps the bounded triangular
-        // loops below, its multiply-adds being scarce): two barriers per block step.  The loop-top
-        // barrier publishes the staged step and closes the previous one; the
-        // input scaling is fused into the first product, the output stores
-        // into the second.
-        const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
-        const double inv0 = inv[0];
-        for (int t = 0; t < steps; ++t) {
-            cp_async_wait<PDS - 1>();
-            __syncthreads();
-            // buffer (t + PDS) % NBUF last served step t-1, closed by the barrier above
-            if (t + PDS < steps) stage(t + PDS);
-            cp_async_commit();
-            const T *tile = tb + (t % NBUF) * KB * LDP + a * LDP;
-            const double *in = ib + (t % NBUF) * pm;
-            if (t < nb) {
-                const int J = t;
-                const int64_t row = (int64_t)J * KB + a;
-                // t = b_J - L_{J,J-1} y_{J-1}   (upper triangle incl. diagonal)
-                const T p1 = (J > 0) ? tri_dot1<T, KB, 0>(tile, Yp, a, q) : T(0);
-                if (q == 0) {
-                    const T b = (row >= ni) ? T(0) : (T)(in[a] * inv0);
-                    Tt[a] = b - p1;
-                }
+    bool fused = false;
+    if constexpr (sizeof(T) == 4 && KB == 64) {
+        if (nrhs == 1) {
+            // One right-hand side, KB = 64: two barriers per block step; the
+            // tile row chunks are read from shared memory once and serve both
+            // triangular products (forward j >= a and j < a, backward j <= a
+            // and j > a).
+            fused = true;
+            const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
+            int co[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) co[u] = 16 * q + 4 * ((u + q) & 3);
+            unsigned m[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) m[e] = (co[e / 4] + (e % 4) >= a) ? ~0u : 0u;
+            const double inv0 = inv[0];
+            float mv[16];
+            for (int t = 0; t < nb; ++t) {
+                cp_async_wait<PDS - 1>();
+                __syncthreads();
+                // buffer (t + PDS) % NBUF last served step t-1, closed by the barrier above
+                if (t + PDS < steps) stage(t + PDS);
+                cp_async_commit();
+                ds_row64(tb + (t % NBUF) * KB * LDP + a * LDP, co, mv);
+                const int64_t row = (int64_t)t * KB + a;
+                // the scaled input (an FP64 product, on the slow FP64 pipe) only where it is stored
+                const float b = (q != 0 || row >= ni) ? 0.f : (float)(ib[(t % NBUF) * pm + a] * inv0);
+                // t = b_J - L_{J,J-1} y_{J-1}  (t and y are kept by lane q = 0)
+                const float tv = b - ((t > 0) ? ds_dot64<false>(mv, Yp, co, m) : 0.f);
+                if (q == 0) Tt[a] = tv;
                 __syncthreads();
                 // y_J = t + (L^{-1} strictly lower) t
-                const T y = Tt[a] + tri_dot1<T, KB, 1>(tile, Tt, a, q);
+                const float y = tv + ds_dot64<true>(mv, Tt, co, m);
                 if (q == 0) {
                     Yp[a] = y;
                     if (row < ni) Yv[s + row] = y;
-                    if (J == nb - 2) Yk[a] = y;
+                    if (t == nb - 2) Yk[a] = y;
                 }
-            } else {
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) m[e] = (co[e / 4] + (e % 4) <= a) ? ~0u : 0u;
+            for (int t = nb; t < steps; ++t) {
+                cp_async_wait<PDS - 1>();
+                __syncthreads();
+                if (t + PDS < steps) stage(t + PDS);
+                cp_async_commit();
+                ds_row64(tb + (t % NBUF) * KB * LDP + a * LDP, co, mv);
                 const int J = steps - 1 - t;
                 const int64_t row = (int64_t)J * KB + a;
-                const T *inT = reinterpret_cast<const T *>(in);
-                const T yin = (row >= ni) ? T(0) : (J == nb - 1) ? Yp[a] : (J == nb - 2) ? Yk[a] : inT[a];
-                const T dsm = db[(t % NBUF) * KB + a];
-                // t = D^{-1} y_J - (D^{-1}U_{J,J+1}) x_{J+1}   (lower triangle incl. diagonal)
-                const T p1 = (J < nb - 1) ? tri_dot1<T, KB, 2>(tile, Yp, a, q) : T(0);
-                if (q == 0) Tt[a] = yin * dsm - p1;
+                const float *inT = reinterpret_cast<const float *>(ib + (t % NBUF) * pm);
+                const float yin = (row >= ni) ? 0.f : (J == nb - 1) ? Yp[a] : (J == nb - 2) ? Yk[a] : inT[a];
+                const float dsm = db[(t % NBUF) * KB + a];
+                // t = D^{-1} y_J - (D^{-1}U_{J,J+1}) x_{J+1}
+                const float tv = yin * dsm - ((J < nb - 1) ? ds_dot64<false>(mv, Yp, co, m) : 0.f);
+                if (q == 0) Tt[a] = tv;
                 __syncthreads();
                 // x_J = t + ((D^{-1}U_JJ)^{-1} strictly upper) t
-                const T x = Tt[a] + tri_dot1<T, KB, 3>(tile, Tt, a, q);
+                const float x = tv + ds_dot64<true>(mv, Tt, co, m);
                 if (q == 0) {
                     Yp[a] = x;
                     if (row < ni) Gv[s + row] = x;
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
-    } else
+    } else if constexpr (sizeof(T) == 4) {
+        if (nrhs == 1) {
+            // One right-hand side in FP32 (FP64 keeps the bounded triangular
+            // loops below, its multiply-adds being scarce): two barriers per block step.  The loop-top
+            // barrier publishes the staged step and closes the previous one; the
+            // input scaling is fused into the first product, the output stores
+            // into the second.  Lane q of row a keeps bit masks of its quarter row:
+            // forward j >= a (L_{J,J-1}, upper with diagonal) and its complement
+            // j < a (L_JJ^{-1}); backward j <= a (D^{-1}U_{J,J+1}) and j > a.
+            fused = true;
+            constexpr int QW = KB / 4;
+            const int a = threadIdx.x >> 2, q = threadIdx.x & 3;
+            const double inv0 = inv[0];
+            unsigned msk[QW];
+#pragma unroll
+            for (int w = 0; w < QW; ++w) msk[w] = (q * QW + w >= a) ? ~0u : 0u;
+            for (int t = 0; t < nb; ++t) {
+                cp_async_wait<PDS - 1>();
+                __syncthreads();
+                // buffer (t + PDS) % NBUF last served step t-1, closed by the barrier above
+                if (t + PDS < steps) stage(t + PDS);
+                cp_async_commit();
+                const float *tile = tb + (t % NBUF) * KB * LDP + a * LDP;
+                const double *in = ib + (t % NBUF) * pm;
+                const int64_t row = (int64_t)t * KB + a;
+                // t = b_J - L_{J,J-1} y_{J-1}
+                const float p1 = (t > 0) ? tri_dot1m<KB, false>(tile, Yp, q, msk) : 0.f;
+                if (q == 0) {
+                    const float b = (row >= ni) ? 0.f : (float)(in[a] * inv0);
+                    Tt[a] = b - p1;
+                }
+                __syncthreads();
+                // y_J = t + (L^{-1} strictly lower) t
+                const float y = Tt[a] + tri_dot1m<KB, true>(tile, Tt, q, msk);
+                if (q == 0) {
+                    Yp[a] = y;
+                    if (row < ni) Yv[s + row] = y;
+                    if (t == nb - 2) Yk[a] = y;
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < QW; ++w) msk[w] = (q * QW + w <= a) ? ~0u : 0u;
+            for (int t = nb; t < steps; ++t) {
+                cp_async_wait<PDS - 1>();
+                __syncthreads();
+                if (t + PDS < steps) stage(t + PDS);
+                cp_async_commit();
+                const float *tile = tb + (t % NBUF) * KB * LDP + a * LDP;
+                const double *in = ib + (t % NBUF) * pm;
+                const int J = steps - 1 - t;
+                const int64_t row = (int64_t)J * KB + a;
+                const float *inT = reinterpret_cast<const float *>(in);
+                const float yin = (row >= ni) ? 0.f : (J == nb - 1) ? Yp[a] : (J == nb - 2) ? Yk[a] : inT[a];
+                const float dsm = db[(t % NBUF) * KB + a];
+                // t = D^{-1} y_J - (D^{-1}U_{J,J+1}) x_{J+1}
+                const float p1 = (J < nb - 1) ? tri_dot1m<KB, false>(tile, Yp, q, msk) : 0.f;
+                if (q == 0) Tt[a] = yin * dsm - p1;
+                __syncthreads();
+                // x_J = t + ((D^{-1}U_JJ)^{-1} strictly upper) t
+                const float x = Tt[a] + tri_dot1m<KB, true>(tile, Tt, q, msk);
+                if (q == 0) {
+                    Yp[a] = x;
+                    if (row < ni) Gv[s + row] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (!fused)
     for (int t = 0; t < steps; ++t) {
         // buffer (t + PDS) % NBUF last served step t-1, closed by the barrier ending it
         if (t + PDS < steps) stage(t + PDS);
@@ -287,7 +408,7 @@ __device__ void dstage_body(const T *__restrict__ LT, const T *__restrict__ UT, 
 }
 
 template <typename T, int KB, int NBUF>
-__global__ void __launch_bounds__(Geo<KB>::NT)
+__global__ void __launch_bounds__(Geo<KB>::NT, 2)
     k_dstage(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
              const T *__restrict__ PQ, Parts P, int k, int r, int64_t n, const double *__restrict__ rin,
              const double *__restrict__ inv, int nrhs, T *__restrict__ Yv, T *__restrict__ Gv,
@@ -573,7 +694,7 @@ bool run_norms(Ctx *c, const double *v, int64_t ld, int nrhs, double *out) {
 template <typename T, int KB, int NBUF>
 static size_t dstage_smem(int nrhs) {
     return (size_t)NBUF * KB * nrhs * sizeof(double) +
-           ((size_t)NBUF * KB * (KB + 16 / sizeof(T)) + NBUF * KB + 3 * KB * nrhs) * sizeof(T);
+           ((size_t)NBUF * KB * ds_ldp<T, KB>() + NBUF * KB + 3 * KB * nrhs) * sizeof(T);
 }
 
 template <typename T, int KB, int NBUF>

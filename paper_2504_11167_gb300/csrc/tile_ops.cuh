@@ -204,6 +204,29 @@ __device__ __forceinline__ T tri_dot1(const T *__restrict__ Mrow, const T *v, in
     return quad_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
 }
 
+// FP32 form of tri_dot1 with the triangle given as per-lane bit masks:
+// msk[w] is all ones where entry q KB/4 + w of the row belongs to the product
+// (INV: where it does not), so each entry costs one AND and one fused
+// multiply-add (masked-out entries contribute fma(+0, v, acc) = acc).
+template <int KB, bool INV>
+__device__ __forceinline__ float tri_dot1m(const float *__restrict__ Mrow, const float *v, int q,
+                                          const unsigned (&msk)[KB / 4]) {
+    constexpr int QW = KB / 4, VW = QW < 4 ? QW : 4;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < QW; u += VW) {
+        float mv[VW], vv[VW];
+        ld_row<float, VW>(Mrow + q * QW + u, mv);
+        ld_row<float, VW>(v + q * QW + u, vv);
+#pragma unroll
+        for (int w = 0; w < VW; ++w) {
+            const unsigned m = INV ? ~msk[u + w] : msk[u + w];
+            acc[w] = fmaf(__uint_as_float(__float_as_uint(mv[w]) & m), vv[w], acc[w]);
+        }
+    }
+    return quad_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+}
+
 // acc[i][j] (+/-)= sum_{q0 <= q < q1} A[(a0+i)*LDA + q] * B[q*LDB + c0 + j]
 template <typename T, int MT, bool SUB>
 __device__ __forceinline__ void panel_mac(T (&acc)[4][MT], const T *__restrict__ A, int LDA,
@@ -242,15 +265,26 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Stages a KB x KB tile into shared memory rows of stride LDP = KB + 16/sizeof(T)
-// (one 16-byte pad per row), plus optionally KB diagonal values.
-template <typename T, int KB>
+// Stages a KB x KB tile into shared memory rows of stride LDP (by default
+// KB + 16/sizeof(T): one 16-byte pad per row), plus optionally KB diagonal values.
+template <typename T, int KB, int LDP = KB + 16 / (int)sizeof(T)>
 __device__ __forceinline__ void stage_tile(const T *__restrict__ src, T *dst, const T *__restrict__ dsrc,
                                            T *ddst) {
-    constexpr int CH = 16 / sizeof(T), CPR = KB / CH, LDP = KB + CH;
-    for (int e = threadIdx.x; e < KB * CPR; e += Geo<KB>::NT) {
-        const int row = e / CPR, ch = e % CPR;
-        cp_async16(dst + row * LDP + ch * CH, src + row * KB + ch * CH);
+    constexpr int CH = 16 / sizeof(T), CPR = KB / CH, NT = Geo<KB>::NT;
+    static_assert(LDP % CH == 0, "staged rows must stay 16-byte aligned");
+    if constexpr ((KB * CPR) % NT == 0 && NT % CPR == 0) {
+        // every thread copies the same chunk column of KB CPR / NT rows
+        const int row0 = threadIdx.x / CPR, ch = threadIdx.x % CPR;
+#pragma unroll
+        for (int i = 0; i < KB * CPR / NT; ++i) {
+            const int row = row0 + i * (NT / CPR);
+            cp_async16(dst + row * LDP + ch * CH, src + row * KB + ch * CH);
+        }
+    } else {
+        for (int e = threadIdx.x; e < KB * CPR; e += NT) {
+            const int row = e / CPR, ch = e % CPR;
+            cp_async16(dst + row * LDP + ch * CH, src + row * KB + ch * CH);
+        }
     }
     if (dsrc)
         for (int e = threadIdx.x; e < CPR; e += Geo<KB>::NT) cp_async16(ddst + e * CH, dsrc + e * CH);
