@@ -113,6 +113,9 @@ static void free_all(Ctx *c) {
         cudaEventDestroy(pd.b);
     }
     for (auto e : c->free_events) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
 }
 
 extern "C" lrspike_status lrspike_options_default(lrspike_options *o, int64_t n, int32_t k, int32_t p,
@@ -257,6 +260,10 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     if (ok && c->otf) ok = otf_alloc(c);
     if (ok && wide) ok = wide_setup(c);
     if (ok) ok = cudaMallocHost((void **)&c->host, (8 * mx + 8) * 8) == cudaSuccess;
+    if (ok && spikes && !wide && o.compress == LRSPIKE_COMPRESS_COUPLING)
+        ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -319,13 +326,33 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
             return cuda_fail(c, "status reset");
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "stream sync");
     }
-    bool ok = c->wide ? run_wide_factor(c) : run_band_lu(c);
-    if (ok && !c->wide && c->p > 1 && c->r > 0) {
-        if (c->opt.compress == LRSPIKE_COMPRESS_COUPLING)
-            ok = run_coupling_gram(c) && run_jacobi(c) && run_spike_rhs(c) && run_sweep(c) && run_make_u(c);
-        else
-            ok = run_spike_rhs(c) && run_sweep(c) && run_gram(c) && run_jacobi(c) && run_make_u(c);
-        ok = ok && run_reduced_build(c) && run_reduced_factor(c);
+    bool ok;
+    if (c->side) {
+        // Coupling compression: the Gram matrices of B_i and C_i, their
+        // eigenvectors and the spike right-hand sides need the band only, so
+        // they run on the side stream while the band LU (one CTA per
+        // partition, SMs not full) runs on the handle's stream; the spike
+        // sweep waits for both.  The LU is enqueued first.
+        ok = cudaEventRecord(c->ev_fork, c->stream) == cudaSuccess && run_band_lu(c) &&
+             cudaStreamWaitEvent(c->side, c->ev_fork, 0) == cudaSuccess;
+        if (ok) {
+            cudaStream_t own = c->stream;
+            c->stream = c->side;
+            ok = run_coupling_gram(c) && run_jacobi(c) && run_spike_rhs(c);
+            c->stream = own;
+            ok = ok && cudaEventRecord(c->ev_join, c->side) == cudaSuccess &&
+                 cudaStreamWaitEvent(c->stream, c->ev_join, 0) == cudaSuccess;
+        }
+        ok = ok && run_sweep(c) && run_make_u(c) && run_reduced_build(c) && run_reduced_factor(c);
+    } else {
+        ok = c->wide ? run_wide_factor(c) : run_band_lu(c);
+        if (ok && !c->wide && c->p > 1 && c->r > 0) {
+            if (c->opt.compress == LRSPIKE_COMPRESS_COUPLING)
+                ok = run_coupling_gram(c) && run_jacobi(c) && run_spike_rhs(c) && run_sweep(c) && run_make_u(c);
+            else
+                ok = run_spike_rhs(c) && run_sweep(c) && run_gram(c) && run_jacobi(c) && run_make_u(c);
+            ok = ok && run_reduced_build(c) && run_reduced_factor(c);
+        }
     }
     if (!ok) return fail(c, LRSPIKE_ERR_CUDA, c->err);
     if (gs) {  // the status is read by lrspike_finish

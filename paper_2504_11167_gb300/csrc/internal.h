@@ -52,6 +52,11 @@ struct Pending {
 struct Ctx {
     lrspike_options opt{};
     cudaStream_t stream = nullptr;
+    // coupling compression: second stream (non-blocking) on which the
+    // coupling-block Gram matrices, their eigenvectors and the spike
+    // right-hand sides run beside the band LU; fork / join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     int KB = 8;          // block size (>= k, power of two in 8..64)
     bool fp64 = true;    // working precision is double
