@@ -101,7 +101,7 @@ static void free_all(Ctx *c) {
                     c->PQ,    c->Gram,   c->Gpart, c->sigma, c->E, c->F,    c->Gs,    c->Rinv,
                     c->Gam,   c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
                     c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots,
-                    c->bpartial, c->PF, c->PIVP, c->ocv, c->og, c->orv, c->osc, c->oone};
+                    c->bpartial, c->PF, c->PIVP, c->ocv, c->og, c->orv, c->osc, c->oone, c->xalt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (double *p : c->bv)
@@ -258,6 +258,11 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     }
     if (ok && o.outer == LRSPIKE_OUTER_BICGSTAB) ok = bicgstab_alloc(c);
     if (ok && c->otf) ok = otf_alloc(c);
+    // fused retrieval + residual in the IR loop: rows of one CTA (256) and its
+    // 2k halo rows may span at most two partitions
+    if (ok && !wide && !piv && !c->otf && !o.graph_safe && o.outer == LRSPIKE_OUTER_IR &&
+        c->n / c->p >= 256 + 2 * (int64_t)c->k)
+        ok = dalloc(&c->xalt, (size_t)c->n * 8);
     if (ok && wide) ok = wide_setup(c);
     if (ok) ok = cudaMallocHost((void **)&c->host, (8 * mx + 8) * 8) == cudaSuccess;
     if (ok && spikes && !wide && o.compress == LRSPIKE_COMPRESS_COUPLING)
@@ -461,8 +466,20 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
         converged = !nan && worst <= c->opt.tol;
         stalled = br.breakdown;
     }
+    // With fused_retrieve_ok an application's retrieval waits for the next
+    // residual (one kernel); the iterate alternates between xd and xalt.
+    const bool fuse = outer == LRSPIKE_OUTER_IR && fused_retrieve_ok(c, nrhs, trans);
+    double *xcur = xd;
+    bool pending = false;
     for (; outer != LRSPIKE_OUTER_BICGSTAB; ++it) {
-        if (!run_residual(c, fd, xd, ldd, nrhs, trans, it == 0)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        if (pending) {
+            double *xnext = (xcur == xd) ? c->xalt : xd;
+            if (!run_residual_retrieve(c, fd, xcur, xnext)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+            xcur = xnext;
+            pending = false;
+        } else if (!run_residual(c, fd, xd, ldd, nrhs, trans, it == 0)) {
+            return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        }
         if (outer == LRSPIKE_OUTER_NONE) {
             if (!apply_precond(c, c->rv, xd, ldd, nrhs, trans, true)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
             it = 1;
@@ -483,8 +500,15 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
         if (worst <= c->opt.tol) { converged = true; break; }
         if (it >= max_it) break;
         if (it >= 3 && worst > 0.9 * hist[it - 3]) { stalled = true; break; }
-        if (!apply_precond(c, c->rv, xd, ldd, nrhs, trans, true)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        if (fuse) {
+            if (!apply_precond_deferred(c, c->rv, nrhs)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+            pending = true;
+        } else if (!apply_precond(c, c->rv, xd, ldd, nrhs, trans, true)) {
+            return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        }
     }
+    if (xcur != xd && cudaMemcpyAsync(xd, xcur, (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return cuda_fail(c, "iterate copy");
     if (!fdev) {
         if (cudaMemcpy2DAsync(x, ld * 8, xd, ldd * 8, c->n * 8, nrhs, cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess)

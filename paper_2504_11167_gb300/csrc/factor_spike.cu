@@ -535,15 +535,17 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
             __syncthreads();
             // warp w applies the rotations of pairs w*PPW.. in turn, its lanes over
             // consecutive entries (conflict-free); a pair's indices and
-            // coefficients are read once per pass
+            // coefficients are read once per pass, and a pair left as it is
+            // (c = 1, s = 0: already diagonal) is skipped by the whole warp
             constexpr int NWJ = NT / 32, PPW = (NP + NWJ - 1) / NWJ;  // warps, pairs per warp
             const int wj = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
             for (int ii = 0; ii < PPW; ++ii) {  // rows p, q
                 const int i = wj * PPW + ii;
                 if (i >= NP) break;
-                const int p = pp[i], q = qq[i];
                 const T c = cs[i], s = sn[i];
+                if (s == T(0)) continue;
+                const int p = pp[i], q = qq[i];
                 for (int j = lane; j < KB; j += 32) {
                     const T ap = A[p * LD + j], aq = A[q * LD + j];
                     A[p * LD + j] = c * ap - s * aq;
@@ -555,8 +557,9 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
             for (int ii = 0; ii < PPW; ++ii) {  // columns p, q and V
                 const int i = wj * PPW + ii;
                 if (i >= NP) break;
-                const int p = pp[i], q = qq[i];
                 const T c = cs[i], s = sn[i];
+                if (s == T(0)) continue;
+                const int p = pp[i], q = qq[i];
                 for (int j = lane; j < KB; j += 32) {
                     const T ap = A[j * LD + p], aq = A[j * LD + q];
                     A[j * LD + p] = c * ap - s * aq;

@@ -56,6 +56,9 @@ struct Ctx {
     // coupling-block Gram matrices, their eigenvectors and the spike
     // right-hand sides run beside the band LU; fork / join events
     cudaStream_t side = nullptr;
+    // second iterate buffer (n doubles) for the fused retrieval + residual of
+    // the IR loop; allocated when every partition holds >= 256 + 2k rows
+    double *xalt = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     int KB = 8;          // block size (>= k, power of two in 8..64)
@@ -211,6 +214,14 @@ void set_handleless_error(const std::string &msg);
 // dimension n) whose column norms |in| and 1/|in| are at nrm + max_nrhs and
 // nrm + 2 max_nrhs: out (+)= |in| * M^{-1}(in/|in|).  Used by the outer loops.
 bool apply_precond(Ctx *c, const double *in, double *out, int64_t ldo, int nrhs, bool trans, bool accumulate);
+// The outer IR loop may defer the retrieval of an application into the next
+// residual: apply_precond_deferred leaves g (Gv) and z (zr) for
+// run_residual_retrieve, which forms x_out = x_in + |r| (g - U z) and
+// r = f - A x_out in one kernel (x_out != x_in).  Only where
+// fused_retrieve_ok holds.
+bool fused_retrieve_ok(const Ctx *c, int nrhs, bool trans);
+bool apply_precond_deferred(Ctx *c, const double *in, int nrhs);
+bool run_residual_retrieve(Ctx *c, const double *f, const double *x_in, double *x_out);
 // LR-SPIKE-OTF (otf.cu): out (+)= |in| * (OTF solve of in/|in|)
 constexpr int kOtfVecs = 10;
 bool otf_alloc(Ctx *c);

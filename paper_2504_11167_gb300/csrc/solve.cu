@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(RBS)
                 const double a = trans ? band[(int64_t)t * ldb + i] : band[(int64_t)(2 * k - t) * ldb + j];
 #pragma unroll
                 for (int c = 0; c < NR; ++c)
-                    if (c < nrhs) acc[c] -= a * x[c * ld + j];
+                    if (c < nrhs) acc[c] = fma(-a, x[c * ld + j], acc[c]);
             }
         }
 #pragma unroll
@@ -103,6 +103,100 @@ __global__ void __launch_bounds__(RBS)
             }
     }
     reduce_columns<NR>(ss, nrhs, partial, counter, nrm_out, inv_out);
+}
+
+// One row of the retrieval, shared by k_retrieve1 and k_residual_ret so the two
+// round identically: d = g - u . z (working precision, 16-byte loads of u
+// where the type allows), then x + nrm d with the product and the sum each
+// rounded once (no contraction).
+template <typename T, int NQ>
+__device__ __forceinline__ T retrieve_row(T g, const T *__restrict__ u, const T *z, int n2) {
+    T d = g;
+    if (sizeof(T) == 4 && n2 % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; q += 4)
+            if (q < n2) {
+                const float4 v = *reinterpret_cast<const float4 *>(u + q);
+                d -= v.x * z[q] + v.y * z[q + 1] + v.z * z[q + 2] + v.w * z[q + 3];
+            }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if (q < n2) d -= u[q] * z[q];
+    }
+    return d;
+}
+__device__ __forceinline__ double retrieve_update(double x, double nrm, double d, bool accumulate) {
+    const double upd = __dmul_rn(nrm, d);
+    return accumulate ? __dadd_rn(x, upd) : upd;
+}
+
+// The retrieval of one preconditioner application fused into the next
+// residual (one right-hand side, A not transposed, unpivoted k <= 64 factors):
+// x_out = x_in + nrm (g - U z) on the CTA's rows and k halo rows on each side
+// (the same arithmetic as k_retrieve1), the CTA's own rows written to x_out (a
+// different buffer from x_in: halo rows belong to other CTAs), then
+// r = f - A x_out on its rows from shared memory (the arithmetic of
+// k_residual), column norms as there.  Every partition holds at least
+// RBS + 2k rows, so the rows a CTA touches span at most two partitions.
+template <typename T, int NQ>
+__global__ void __launch_bounds__(RBS)
+    k_residual_ret(const double *__restrict__ band, int64_t ldb, int k, int64_t n,
+                   const double *__restrict__ f, const double *__restrict__ x_in, double *__restrict__ x_out,
+                   const T *__restrict__ Gv, const T *__restrict__ Ucat, const double *__restrict__ zr, Parts P,
+                   int r, const double *nrm_in, double *__restrict__ rres, double *partial,
+                   unsigned *counter, double *nrm_out, double *inv_out) {
+    extern __shared__ double xs[];  // rows i0-k .. i0+RBS+k-1
+    __shared__ T zs[2][NQ];
+    __shared__ int pa_s;
+    const int64_t i0 = blockIdx.x * (int64_t)RBS;
+    const int64_t lo = i0 - k > 0 ? i0 - k : 0, hi = i0 + RBS + k < n ? i0 + RBS + k : n;
+    const int n2 = 2 * r;
+    if (threadIdx.x == 0) {  // partition holding row lo
+        int a = 0, b = P.p - 1;
+        while (a < b) {
+            const int mid = (a + b + 1) / 2;
+            if (P.off[mid] <= lo) a = mid;
+            else b = mid - 1;
+        }
+        pa_s = a;
+    }
+    __syncthreads();
+    const int pa = pa_s;
+    for (int e = threadIdx.x; e < 2 * NQ; e += RBS) {
+        const int side = e / NQ, j = e % NQ, part = pa + side;
+        double v = 0.0;
+        if (part < P.p && j < n2) {
+            if (j < r) { if (part <= P.p - 2) v = zr[(int64_t)part * n2 + j]; }
+            else if (part >= 1) v = zr[(int64_t)(part - 1) * n2 + j];
+        }
+        zs[side][j] = (T)v;
+    }
+    __syncthreads();
+    // |r| of the preconditioned residual; nrm_in is also nrm_out, which only the
+    // last CTA writes, after every CTA has taken its ticket (and so read this)
+    const double sc = nrm_in[0];
+    const int64_t pb = (pa + 1 < P.p) ? P.off[pa + 1] : n;  // first row of partition pa+1
+    for (int64_t j = lo + threadIdx.x; j < hi; j += RBS) {
+        const T d = retrieve_row<T, NQ>(Gv[j], Ucat + j * n2, zs[j >= pb ? 1 : 0], n2);
+        const double xv = retrieve_update(x_in[j], sc, (double)d, true);
+        xs[j - (i0 - k)] = xv;
+        if (j >= i0 && j < i0 + RBS) x_out[j] = xv;
+    }
+    __syncthreads();
+    const int64_t i = i0 + threadIdx.x;
+    double ss[1] = {0.0};
+    if (i < n) {
+        double acc = f[i];
+        for (int t = 0; t < 2 * k + 1; ++t) {
+            const int64_t j = i - k + t;
+            if (j < 0 || j >= n) continue;
+            acc = fma(-band[(int64_t)(2 * k - t) * ldb + j], xs[j - (i0 - k)], acc);
+        }
+        rres[i] = acc;
+        ss[0] = acc * acc;
+    }
+    reduce_columns<1>(ss, 1, partial, counter, nrm_out, inv_out);
 }
 
 template <int NR>
@@ -478,25 +572,10 @@ __global__ void __launch_bounds__(RBS)
         z[j] = (T)v;
     }
     const double sc = nrm[0];
-    const bool vec = (sizeof(T) == 4) && (n2 % 4 == 0);
     for (int64_t row = blockIdx.x * (int64_t)RBS + threadIdx.x; row < ni; row += (int64_t)gridDim.x * RBS) {
         const int64_t gi = s + row;
-        T d = Gv[gi];
-        const T *u = Ucat + gi * n2;
-        if (vec) {
-#pragma unroll
-            for (int j = 0; j < NQ; j += 4)
-                if (j < n2) {
-                    const float4 v = *reinterpret_cast<const float4 *>(u + j);
-                    d -= v.x * z[j] + v.y * z[j + 1] + v.z * z[j + 2] + v.w * z[j + 3];
-                }
-        } else {
-#pragma unroll
-            for (int j = 0; j < NQ; ++j)
-                if (j < n2) d -= u[j] * z[j];
-        }
-        const double upd = sc * (double)d;
-        x[gi] = accumulate ? x[gi] + upd : upd;
+        const T d = retrieve_row<T, NQ>(Gv[gi], Ucat + gi * n2, z, n2);
+        x[gi] = retrieve_update(accumulate ? x[gi] : 0.0, sc, (double)d, accumulate);
     }
 }
 
@@ -822,6 +901,39 @@ bool run_retrieve(Ctx *c, double *x, int64_t ld, int nrhs, bool accumulate) {
 bool run_project_t(Ctx *c, const double *hin, int64_t, int nrhs) {
     if (c->p < 2 || c->r == 0) return true;
     return c->fp64 ? project_t_impl<double>(c, hin, nrhs) : project_t_impl<float>(c, hin, nrhs);
+}
+
+bool fused_retrieve_ok(const Ctx *c, int nrhs, bool trans) {
+    return c->xalt && nrhs == 1 && !trans && !c->otf && !c->wide && !c->opt.pivoting;
+}
+
+bool apply_precond_deferred(Ctx *c, const double *in, int nrhs) {
+    return run_dstage(c, in, c->n, nrhs) && run_reduced_solve(c, nrhs, false);
+}
+
+template <typename T, int NQ>
+static bool residual_ret_nq(Ctx *c, const double *f, const double *x_in, double *x_out) {
+    Parts P{c->off_d, c->boff_d, c->p};
+    const size_t smem = (size_t)(RBS + 2 * c->k) * sizeof(double);
+    return launch(c, KID_RESIDUAL, [&] {
+        k_residual_ret<T, NQ><<<row_blocks(c->n), RBS, smem, c->stream>>>(
+            c->band, c->ld, c->k, c->n, f, x_in, x_out, (const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r,
+            c->nrm + c->opt.max_nrhs, c->rv, c->partial, c->counter, c->nrm + c->opt.max_nrhs,
+            c->nrm + 2 * c->opt.max_nrhs);
+    });
+}
+
+template <typename T>
+static bool residual_ret_impl(Ctx *c, const double *f, const double *x_in, double *x_out) {
+    const int n2 = 2 * c->r;
+    if (n2 <= 8) return residual_ret_nq<T, 8>(c, f, x_in, x_out);
+    if (n2 <= 16) return residual_ret_nq<T, 16>(c, f, x_in, x_out);
+    if (n2 <= 32) return residual_ret_nq<T, 32>(c, f, x_in, x_out);
+    return residual_ret_nq<T, 64>(c, f, x_in, x_out);
+}
+
+bool run_residual_retrieve(Ctx *c, const double *f, const double *x_in, double *x_out) {
+    return c->fp64 ? residual_ret_impl<double>(c, f, x_in, x_out) : residual_ret_impl<float>(c, f, x_in, x_out);
 }
 
 bool apply_precond(Ctx *c, const double *in, double *out, int64_t ldo, int nrhs, bool trans, bool accumulate) {
