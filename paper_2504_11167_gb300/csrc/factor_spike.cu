@@ -383,6 +383,203 @@ __global__ void __launch_bounds__((KB / 4) * CG)
 }
 
 // ---------------------------------------------------------------------------
+// The pipelined sweep for FP32, KB = 64 and 32 MT panel columns with a balanced
+// thread map.  In k_sweep_pipe a thread owns one group of four rows, and the two
+// triangular products of a block step cost row group g about 15 - g and g
+// four-column chunks: the barrier between them makes every step pay the
+// longest of each.  Here thread (pair, column) owns the row groups pair and
+// 15 - pair (pair = 0..7) and MT columns, so both products cost every thread
+// about 15 chunks.  A warp covers two pairs and the 16 column groups of one
+// half of the panel (T_i or W_i columns: a whole warp skips an inactive half);
+// the two tile rows a quarter-warp reads are 4 apart (68 floats: 16 mod 32
+// words), so the 16-byte tile loads are conflict-free.  Staging, ring and
+// barriers as in k_sweep_pipe.
+template <int MT> struct SweepBal {
+    static constexpr int KB = 64, NT = 256, M = 32 * MT, NBUF = 3, PDS = 2;
+    static constexpr int LDT = KB + 4, LDM = M + 4;
+    static constexpr size_t bytes =
+        ((size_t)NBUF * (KB * LDT + KB * LDM + KB) + (size_t)2 * KB * LDM) * sizeof(float);
+};
+
+template <int MT>
+__global__ void __launch_bounds__(256)
+    k_sweep_bal(const float *__restrict__ LT, const float *__restrict__ UT, const float *__restrict__ DI, Parts P,
+                int k, float *__restrict__ X) {
+    using SB = SweepBal<MT>;
+    constexpr int KB = SB::KB, NT = SB::NT, M = SB::M, NBUF = SB::NBUF, PDS = SB::PDS;
+    constexpr int LDT = SB::LDT, LDM = SB::LDM, CH = 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tiles = reinterpret_cast<float *>(smem_raw);  // [NBUF][KB x LDT] raw factor tiles
+    float *pans = tiles + NBUF * KB * LDT;               // [NBUF][KB x LDM] panel blocks
+    float *dis = pans + NBUF * KB * LDM;                 // [NBUF][KB] D^{-1}
+    float *Tt = dis + NBUF * KB;                         // KB x LDM
+    float *Yp = Tt + KB * LDM;                           // KB x LDM
+    const int part = blockIdx.x;
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int64_t b0 = P.boff[part];
+    const int nb = (int)(P.boff[part + 1] - b0), steps = 2 * nb;
+    const bool hasV = part < P.p - 1, hasW = part > 0;
+    const int Jv0 = (int)((ni - k) / KB);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const bool isV = (w >> 2) == 0;
+    const int pair = (w & 3) * 2 + (l & 1);
+    const int c0 = MT * ((w >> 2) * 16 + (l >> 1));
+    const int ga[2] = {4 * pair, 4 * (15 - pair)};  // first rows of the two row groups
+
+    auto stage = [&](int t) {
+        const int buf = t % NBUF;
+        const bool fwd = t < nb;
+        const int J = fwd ? t : steps - 1 - t;
+        const int64_t g = b0 + J;
+        const float *tsrc = (fwd ? LT : UT) + g * KB * KB;
+        float *tdst = tiles + buf * KB * LDT;
+#pragma unroll
+        for (int i = 0; i < KB * (KB / CH) / NT; ++i) {
+            const int e = threadIdx.x + i * NT, row = e / (KB / CH), ch = e % (KB / CH);
+            cp_async16(tdst + row * LDT + ch * CH, tsrc + row * KB + ch * CH);
+        }
+        if (fwd || J < nb - 1) {
+            const float *psrc = X + g * KB * M;
+            float *pdst = pans + buf * KB * LDM;
+#pragma unroll
+            for (int i = 0; i < KB * (M / CH) / NT; ++i) {
+                const int e = threadIdx.x + i * NT, row = e / (M / CH), ch = e % (M / CH);
+                cp_async16(pdst + row * LDM + ch * CH, psrc + row * M + ch * CH);
+            }
+        }
+        if (!fwd && threadIdx.x < KB / CH) cp_async16(dis + buf * KB + threadIdx.x * CH, DI + g * KB + threadIdx.x * CH);
+    };
+    // acc (+/-)= tile rows a0..a0+3 x B over q in [a0, a0+4), masked per (row, column)
+    auto chunk = [&](float (&acc)[4][MT], const float *tile, const float *B, int a0, int mode, bool sub) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float bv[MT];
+            ld_row<float, MT>(B + (a0 + u) * LDM + c0, bv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                // column a0+u against row a0+i: 0: q >= a, 1: q < a, 2: q <= a, 3: q > a
+                const bool in = mode == 0 ? u >= i : mode == 1 ? u < i : mode == 2 ? u <= i : u > i;
+                if (!in) continue;
+                const float av = tile[(a0 + i) * LDT + a0 + u];
+#pragma unroll
+                for (int j = 0; j < MT; ++j) acc[i][j] = sub ? acc[i][j] - av * bv[j] : acc[i][j] + av * bv[j];
+            }
+        }
+    };
+    // acc (+/-)= tile rows a0..a0+3 x B over q in [q0, q1) (multiples of 4)
+    auto mac4 = [&](float (&acc)[4][MT], const float *tile, const float *B, int a0, int q0, int q1, bool sub) {
+        for (int q = q0; q < q1; q += 4) {
+            float av[4][4], bv[4][MT];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ld_row<float, 4>(tile + (a0 + i) * LDT + q, av[i]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ld_row<float, MT>(B + (q + u) * LDM + c0, bv[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < MT; ++j)
+                        acc[i][j] = sub ? acc[i][j] - av[i][u] * bv[u][j] : acc[i][j] + av[i][u] * bv[u][j];
+        }
+    };
+    for (int t = 0; t < PDS; ++t) {
+        if (t < steps) stage(t);
+        cp_async_commit();
+    }
+    float acc[4][MT];
+    for (int t = 0; t < steps; ++t) {
+        cp_async_wait<PDS - 1>();
+        __syncthreads();
+        // buffer (t + PDS) % NBUF last served step t-1, closed by the barrier above
+        if (t + PDS < steps) stage(t + PDS);
+        cp_async_commit();
+        const int buf = t % NBUF;
+        const float *tile = tiles + buf * KB * LDT, *pan = pans + buf * KB * LDM;
+        if (t < nb) {
+            const int J = t;
+            const bool active = isV ? (hasV && J >= Jv0) : hasW;
+            const bool first = (J == 0) || (isV && J == Jv0);
+            if (active) {
+                // t = b_J - L_{J,J-1} y_{J-1}   (L_{J,J-1} upper incl. diagonal: q >= a)
+#pragma unroll
+                for (int G = 0; G < 2; ++G) {
+                    const int a0 = ga[G];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) ld_row<float, MT>(pan + (a0 + i) * LDM + c0, acc[i]);
+                    if (!first) {
+                        chunk(acc, tile, Yp, a0, 0, true);
+                        mac4(acc, tile, Yp, a0, a0 + 4, KB, true);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) st_row<float, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+                }
+            }
+            __syncthreads();
+            if (active) {
+                // y_J = t + (L_JJ^{-1} strictly lower) t
+                float *xg = X + (b0 + J) * KB * M;
+#pragma unroll
+                for (int G = 0; G < 2; ++G) {
+                    const int a0 = ga[G];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) ld_row<float, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+                    mac4(acc, tile, Tt, a0, 0, a0, false);
+                    chunk(acc, tile, Tt, a0, 1, false);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        st_row<float, MT>(Yp + (a0 + i) * LDM + c0, acc[i]);
+                        st_row<float, MT>(xg + (a0 + i) * M + c0, acc[i]);
+                    }
+                }
+            }
+        } else {
+            const int J = steps - 1 - t;
+            const bool active = isV ? hasV : hasW;
+            const float *dsm = dis + buf * KB;
+            if (active) {
+                // t = D^{-1} y_J - (D^{-1}U_{J,J+1}) x_{J+1}   (lower incl. diagonal: q <= a)
+                const float *src = (J == nb - 1) ? Yp : pan;
+#pragma unroll
+                for (int G = 0; G < 2; ++G) {
+                    const int a0 = ga[G];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        ld_row<float, MT>(src + (a0 + i) * LDM + c0, acc[i]);
+#pragma unroll
+                        for (int j = 0; j < MT; ++j) acc[i][j] *= dsm[a0 + i];
+                    }
+                    if (J < nb - 1) {
+                        mac4(acc, tile, Yp, a0, 0, a0, true);
+                        chunk(acc, tile, Yp, a0, 2, true);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) st_row<float, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+                }
+            }
+            __syncthreads();
+            if (active) {
+                // x_J = t + ((D^{-1}U_JJ)^{-1} strictly upper) t
+                float *xg = X + (b0 + J) * KB * M;
+#pragma unroll
+                for (int G = 0; G < 2; ++G) {
+                    const int a0 = ga[G];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) ld_row<float, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
+                    chunk(acc, tile, Tt, a0, 3, false);
+                    mac4(acc, tile, Tt, a0, a0 + 4, KB, false);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        st_row<float, MT>(Yp + (a0 + i) * LDM + c0, acc[i]);
+                        st_row<float, MT>(xg + (a0 + i) * M + c0, acc[i]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Gram matrices of the two spike panels, partial sums over a chunk of blocks.
 // Thread tile: 4 rows x GC columns of one Gram matrix (GC = KB/8).
 template <typename T, int KB>
@@ -706,6 +903,16 @@ template <typename T, int KB, int MT, int CG>
 static bool sweep_mt(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
     constexpr int M = MT * CG, LDM = M + 16 / (int)sizeof(T), NT = (KB / 4) * CG;
+    if constexpr (sizeof(T) == 4 && KB == 64 && M == 32) {
+        using SB = SweepBal<1>;
+        static_assert(SB::bytes <= 110 * 1024, "two CTAs per SM");
+        auto kb = k_sweep_bal<1>;
+        cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB::bytes);
+        return launch(c, KID_SWEEP, [&] {
+            kb<<<c->p, SB::NT, SB::bytes, c->stream>>>((const float *)c->LT, (const float *)c->UT,
+                                                       (const float *)c->DI, P, c->k, (float *)c->X);
+        });
+    }
     if constexpr (sizeof(T) == 4) {
         using SP = SweepPipe<T, KB, MT, CG>;
         if (SP::bytes <= 110 * 1024) {
