@@ -437,11 +437,15 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
     const int mx = c->opt.max_nrhs;
     if (cudaMemset2DAsync(xd, ldd * 8, 0, c->n * 8, nrhs, c->stream) != cudaSuccess)
         return cuda_fail(c, "x reset");
-    if (!run_norms(c, fd, ldd, nrhs, c->nrm)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
-    double *hf = c->host, *hr = c->host + mx;
-    if (cudaMemcpyAsync(hf, c->nrm, nrhs * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-        return cuda_fail(c, "norm read");
     const int outer = c->opt.outer;
+    double *hf = c->host, *hr = c->host + mx;
+    // |f|: BiCGStab reads it before its first step; the IR loop takes it from
+    // its first residual (x = 0: r = f, the same reduction)
+    if (outer == LRSPIKE_OUTER_BICGSTAB) {
+        if (!run_norms(c, fd, ldd, nrhs, c->nrm)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        if (cudaMemcpyAsync(hf, c->nrm, nrhs * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            return cuda_fail(c, "norm read");
+    }
     const int max_it = (outer == LRSPIKE_OUTER_NONE) ? 1 : c->opt.max_iter;
     std::vector<double> hist;
     int it = 0;
@@ -488,6 +492,8 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
         if (cudaMemcpyAsync(hr, c->nrm + mx, nrhs * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
             cudaStreamSynchronize(c->stream) != cudaSuccess)
             return cuda_fail(c, "outer iteration");
+        if (it == 0)
+            for (int q = 0; q < nrhs; ++q) hf[q] = hr[q];
         double worst = 0.0;
         bool nan = false;
         for (int q = 0; q < nrhs; ++q) {

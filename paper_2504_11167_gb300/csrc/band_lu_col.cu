@@ -659,11 +659,19 @@ __global__ void __launch_bounds__(InvGeo<T, KB>::NT) k_band_lu_inv(T *__restrict
     const int tile = t % TILES, ta = tile / (H / 4), tb = tile % (H / 4);
     T *X11 = Mm, *M21 = Mm + H * LDM, *X22 = Mm + H * LDM + H;
     T acc[4][4];
-    if (act) tile4_mac<T>(M21, X11, LDM, tb * 4, ta * 4, ta * 4, H, acc);
-    __syncthreads();
-    if (act) {
+    {
+        // KB = 64 (8 x 8 tiles per product): the same 32 tiles per warp, lanes
+        // reassigned so that a quarter-warp takes four tile columns of two tile
+        // rows, whose M21 rows (4 apart) fall on disjoint bank halves (the map
+        // above puts eight rows on two bank groups); smaller blocks keep it
+        const int tp = (H == 32) ? ((tile & ~31) | ((tile & 3) << 3) | ((tile >> 2) & 7)) : tile;
+        const int pa = tp / (H / 4), pb = tp % (H / 4);
+        if (act) tile4_mac<T>(M21, X11, LDM, pb * 4, pa * 4, pa * 4, H, acc);
+        __syncthreads();
+        if (act) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) st_row<T, 4>(M21 + (tb * 4 + i) * LDM + ta * 4, acc[i]);
+            for (int i = 0; i < 4; ++i) st_row<T, 4>(M21 + (pb * 4 + i) * LDM + pa * 4, acc[i]);
+        }
     }
     __syncthreads();
     const int i0 = ta * 4, j0 = tb * 4;
