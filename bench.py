@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--profile-partitions", type=int, default=0,
+                    help="partitions of the --profile-case run (default p/4: the bench's n_i; "
+                         "256: the bench's CTA count at n_i = 4096)")
     return ap.parse_args()
 
 
@@ -169,9 +172,11 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------
 # DRAM bytes (read + write) per launch at this workload, from one ncu capture of
-# the quarter-size case (python bench.py --profile-case: n/4 rows, p/4
-# partitions, same n_i) scaled by 4 (both grow with n).  None = not captured.
-NCU_TRAFFIC = {"band_lu": 4 * (1.081185e9 + 0.512351e9), "band_lu_inv": 4 * (0.536948e9 + 0.251501e9)}
+# the quarter-size case (python bench.py --profile-case --profile-partitions 256:
+# n/4 rows, the bench's 256 CTAs) scaled by 4 (both grow with n).  "residual" is
+# a launch after the first of a solve (band product + the fused retrieval).
+# None = not captured for the current kernel.
+NCU_TRAFFIC = {"band_lu": 4 * (1.076124e9 + 0.507302e9), "residual": 4 * (1.238762e9 + 0.022746e9)}
 
 
 def kernel_work(name: str, prof: dict, precision_bytes: int):
@@ -314,16 +319,17 @@ def batch_variant(dev, systems_count=512, steps=3, iterations=10):
                        "graph": "one CUDA graph per batch (factor + solve of every system)"}}
 
 
-def profile_case():
-    """One factor + solve on a quarter-size case (n = 1,048,576, p = 64, same
-    k, r, dominance and n_i): small enough for ncu replays, inputs still larger
-    than L2."""
+def profile_case(parts: int = 0):
+    """One factor + solve on a quarter-size case (n = 1,048,576, same k, r and
+    dominance; p = 64 keeps the bench's n_i, p = 256 its CTA count per
+    partition-parallel kernel): small enough for ncu replays, inputs still
+    larger than L2."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2504_11167_gb300 import inputs
     from paper_2504_11167_gb300.solver import LRSpike
-    n, p = N // 4, P // 4
+    n, p = N // 4, (parts or P // 4)
     seed = inputs.SEED_BASE + 2
     band = torch.from_numpy(inputs.dominant_band(n, K, DOM, seed)).cuda()
     f = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, NRHS, seed).T)).cuda()
@@ -339,7 +345,7 @@ def profile_case():
 def main():
     args = parse()
     if args.profile_case:
-        return profile_case()
+        return profile_case(args.profile_partitions)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
