@@ -116,10 +116,14 @@ __global__ void __launch_bounds__(ColGeo<T, KB>::NT, sizeof(T) == 4 ? 2 : 1)
     const double *src[NU];
     int so[NU], rofs[NU], hi_ofs[NU];
     bool live[NU], inb[NU], idn[NU];
+    // The partial last round of slots (REM of them) goes to the last REM
+    // threads, so that the extra staging and conversion do not fall on the
+    // first warp (the per-step outputs rotate over the warps too, below).
+    constexpr int REM = SLOT - (NU - 1) * NT;  // slots of the last round (1..NT)
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
-        const int e = t + u * NT;
-        live[u] = e < SLOT;
+        const int e = (u == NU - 1) ? (u * NT + t - (NT - REM)) : (t + u * NT);
+        live[u] = (u == NU - 1) ? (t >= NT - REM) : (e < SLOT);
         so[u] = e;
         int iofs, lofs;
         rofs[u] = 0;
@@ -144,17 +148,17 @@ __global__ void __launch_bounds__(ColGeo<T, KB>::NT, sizeof(T) == 4 ? 2 : 1)
         idn[u] = iofs == lofs;
     }
     auto stage = [&](int Gs) {
-        double *r = raw + (Gs % RING) * SLOT + t;
+        double *r = raw + (Gs % RING) * SLOT;
         const int jb = Gs * TR;
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
             if (!live[u]) continue;
-            if (inb[u] && jb + hi_ofs[u] < ni) cp_async_small<8>(r + u * NT, src[u] + jb);
-            else r[u * NT] = (jb + hi_ofs[u] >= ni && idn[u]) ? 1.0 : 0.0;
+            if (inb[u] && jb + hi_ofs[u] < ni) cp_async_small<8>(r + so[u], src[u] + jb);
+            else r[so[u]] = (jb + hi_ofs[u] >= ni && idn[u]) ? 1.0 : 0.0;
         }
     };
     auto convert = [&](int Gs) {
-        const double *r = raw + (Gs % RING) * SLOT + t;
+        const double *r = raw + (Gs % RING) * SLOT;
         T *c = cv_ + (Gs & 1) * SLOTP;
         const int jb = Gs * TR;
 #pragma unroll
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(ColGeo<T, KB>::NT, sizeof(T) == 4 ? 2 : 1)
             const int e = so[u];
             int pos = e;  // far entries keep their slot
             if (e < 2 * TR * KB) pos = (e / KB) * KB + ((jb + rofs[u]) & (KB - 1));
-            c[pos] = from_f64<T>(r[u * NT]);
+            c[pos] = from_f64<T>(r[e]);
         }
     };
 
@@ -286,7 +290,10 @@ __global__ void __launch_bounds__(ColGeo<T, KB>::NT, sizeof(T) == 4 ? 2 : 1)
                 st_row<T, TR>(ls + (g * TR + u) * LDL + ty * TR, v);
             }
         }
-        if (ty == 0) {
+        // scaled pivot rows: every thread row holds them; row (g + GRID/2) mod GRID
+        // writes them, so the work moves from warp to warp
+        const int tw = (g + GRID / 2) % GRID;
+        if (ty == tw) {
             T *ut = UT + ((b0 + J) * KB + g * TR) * KB + tx * TR;
 #pragma unroll
             for (int u = 0; u < TR; ++u) {
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(ColGeo<T, KB>::NT, sizeof(T) == 4 ? 2 : 1)
                 st_row<T, TR>(ut + u * KB, v);
             }
         }
-        if (t == 0) {
+        if (ty == tw && tx == 0) {
 #pragma unroll
             for (int u = 0; u < TR; ++u) DI[b0 * KB + j + u] = pinv[u];
         }
