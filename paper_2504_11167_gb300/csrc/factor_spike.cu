@@ -393,7 +393,10 @@ __global__ void __launch_bounds__((KB / 4) * CG)
 // half of the panel (T_i or W_i columns: a whole warp skips an inactive half);
 // the two tile rows a quarter-warp reads are 4 apart (68 floats: 16 mod 32
 // words), so the 16-byte tile loads are conflict-free.  Staging, ring and
-// barriers as in k_sweep_pipe.
+// barriers as in k_sweep_pipe.  The backward sweep's results are the
+// COUPLING-mode u-factors themselves: they go straight to Ucat (row
+// [u_T | u_W], panel column c -> c for c < r, r + c - M/2 for the W half;
+// zeros where a partition has no such spike), not back to the panel.
 template <int MT> struct SweepBal {
     static constexpr int KB = 64, NT = 256, M = 32 * MT, NBUF = 3, PDS = 2;
     static constexpr int LDT = KB + 4, LDM = M + 4;
@@ -404,7 +407,7 @@ template <int MT> struct SweepBal {
 template <int MT>
 __global__ void __launch_bounds__(256)
     k_sweep_bal(const float *__restrict__ LT, const float *__restrict__ UT, const float *__restrict__ DI, Parts P,
-                int k, float *__restrict__ X) {
+                int k, float *__restrict__ X, int r, float *__restrict__ Ucat) {
     using SB = SweepBal<MT>;
     constexpr int KB = SB::KB, NT = SB::NT, M = SB::M, NBUF = SB::NBUF, PDS = SB::PDS;
     constexpr int LDT = SB::LDT, LDM = SB::LDM, CH = 4;
@@ -425,6 +428,14 @@ __global__ void __launch_bounds__(256)
     const int pair = (w & 3) * 2 + (l & 1);
     const int c0 = MT * ((w >> 2) * 16 + (l >> 1));
     const int ga[2] = {4 * pair, 4 * (15 - pair)};  // first rows of the two row groups
+    const int n2 = 2 * r;
+    // Ucat column of panel column c0 + j (-1: padding column)
+    int ucol[MT];
+#pragma unroll
+    for (int j = 0; j < MT; ++j) {
+        const int c = c0 + j, half = M / 2;
+        ucol[j] = (c < half) ? (c < r ? c : -1) : (c - half < r ? r + c - half : -1);
+    }
 
     auto stage = [&](int t) {
         const int buf = t % NBUF;
@@ -558,21 +569,25 @@ __global__ void __launch_bounds__(256)
                 }
             }
             __syncthreads();
-            if (active) {
-                // x_J = t + ((D^{-1}U_JJ)^{-1} strictly upper) t
-                float *xg = X + (b0 + J) * KB * M;
+            // x_J = t + ((D^{-1}U_JJ)^{-1} strictly upper) t   (zeros for an absent spike)
 #pragma unroll
-                for (int G = 0; G < 2; ++G) {
-                    const int a0 = ga[G];
+            for (int G = 0; G < 2; ++G) {
+                const int a0 = ga[G];
+                if (active) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) ld_row<float, MT>(Tt + (a0 + i) * LDM + c0, acc[i]);
                     chunk(acc, tile, Tt, a0, 3, false);
                     mac4(acc, tile, Tt, a0, a0 + 4, KB, false);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        st_row<float, MT>(Yp + (a0 + i) * LDM + c0, acc[i]);
-                        st_row<float, MT>(xg + (a0 + i) * M + c0, acc[i]);
-                    }
+                    for (int i = 0; i < 4; ++i) st_row<float, MT>(Yp + (a0 + i) * LDM + c0, acc[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t row = (int64_t)J * KB + a0 + i;
+                    if (row < ni)
+#pragma unroll
+                        for (int j = 0; j < MT; ++j)
+                            if (ucol[j] >= 0) Ucat[(s + row) * n2 + ucol[j]] = active ? acc[i][j] : 0.f;
                 }
             }
         }
@@ -903,14 +918,17 @@ template <typename T, int KB, int MT, int CG>
 static bool sweep_mt(Ctx *c) {
     Parts P{c->off_d, c->boff_d, c->p};
     constexpr int M = MT * CG, LDM = M + 16 / (int)sizeof(T), NT = (KB / 4) * CG;
+    // (32 panel columns with KB = 64 occur in COUPLING mode only: SPIKE panels are 2 KB wide)
     if constexpr (sizeof(T) == 4 && KB == 64 && M == 32) {
         using SB = SweepBal<1>;
         static_assert(SB::bytes <= 110 * 1024, "two CTAs per SM");
         auto kb = k_sweep_bal<1>;
         cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB::bytes);
+        c->u_by_sweep = true;
         return launch(c, KID_SWEEP, [&] {
             kb<<<c->p, SB::NT, SB::bytes, c->stream>>>((const float *)c->LT, (const float *)c->UT,
-                                                       (const float *)c->DI, P, c->k, (float *)c->X);
+                                                       (const float *)c->DI, P, c->k, (float *)c->X, c->r,
+                                                       (float *)c->Ucat);
         });
     }
     if constexpr (sizeof(T) == 4) {
@@ -1050,12 +1068,16 @@ LRS_KB_DISPATCH(make_u_impl)
 
 bool run_spike_rhs(Ctx *c) { return c->fp64 ? spike_rhs_impl_kb<double>(c) : spike_rhs_impl_kb<float>(c); }
 bool run_sweep(Ctx *c) {
+    c->u_by_sweep = false;
     if (c->opt.pivoting) return run_sweep_piv(c);
     return c->fp64 ? sweep_impl_kb<double>(c) : sweep_impl_kb<float>(c);
 }
 bool run_gram(Ctx *c) { return c->fp64 ? gram_impl_kb<double>(c) : gram_impl_kb<float>(c); }
 bool run_coupling_gram(Ctx *c) { return coupling_gram_impl_kb<double>(c); }
 bool run_jacobi(Ctx *c) { return c->fp64 ? jacobi_impl_kb<double>(c) : jacobi_impl_kb<float>(c); }
-bool run_make_u(Ctx *c) { return c->fp64 ? make_u_impl_kb<double>(c) : make_u_impl_kb<float>(c); }
+bool run_make_u(Ctx *c) {
+    if (c->u_by_sweep) return true;  // the sweep wrote Ucat itself
+    return c->fp64 ? make_u_impl_kb<double>(c) : make_u_impl_kb<float>(c);
+}
 
 }  // namespace lrs

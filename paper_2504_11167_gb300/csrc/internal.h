@@ -59,6 +59,9 @@ struct Ctx {
     // second iterate buffer (n doubles) for the fused retrieval + residual of
     // the IR loop; allocated when every partition holds >= 256 + 2k rows
     double *xalt = nullptr;
+    // set by run_sweep when the spike sweep wrote the COUPLING-mode u-factors
+    // into Ucat itself (run_make_u then has nothing to do)
+    bool u_by_sweep = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     int KB = 8;          // block size (>= k, power of two in 8..64)

@@ -49,6 +49,52 @@ __global__ void k_red_build(const T *__restrict__ PQ, int KB, const T *__restric
     }
 }
 
+// The same blocks with the operands staged in shared memory first (P_i,
+// Q_{i+1}, the top k rows of u of partition i+1 and the bottom k rows of
+// partition i, as doubles): every entry sums the same terms in the same order
+// as k_red_build, but reads shared memory instead of strided global loads.
+template <typename T>
+__global__ void k_red_build_s(const T *__restrict__ PQ, int KB, const T *__restrict__ Ucat, Parts P, int k,
+                              int r, double *__restrict__ E, double *__restrict__ F,
+                              double *__restrict__ Gs) {
+    extern __shared__ double sb[];
+    const int i = blockIdx.x;
+    const int n2 = 2 * r;
+    const int64_t sn = P.off[i + 1];
+    double *Ps = sb, *Qs = Ps + r * k, *Ut = Qs + r * k, *Ub = Ut + k * n2;  // [r][k] [r][k] [k][n2] [k][n2]
+    const T *Pi = PQ + ((int64_t)i * 2 + 0) * r * KB;
+    const T *Qn = PQ + ((int64_t)(i + 1) * 2 + 1) * r * KB;
+    for (int e = threadIdx.x; e < r * k; e += blockDim.x) {
+        const int a = e / k, q = e % k;
+        Ps[e] = (double)Pi[a * KB + q];
+        Qs[e] = (double)Qn[a * KB + q];
+    }
+    for (int e = threadIdx.x; e < k * n2; e += blockDim.x) {
+        const int q = e / n2, b = e % n2;
+        Ut[e] = (double)Ucat[(sn + q) * n2 + b];
+        Ub[e] = (double)Ucat[(sn - k + q) * n2 + b];
+    }
+    __syncthreads();
+    double *e_ = E + (int64_t)i * n2 * n2, *f = F + (int64_t)i * n2 * n2, *g = Gs + (int64_t)i * n2 * n2;
+    const bool hasF = (i + 1 <= P.p - 2), hasG = (i >= 1);
+    for (int t = threadIdx.x; t < n2 * n2; t += blockDim.x) {
+        const int a = t / n2, b = t % n2;
+        double ev = (a == b) ? 1.0 : 0.0, fv = 0.0, gv = 0.0;
+        if (a < r && b >= r) {            // P_i u_{W,i+1}^t
+            for (int q = 0; q < k; ++q) ev += Ps[a * k + q] * Ut[q * n2 + b];
+        } else if (a >= r && b < r) {     // Q_{i+1} u_{T,i}^b
+            for (int q = 0; q < k; ++q) ev += Qs[(a - r) * k + q] * Ub[q * n2 + b];
+        }
+        if (hasF && a < r && b < r)       // P_i u_{T,i+1}^t
+            for (int q = 0; q < k; ++q) fv += Ps[a * k + q] * Ut[q * n2 + b];
+        if (hasG && a >= r && b >= r)     // Q_{i+1} u_{W,i}^b
+            for (int q = 0; q < k; ++q) gv += Qs[(a - r) * k + q] * Ub[q * n2 + b];
+        e_[t] = ev;
+        f[t] = fv;
+        g[t] = gv;
+    }
+}
+
 // In-place inverse of the n x n matrix in Ms (row stride n) by Gauss-Jordan
 // elimination with partial pivoting on [M | I]; aug has room for n x 2n.
 // Returns false (to thread 0) on a zero pivot.
@@ -250,6 +296,14 @@ __global__ void k_red_solve_full(const double *__restrict__ Rinv, const double *
 template <typename T>
 static bool build_impl(Ctx *c, int ldpq) {
     Parts P{c->off_d, c->boff_d, c->p};
+    const size_t smem = (size_t)(2 * c->r * c->k + 4 * c->k * c->r) * sizeof(double);
+    if (smem <= 96 * 1024) {
+        cudaFuncSetAttribute(k_red_build_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return launch(c, KID_RED_BUILD, [&] {
+            k_red_build_s<T><<<c->p - 1, 256, smem, c->stream>>>((const T *)c->PQ, ldpq, (const T *)c->Ucat, P,
+                                                                 c->k, c->r, c->E, c->F, c->Gs);
+        });
+    }
     return launch(c, KID_RED_BUILD, [&] {
         k_red_build<T><<<c->p - 1, 256, 0, c->stream>>>((const T *)c->PQ, ldpq, (const T *)c->Ucat, P, c->k,
                                                         c->r, c->E, c->F, c->Gs);
