@@ -176,7 +176,7 @@ class ClockSampler:
 # n/4 rows, the bench's 256 CTAs) scaled by 4 (both grow with n).  "residual" is
 # a launch after the first of a solve (band product + the fused retrieval).
 # None = not captured for the current kernel.
-NCU_TRAFFIC = {"band_lu": 4 * (1.076124e9 + 0.507302e9), "residual": 4 * (1.238762e9 + 0.022746e9)}
+NCU_TRAFFIC = {"residual": 4 * (1.238762e9 + 0.022746e9)}
 
 
 def kernel_work(name: str, prof: dict, precision_bytes: int):
