@@ -119,6 +119,29 @@ def test_preconditioner_parity_mixed(torch_cuda, case):
     assert rel(gotT, O.apply_T(fac, np.asarray(f))) <= MIXED_TOL
 
 
+# FP32, KB = 64, COUPLING with 2r <= 32: the balanced spike sweep writes the
+# u-factors into Ucat itself.  r < 16 leaves padding columns in the 32-column
+# panel (T half: columns r..15, W half: 16+r..31); with p = 2 the first
+# partition has no W spike and the last no T spike (their u columns are zero).
+SWEEP_U_CASES = [(6000, 50, 5, 12, 1.2), (3000, 64, 2, 9, 1.2), (8000, 64, 4, 16, 1.1)]
+
+
+@pytest.mark.parametrize("case", SWEEP_U_CASES, ids=["n{}-k{}-p{}-r{}".format(*c[:4]) for c in SWEEP_U_CASES])
+def test_coupling_u_factors_written_by_the_sweep(torch_cuda, case):
+    n, k, p, r, dom = case
+    seed = 3000 + n + k + r
+    ab = inputs.dominant_band(n, k, dom, seed)
+    f = inputs.rhs(n, 1, seed)
+    fac = O.factor(ab, k, p, r, compress="coupling", reduced="truncated")
+    got, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress="coupling", reduced="truncated",
+                          outer="none", precision="fp32")
+    assert rel(got, O.apply(fac, np.asarray(f))) <= MIXED_TOL
+    x, info, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress="coupling", precision="fp32", tol=1e-10)
+    assert info["converged"]
+    res = np.asarray(f) - O.band_matvec(ab, k, x)
+    assert np.linalg.norm(res) / np.linalg.norm(f) <= 1e-10 * 1.01
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-10)])
 @pytest.mark.parametrize("reduced", ["full", "truncated"])
 @pytest.mark.parametrize("transpose", [False, True])
