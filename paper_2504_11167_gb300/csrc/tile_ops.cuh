@@ -182,32 +182,14 @@ __device__ __forceinline__ void st_row(T *p, const T (&v)[MT]) {
     }
 }
 
-// One right-hand side: lane q of row a takes the contiguous quarter
+// One right-hand side, FP32: lane q of row a takes the contiguous quarter
 // [q KB/4, (q+1) KB/4) of the masked dot product sum_j M[a][j] v[j] (16-byte
-// vector loads of the tile row and of v, four independent partial sums);
-// the quad of lanes combines it with two shuffles (every lane gets the sum).
-template <typename T, int KB, int MODE>
-__device__ __forceinline__ T tri_dot1(const T *__restrict__ Mrow, const T *v, int a, int q) {
-    constexpr int QW = KB / 4, VW = QW < 4 ? QW : 4;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-    for (int u = 0; u < QW; u += VW) {
-        T mv[VW], vv[VW];
-        ld_row<T, VW>(Mrow + q * QW + u, mv);
-        ld_row<T, VW>(v + q * QW + u, vv);
-#pragma unroll
-        for (int w = 0; w < VW; ++w) {
-            const int j = q * QW + u + w;
-            acc[w] += tri_in<MODE>(j, a) ? mv[w] * vv[w] : T(0);
-        }
-    }
-    return quad_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
-}
-
-// FP32 form of tri_dot1 with the triangle given as per-lane bit masks:
-// msk[w] is all ones where entry q KB/4 + w of the row belongs to the product
-// (INV: where it does not), so each entry costs one AND and one fused
-// multiply-add (masked-out entries contribute fma(+0, v, acc) = acc).
+// vector loads of the tile row and of v, four independent partial sums; the
+// quad of lanes combines them with two shuffles, every lane gets the sum).
+// The triangle is given as per-lane bit masks: msk[w] is all ones where entry
+// q KB/4 + w of the row belongs to the product (INV: where it does not), so
+// each entry costs one AND and one fused multiply-add (masked-out entries
+// contribute fma(+0, v, acc) = acc).
 template <int KB, bool INV>
 __device__ __forceinline__ float tri_dot1m(const float *__restrict__ Mrow, const float *v, int q,
                                           const unsigned (&msk)[KB / 4]) {
