@@ -78,7 +78,12 @@ enum { LRSPIKE_COMPRESS_SPIKE = 0, LRSPIKE_COMPRESS_COUPLING = 1 };
  * FP64 n x max_nrhs, working precision n x max_nrhs, 10 x 2k(p-1) x max_nrhs
  * FP64. */
 enum { LRSPIKE_REDUCED_FULL = 0, LRSPIKE_REDUCED_TRUNCATED = 1, LRSPIKE_REDUCED_OTF = 2 };
-/* Outer iteration: IR = iterative refinement x += M^{-1}(f - A x);
+/* Outer iteration: IR = iterative refinement x += M^{-1}(f - A x); with
+ * k <= 64, no pivoting, not OTF, not graph_safe and every partition holding
+ * >= 256 + 2k rows, the handle allocates one extra FP64 vector of n at create
+ * and a one-RHS solve forms each correction's retrieval inside the next
+ * residual kernel, the iterate alternating between x and that vector (x holds
+ * the result on return; the arithmetic is that of the separate kernels);
  * BICGSTAB = right-preconditioned BiCGStab (the paper's outer solver, section
  * 4), FP64 vectors and scalars, one iteration = two applications of M^{-1};
  * each column stops when its residual meets tol, and convergence is confirmed
@@ -150,6 +155,12 @@ lrspike_status lrspike_options_default(lrspike_options *opt, int64_t n, int32_t 
  * block kernels; 64 < k <= 1024 (wide bands) uses blocks of W = 64 ceil(k/64)
  * whose products are batched GEMMs (cuBLAS: FP64, FP32, or TF32 tensor cores
  * with LRSPIKE_MIXED_TF32), SPIKE compression, no pivoting, r <= 32.
+ * COUPLING compression with k <= 64, p > 1 and r > 0: the handle also owns a
+ * second, non-blocking stream and two events; lrspike_factor runs the
+ * coupling blocks' Gram matrices, eigenvectors and spike right-hand sides on
+ * it beside the band LU, forked from and joined back into cuda_stream (work
+ * after the factor call on cuda_stream sees all of it; under stream capture
+ * the fork and join become graph edges).
  * Errors: INVALID_ARG (n < 1, k < 0 or k > 1024, r < 0 or r > k, p < 1,
  * n_i <= k with p > 1, max_nrhs < 1, unknown enum), UNSUPPORTED, OOM, CUDA. */
 lrspike_status lrspike_create(const lrspike_options *opt, void *cuda_stream, lrspike_handle *out);
