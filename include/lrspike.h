@@ -95,7 +95,7 @@ enum { LRSPIKE_OUTER_IR = 0, LRSPIKE_OUTER_BICGSTAB = 1, LRSPIKE_OUTER_NONE = 2 
 
 typedef struct {
     int64_t n;            /* matrix order, n >= 1                                    */
-    int32_t k;            /* half-bandwidth, 0 <= k <= 64                            */
+    int32_t k;            /* half-bandwidth, 0 <= k <= 1024 (k > 64: wide-band path) */
     int32_t p;            /* partitions, 1 <= p, every n_i > k when p > 1           */
     int32_t r;            /* compression rank n_svd, 0 <= r <= k                     */
     int32_t precision;    /* LRSPIKE_FP64 | LRSPIKE_MIXED_FP32 | LRSPIKE_MIXED_TF32  */

@@ -34,13 +34,18 @@ lrspike_status err(lrspike_status st, const std::string &m) {
     return st;
 }
 
-bool on_device(const void *p) {
+// Device memory of GPU `dev` (the current device), or managed memory (which
+// every device can reach).  Device memory of another GPU is refused: the
+// kernel runs on the current device and would reach it only through peer
+// access, if at all.
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -56,13 +61,15 @@ extern "C" lrspike_status lrspike_residual_noalloc(const double *band, int64_t l
     if (ctas * nrhs > kPartials)
         return err(LRSPIKE_ERR_INVALID_ARG,
                    "ceil(n/256) * nrhs exceeds the static scratch of LRSPIKE_NOALLOC_MAX_PARTIALS partial sums");
-    if (!on_device(band) || !on_device(f) || !on_device(x) || !on_device(r) || !on_device(norms))
-        return err(LRSPIKE_ERR_INVALID_ARG, "band, f, x, r and norms must be device memory");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return err(LRSPIKE_ERR_CUDA, "no usable current CUDA device");
     }
+    if (!on_device(band, dev) || !on_device(f, dev) || !on_device(x, dev) || !on_device(r, dev) ||
+        !on_device(norms, dev))
+        return err(LRSPIKE_ERR_INVALID_ARG,
+                   "band, f, x, r and norms must be device memory of the current device (or managed memory)");
     DeviceScratch sc;
     {
         // once per device, with that device current: the device addresses of
@@ -77,6 +84,14 @@ extern "C" lrspike_status lrspike_residual_noalloc(const double *band, int64_t l
                 return err(LRSPIKE_ERR_CUDA, std::string("cudaGetSymbolAddress failed: ") +
                                                  cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
             }
+            // the ticket counter must start at zero; the last CTA of every
+            // launch puts it back to zero, so it is cleared here once, on the
+            // first call's stream (the static array starts zeroed at module
+            // load as well)
+            if (cudaMemsetAsync(pc, 0, sizeof(unsigned int), (cudaStream_t)cuda_stream) != cudaSuccess) {
+                cudaGetLastError();
+                return err(LRSPIKE_ERR_CUDA, "counter reset failed");
+            }
             g_dev[dev].partial = static_cast<double *>(pp);
             g_dev[dev].counter = static_cast<unsigned int *>(pc);
             g_dev[dev].ready = true;
@@ -84,11 +99,6 @@ extern "C" lrspike_status lrspike_residual_noalloc(const double *band, int64_t l
         sc = g_dev[dev];
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    // the ticket counter must start at zero (the array keeps the last call's contents)
-    if (cudaMemsetAsync(sc.counter, 0, sizeof(unsigned int), st) != cudaSuccess) {
-        cudaGetLastError();
-        return err(LRSPIKE_ERR_CUDA, "counter reset failed");
-    }
     if (!lrs::launch_residual_raw(band, ld_band, k, n, f, x, ld, nrhs, r, sc.partial, sc.counter, norms, st))
         return err(LRSPIKE_ERR_CUDA, "residual kernel launch failed");
     lrs::set_handleless_error("");

@@ -113,13 +113,27 @@ def residual_noalloc(band, k: int, f, x, r, norms, stream=None) -> None:
     lib = load_library()
     F = f.unsqueeze(0) if f.dim() == 1 else f
     X = x.unsqueeze(0) if x.dim() == 1 else x
-    n = r.shape[-1]
+    R = r.unsqueeze(0) if r.dim() == 1 else r
     nrhs, ld = F.shape
+    n = R.shape[-1]
+    # the C entry point sees raw pointers only: every extent it will touch is
+    # checked here against the tensors
+    for name, t in (("band", band), ("f", F), ("x", X), ("r", R), ("norms", norms)):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if X.shape != F.shape:
+        raise ValueError("x must have the shape of f")
+    if R.shape != (nrhs, n) or ld < n:
+        raise ValueError("r must be (nrhs, n) with n <= the leading dimension of f")
+    if norms.numel() < nrhs:
+        raise ValueError("norms must hold nrhs values")
+    if band.dim() != 2 or band.shape[0] != 2 * k + 1 or band.shape[1] < n:
+        raise ValueError("band must be (2k+1, ld_band) with ld_band >= n")
     if stream is None:
         stream = torch.cuda.current_stream()
     st = lib.lrspike_residual_noalloc(ctypes.c_void_p(_ptr(band)), band.shape[1], n, k,
                                       ctypes.c_void_p(_ptr(F)), ctypes.c_void_p(_ptr(X)),
-                                      ctypes.c_void_p(_ptr(r)), nrhs, ld,
+                                      ctypes.c_void_p(_ptr(R)), nrhs, ld,
                                       ctypes.c_void_p(_ptr(norms)),
                                       ctypes.c_void_p(stream.cuda_stream))
     if st != 0:
