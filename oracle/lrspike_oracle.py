@@ -21,7 +21,8 @@ What it computes, step by step in the paper's order:
     alternative the paper discusses at the end of section 3.1.  For wide bands
     (k > 64) the truncation is the randomized SVD the paper uses (section 3.1,
     Halko-Martinsson-Tropp proto-algorithm with a few passes and oversampling),
-    written here on the right singular subspace through the Gram matrix;
+    applied to the explicit spike: sketch, Householder QR, power passes,
+    small SVD of Q^T T;
   * the reduced system of the low-rank spike matrix S~ = I + U V
     (section 3.2, eqs. 'per-partition_1/2' and 'red_sys_prec_mid_1'), in
     compressed unknowns zeta_i = P_i x_{i+1,t}, omega_{i+1} = Q_{i+1} x_{i,b}
@@ -215,48 +216,29 @@ def gaussian_sketch(rows: int, cols: int, seed: int) -> np.ndarray:
     return om
 
 
-def _orth_by_gram(Y: np.ndarray, tol: float) -> np.ndarray:
-    """Orthonormal basis of range(Y) from the eigendecomposition of Y^T Y:
-    Q = Y V Lambda^{-1/2}; directions with sqrt(lambda_j) <= tol sqrt(lambda_max)
-    are dropped (zero columns)."""
-    C = Y.T @ Y
-    lam, V = np.linalg.eigh(C)
-    Q = np.zeros_like(Y)
-    top = np.sqrt(max(lam.max(), 0.0))
-    for j in range(lam.size):
-        sj = np.sqrt(max(lam[j], 0.0))
-        if top > 0.0 and sj > tol * top:
-            Q[:, j] = (Y @ V[:, j]) / sj
-    return Q
+def randomized_truncation(X: np.ndarray, r: int, ell: int, q: int, seed: int, rank_tol: float):
+    """Rank-r truncation of X (n_i x k) by the randomized SVD of section 3.1
+    (Halko, Martinsson and Tropp's proto-algorithm: a Gaussian sketch of ell =
+    r + oversampling columns and q power passes), applied to X itself:
 
+      Y = X Omega (Omega: k x ell Gaussian sketch);   Q = qr(Y)
+      q times:   Y = X (X^T Q);   Q = qr(Y)          (re-orthonormalised pass)
+      B = Q^T X  (ell x k);   B = U_B diag(s) V^T    (SVD)
+      U = Q U_B,  keep the r largest s.
 
-def randomized_truncation(X: np.ndarray, r: int, ell: int, q: int, seed: int, rank_tol: float,
-                          orth_tol: float = 1e-7):
-    """Rank-r truncation of X (n_i x k) by randomized subspace iteration on
-    its right singular subspace (the HMT proto-algorithm with q power passes
-    and ell = r + oversampling columns, applied to G = X^T X):
-      Y = G Omega;  q times: Q = orth(Y), Y = G Q;  Q = orth(Y);
-      H = Q^T G Q = W Theta W^T (Rayleigh-Ritz);  V_r = Q W[:, top r];
-      sigma_j = sqrt(theta_j).
-    With ell = k the basis Q spans everything and the result is the exact
-    truncated SVD.  Returns (U, sig, Vt, all Ritz values) like truncated_svd,
-    with U = X V_r / sigma (the left factor) and the rank guard of
-    truncated_svd."""
+    qr is the Householder QR of LAPACK (numpy), the SVD LAPACK's.  With ell = k
+    and X of rank k, Q spans range(X), Q Q^T X = X and the result is the exact
+    truncated SVD.  Returns (U, sig, Vt, all singular values of B) like
+    truncated_svd, with its rank guard."""
     k = X.shape[1]
-    G = X.T @ X
-    Y = G @ gaussian_sketch(k, ell, seed)
+    Q = np.linalg.qr(X @ gaussian_sketch(k, ell, seed))[0]
     for _ in range(q):
-        Y = G @ _orth_by_gram(Y, orth_tol)
-    Q = _orth_by_gram(Y, orth_tol)
-    th, Wm = np.linalg.eigh(Q.T @ G @ Q)
-    order = np.argsort(-th, kind="stable")
-    th = np.maximum(th[order], 0.0)
-    sv = np.sqrt(th)
+        Q = np.linalg.qr(X @ (X.T @ Q))[0]
+    Ub, sv, Vt = np.linalg.svd(Q.T @ X, full_matrices=False)
     U, sig, V = np.zeros((X.shape[0], r)), np.zeros(r), np.zeros((r, k))
     for j in range(min(r, sv.size)):
         if sv[0] > 0.0 and sv[j] > rank_tol * sv[0]:
-            v = Q @ Wm[:, order[j]]
-            U[:, j], sig[j], V[j, :] = (X @ v) / sv[j], sv[j], v
+            U[:, j], sig[j], V[j, :] = Q @ Ub[:, j], sv[j], Vt[j, :]
     return U, sig, V, sv
 
 
@@ -318,7 +300,7 @@ class Factor:
 def factor(ab: np.ndarray, k: int, p: int, r: int, compress: str = "spike",
            reduced: str = "full", pivoting: bool = False, rank_tol: float = 1e-13,
            threads: int = 1, randomized: Optional[bool] = None, oversample: Optional[int] = None,
-           power_iters: int = 2, seed: int = SKETCH_SEED, orth_tol: float = 1e-7) -> Factor:
+           power_iters: int = 2, seed: int = SKETCH_SEED) -> Factor:
     """LR-SPIKE factorisation of the banded A (FP64).
 
     compress: "spike" (truncated SVD of the explicit spikes, section 3.1) or
@@ -351,8 +333,7 @@ def factor(ab: np.ndarray, k: int, p: int, r: int, compress: str = "spike",
 
     def trunc(X, i, side):
         if randomized and compress == "spike":
-            return randomized_truncation(X, r, ell, power_iters, sketch_seed(seed, i, side), rank_tol,
-                                         orth_tol)
+            return randomized_truncation(X, r, ell, power_iters, sketch_seed(seed, i, side), rank_tol)
         return truncated_svd(X, r, rank_tol)
 
     def one(i):

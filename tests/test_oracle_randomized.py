@@ -1,12 +1,15 @@
 """Pins of the oracle's randomized truncation (wide bands, k > 64).
 
 The paper truncates the spikes with the randomized SVD of Halko, Martinsson
-and Tropp (section 3.1).  What fixes the oracle here, independently of its own
-code: the published output sequence of the SplitMix64 generator, the moments
-of the Gaussian sketch, the special case ell = k (the randomized truncation
-must then equal the exact truncated SVD), the Eckart-Young error of the exact
-truncation (the randomized one may not beat it and should stay close to it on
-a fast-decaying spectrum), and the final residual of a wide-band solve.
+and Tropp (section 3.1): sketch the spike, orthonormalise, power passes, small
+SVD of Q^T T.  What fixes the oracle here, independently of its own code: the
+published output sequence of the SplitMix64 generator, the moments of the
+Gaussian sketch, the special case ell = k (the randomized truncation must then
+equal the exact truncated SVD, also for spectra spanning many orders of
+magnitude), exactly low-rank inputs (recovered to rounding), the Eckart-Young
+error of the exact truncation (the randomized one may not beat it and should
+stay close to it on a fast-decaying spectrum, closer with power passes than
+without), and wide-band solves (r = k reproduces A^{-1} to rounding).
 """
 import numpy as np
 import pytest
@@ -44,16 +47,49 @@ def decaying(m, k, seed, rate=0.7):
 
 
 def test_full_sketch_equals_exact_truncated_svd():
-    """ell = k with every direction kept (sigma_k^2 / sigma_1^2 = 0.9^78 = 2.7e-4,
-    far above the orthonormalisation cut of 1e-7): the basis spans R^k and the
-    Rayleigh-Ritz step returns the exact truncated SVD, up to rounding."""
+    """ell = k: the basis spans range(X) and the truncation is the exact
+    truncated SVD, up to rounding."""
     X, _ = decaying(600, 40, 1, rate=0.9)
     r = 6
     Ue, se, Ve, _ = O.truncated_svd(X, r, 1e-13)
     Ur, sr, Vr, _ = O.randomized_truncation(X, r, 40, 2, 99, 1e-13)
-    assert np.allclose(sr, se, rtol=1e-10, atol=0)
+    assert np.allclose(sr, se, rtol=1e-12, atol=0)
     Te, Tr = (Ue * se) @ Ve, (Ur * sr) @ Vr
-    assert np.linalg.norm(Tr - Te) <= 1e-10 * np.linalg.norm(Te)
+    assert np.linalg.norm(Tr - Te) <= 1e-12 * np.linalg.norm(Te)
+
+
+def test_full_sketch_resolves_a_wide_spectrum():
+    """Singular values from 1 down to 1e-12 (a Gram matrix X^T X would square
+    them below FP64 resolution): with ell = r = k the sketch spans range(X) and
+    X is reproduced to rounding, every singular value to ~eps relative to
+    sigma_1."""
+    X, s = decaying(500, 48, 4, rate=10 ** (-12 / 47))
+    Ur, sr, Vr, _ = O.randomized_truncation(X, 48, 48, 2, 3, 1e-15)
+    assert np.linalg.norm(X - (Ur * sr) @ Vr, 2) <= 1e-14 * s[0]
+    assert np.all(np.abs(sr - s) <= 1e-14 * s[0])
+
+
+def test_exactly_low_rank_input_is_recovered():
+    """rank(X) = 7 <= r: Q spans range(X) whatever the sketch, so the
+    truncation returns X itself (the rank <= r invariant of the survey)."""
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((400, 7)) @ rng.standard_normal((7, 90))
+    for q in (0, 1, 2):
+        Ur, sr, Vr, _ = O.randomized_truncation(X, 7, 12, q, 5, 1e-13)
+        assert np.linalg.norm(X - (Ur * sr) @ Vr) <= 1e-13 * np.linalg.norm(X)
+
+
+def test_power_passes_reduce_the_error():
+    """Slowly decaying spectrum: each power pass raises the spectrum seen by
+    the sketch to a higher power, so the error approaches sigma_{r+1}."""
+    X, s = decaying(700, 120, 6, rate=0.97)
+    r = 10
+    errs = []
+    for q in (0, 1, 3):
+        Ur, sr, Vr, _ = O.randomized_truncation(X, r, 2 * r, q, 17, 1e-13)
+        errs.append(np.linalg.norm(X - (Ur * sr) @ Vr, 2))
+    assert errs[0] > errs[1] > errs[2] >= s[r] * (1 - 1e-9)
+    assert errs[2] <= 1.1 * s[r]
 
 
 def test_randomized_error_close_to_eckart_young():
@@ -86,20 +122,16 @@ def test_wide_band_factor_defaults_to_randomized_and_solves():
     assert np.linalg.norm(g1 - g2) <= 1e-2 * np.linalg.norm(g2)
 
 
-def test_wide_band_full_rank_sketch_is_near_exact_spike():
-    """r = k, ell = k on a wide band: the exact truncation would give
-    M^{-1} = A^{-1}; through G = T^T T the FP64 eigenvalues carry absolute
-    errors ~ eps sigma_1^2, so spike directions below ~1e-4 sigma_1 (here the
-    tail of a fast-decaying spike spectrum) are not resolved.  M^{-1} f then
-    agrees with A^{-1} f to ~1e-5, each refinement step contracts the residual
-    by ~1e-5, so 1e-12 takes at most three steps; the exact truncation stays
-    exact to rounding."""
+def test_wide_band_full_rank_sketch_is_exact():
+    """r = k, ell = k on a wide band: every truncated spike is the exact spike,
+    so M^{-1} = A^{-1} (FULL reduced system) to rounding, and refinement needs
+    one step; the exact truncated SVD gives the same."""
     n, k, p = 900, 70, 3
     ab = inputs.dominant_band(n, k, 1.5, 5)
     f = inputs.rhs(n, 1, 5)
     xs = np.linalg.solve(O.band_to_dense(ab, k), f)
     fac = O.factor(ab, k, p, k, reduced="full")
-    assert np.linalg.norm(O.apply(fac, f) - xs) <= 1e-5 * np.linalg.norm(xs)
-    assert O.ir_solve(ab, k, fac, f, tol=1e-12).iterations <= 3
+    assert np.linalg.norm(O.apply(fac, f) - xs) <= 1e-12 * np.linalg.norm(xs)
+    assert O.ir_solve(ab, k, fac, f, tol=1e-12).iterations <= 1
     exact = O.factor(ab, k, p, k, reduced="full", randomized=False)
     assert np.linalg.norm(O.apply(exact, f) - xs) <= 1e-12 * np.linalg.norm(xs)
