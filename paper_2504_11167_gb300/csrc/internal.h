@@ -211,6 +211,28 @@ bool run_dstage_t_piv(Ctx *c, const double *hin, double *x, int64_t ldx, int nrh
 bool launch_residual_raw(const double *band, int64_t ldb, int k, int64_t n, const double *f,
                          const double *x, int64_t ld, int nrhs, double *r, double *partial,
                          unsigned *counter, double *nrm, cudaStream_t st);
+// Block products of the wide-band path on the tensor cores (tc_gemm.cu):
+// C_b = alpha A'_b B'_b^T + beta C_b with K-contiguous operands, element
+// (m, k) of A'_b at p + b s + m ld + k (FP32 values read as TF32, or BF16).
+struct GemmOperand {
+    const void *p;
+    int64_t ld, s;
+};
+// Outputs (each nullable): f, FP32 column-major f[m + n ldf + b sf] (beta
+// reads it); row, operand type, row-major row[(n % rsplit) + (n / rsplit) rss
+// + m ldr + b sr] (rsplit 0 = no split); col, operand type, column-major.
+struct GemmOutput {
+    float *f = nullptr;
+    int64_t ldf = 0, sf = 0;
+    void *row = nullptr;
+    int64_t ldr = 0, sr = 0;
+    int rsplit = 0;
+    int64_t rss = 0;
+    void *col = nullptr;
+    int64_t ldc = 0, sc = 0;
+};
+bool tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, int batch, float alpha, const GemmOperand &A,
+             const GemmOperand &B, float beta, const GemmOutput &C, int *err_dev, std::string *err);
 // error text returned by lrspike_last_error(NULL)
 void set_handleless_error(const std::string &msg);
 // M^{-1} (or M^{-T}) applied to the FP64 vector in (n x nrhs, leading
