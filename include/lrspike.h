@@ -53,10 +53,15 @@ typedef enum {
 
 /* Working precision of the preconditioner (factors, spikes, D-stage,
  * retrieval).  The residual f - A x, the reduced system and the solution
- * update are always FP64.  MIXED_TF32: as MIXED_FP32 with the block products
- * of the band LU on the tensor cores (TF32 operands, FP32 accumulation; the
- * triangular base blocks stay FP32); for k > 64 every block GEMM. */
-enum { LRSPIKE_FP64 = 0, LRSPIKE_MIXED_FP32 = 1, LRSPIKE_MIXED_TF32 = 2 };
+ * update are always FP64 (the single-precision preconditioner inside a
+ * double-precision solve of section 4).  MIXED_TF32: as MIXED_FP32 with the
+ * block products of the band LU on the tensor cores (TF32 operands, FP32
+ * accumulation; the triangular base blocks stay FP32); for k > 64 every block
+ * product of the factorisation and the spike compression (tcgen05, FP32
+ * accumulator).  MIXED_BF16 (k > 64 only): those block products take BF16
+ * operands (rounded to nearest even from the FP32 values), FP32 accumulation;
+ * factors are stored in FP32 and the D-stage runs in FP32. */
+enum { LRSPIKE_FP64 = 0, LRSPIKE_MIXED_FP32 = 1, LRSPIKE_MIXED_TF32 = 2, LRSPIKE_MIXED_BF16 = 3 };
 /* Compression of the spikes (section 3.1): SPIKE = truncated SVD of the
  * explicit spikes T_i, W_i (the paper's choice, optimal by Eckart-Young);
  * COUPLING = truncated SVD of B_i, C_i, then r-column solves (the cheaper
@@ -98,7 +103,7 @@ typedef struct {
     int32_t k;            /* half-bandwidth, 0 <= k <= 1024 (k > 64: wide-band path) */
     int32_t p;            /* partitions, 1 <= p, every n_i > k when p > 1           */
     int32_t r;            /* compression rank n_svd, 0 <= r <= k                     */
-    int32_t precision;    /* LRSPIKE_FP64 | LRSPIKE_MIXED_FP32 | LRSPIKE_MIXED_TF32  */
+    int32_t precision;    /* LRSPIKE_FP64 | LRSPIKE_MIXED_FP32 | _TF32 | _BF16       */
     int32_t pivoting;     /* 0 = none; 1 = partial pivoting inside each partition   */
     int32_t compress;     /* LRSPIKE_COMPRESS_*                                      */
     int32_t reduced;      /* LRSPIKE_REDUCED_*                                       */
@@ -111,10 +116,13 @@ typedef struct {
     int32_t max_nrhs;     /* largest nrhs a solve may pass (default 16)              */
     int32_t profile;      /* 1 = time every kernel with CUDA events (see below)     */
     /* Wide bands (k > 64) truncate the spikes with the randomized SVD the paper
-     * uses (section 3.1, Halko-Martinsson-Tropp): ell = min(k, r + oversample)
-     * sketch columns (ell <= 64), power_iters passes, Gaussian sketches from
-     * SplitMix64 + Box-Muller at counter a*ell + j with seed + 2 i + side
-     * (partition i, side 0 = T_i, 1 = W_i).  Ignored for k <= 64 (exact SVD). */
+     * uses (section 3.1, Halko-Martinsson-Tropp proto-algorithm on the spike
+     * T: Y = T Omega, orthonormal basis Q, power_iters passes Y = T (T^T Q),
+     * SVD of Q^T T): ell = min(k, r + oversample) sketch columns (ell <= 64 in
+     * FP64, <= 128 in the mixed modes), Gaussian sketches from SplitMix64 +
+     * Box-Muller at counter a*ell + j with seed + 2 i + side (partition i,
+     * side 0 = T_i, 1 = W_i); the basis by shifted CholeskyQR3.  Ignored for
+     * k <= 64 (exact SVD). */
     int32_t oversample;   /* default r                                               */
     int32_t power_iters;  /* default 2                                               */
     uint64_t seed;        /* default 0x4C52535049                                    */
@@ -153,8 +161,12 @@ lrspike_status lrspike_options_default(lrspike_options *opt, int64_t n, int32_t 
  * cuda_stream: a cudaStream_t (NULL = legacy default stream), borrowed.
  * k <= 64 uses blocks of KB in {8, 16, 32, 64} >= k and the hand-written
  * block kernels; 64 < k <= 1024 (wide bands) uses blocks of W = 64 ceil(k/64)
- * whose products are batched GEMMs (cuBLAS: FP64, FP32, or TF32 tensor cores
- * with LRSPIKE_MIXED_TF32), SPIKE compression, no pivoting, r <= 32.
+ * whose products are batched over the partitions: on the tensor cores
+ * (tcgen05; TF32 or BF16 operands, FP32 accumulation) in the MIXED_TF32 and
+ * MIXED_BF16 modes, as SIMT GEMMs in the working precision in the FP64 and
+ * MIXED_FP32 modes; SPIKE compression, no pivoting, r <= 32, sketch width
+ * min(k, r + oversample) <= 64 (FP64) or <= 128 (mixed modes).  The wide-band
+ * D-stage runs one cluster of CTAs per partition (at most 8).
  * COUPLING compression with k <= 64, p > 1 and r > 0: the handle also owns a
  * second, non-blocking stream and two events; lrspike_factor runs the
  * coupling blocks' Gram matrices, eigenvectors and spike right-hand sides on

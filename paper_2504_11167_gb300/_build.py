@@ -1,9 +1,10 @@
 """Builds ``liblrspike.so`` (the CUDA library behind include/lrspike.h) in-tree.
 
 Every translation unit under ``csrc/`` is compiled for sm_103a only, in
-parallel, then linked against the shared CUDA runtime (and cuBLAS, whose
-batched GEMMs carry the block products of wide bands) so the library and
-PyTorch use one runtime instance.
+parallel, then linked against the shared CUDA runtime so the library and
+PyTorch use one runtime instance.  No CUDA library beyond the runtime is
+linked: every kernel is in ``csrc/`` (the tensor-map encoder of the TMA
+copies comes from the driver through the runtime's entry-point query).
 """
 from __future__ import annotations
 
@@ -69,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcublas"], check=True)
+    subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -16,7 +16,8 @@ const char *const kKernelNames[KID_COUNT] = {
     "gram_reduce",  "coupling_gram", "jacobi",      "make_u",      "reduced_build",
     "reduced_factor", "norm",        "residual",    "dstage",      "reduced_solve",
     "retrieve",     "project_t",     "dstage_t",    "bicgstab_vector", "matvec",
-    "wide_gather",  "wide_gemm",     "wide_lu64",   "wide_vector", "nonzero_diagonals", "band_lu_inv", "otf"};
+    "wide_gather",  "wide_gemm_simt", "wide_lu64",  "wide_vector", "wide_gemm_tc", "wide_cholqr", "wide_dstage",
+    "nonzero_diagonals", "band_lu_inv", "otf"};
 
 static cudaEvent_t take_event(Ctx *c) {
     if (!c->free_events.empty()) {
@@ -156,7 +157,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     if (o.r < 0 || o.r > o.k) return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "r must be in 0..k");
     if (o.max_nrhs < 1 || o.max_nrhs > 16)
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "max_nrhs must be in 1..16");
-    if (o.precision < LRSPIKE_FP64 || o.precision > LRSPIKE_MIXED_TF32 || o.compress < 0 || o.compress > 1 ||
+    if (o.precision < LRSPIKE_FP64 || o.precision > LRSPIKE_MIXED_BF16 || o.compress < 0 || o.compress > 1 ||
         o.reduced < 0 || o.reduced > 2 || o.outer < 0 || o.outer > 2 || o.pivoting < 0 || o.pivoting > 1)
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "unknown enum value in options");
     if (o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rank_tol >= 0.0))
@@ -172,8 +173,12 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
         return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "k > 64 supports SPIKE compression without pivoting");
     if (wide && (o.oversample < 0 || o.power_iters < 0))
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "oversample and power_iters must be >= 0");
-    if (wide && o.p > 1 && o.r > 0 && std::min(o.k, o.r + o.oversample) > 64)
-        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "min(k, r + oversample) > 64 sketch columns is not built");
+    if (wide && o.p > 1 && o.r > 0 &&
+        std::min(o.k, o.r + o.oversample) > (o.precision == LRSPIKE_FP64 ? 64 : 128))
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED,
+                    "min(k, r + oversample) sketch columns beyond 64 (FP64) / 128 (mixed) is not built");
+    if (!wide && o.precision == LRSPIKE_MIXED_BF16)
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "BF16 operands are built for the wide-band path (k > 64)");
     if (o.r > 32) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "r > 32 is not built yet");
     if (o.reduced == LRSPIKE_REDUCED_OTF) {
         if (o.p < 2 || o.r < 1)

@@ -1023,6 +1023,7 @@ bool run_jacobi_batch(Ctx *c, int n, const double *G, int nmat, int rout, double
     }
     if (n == 16) return jacobi_batch_kb<float, 16>(c, G, nmat, rout, rank_tol, out, sigma);
     if (n == 32) return jacobi_batch_kb<float, 32>(c, G, nmat, rout, rank_tol, out, sigma);
+    if (n == 128) return jacobi_batch_kb<float, 128>(c, G, nmat, rout, rank_tol, out, sigma);
     return jacobi_batch_kb<float, 64>(c, G, nmat, rout, rank_tol, out, sigma);
 }
 

@@ -1,5 +1,6 @@
 // Internal state and launcher declarations of the LR-SPIKE CUDA library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,6 +35,9 @@ enum KernelId {
     KID_WIDE_GEMM,
     KID_WIDE_LU64,
     KID_WIDE_VEC,
+    KID_WIDE_TC,
+    KID_WIDE_CHOLQR,
+    KID_WIDE_DSTAGE,
     KID_DIAGS,
     KID_LU_INV,
     KID_OTF,
@@ -111,21 +115,37 @@ struct Ctx {
     double *dots = nullptr;
     double *bpartial = nullptr;
 
-    // wide bands (k > 64): blocks of W = 64 ceil(k/64), block products as
-    // batched GEMMs; every partition padded to NBW blocks (PS = NBW W rows)
+    // wide bands (k > 64): blocks of W = 64 ceil(k/64); every partition padded
+    // to NBW blocks (PS = NBW W rows).  Block products run on the tensor cores
+    // (gpath 1: TF32, 2: BF16 operands) or as SIMT GEMMs (gpath 0: FP64 and
+    // FP32 modes).  Each matrix that enters products is kept in the layouts
+    // they read (WMat in wide.cu): working precision column-major / row-major,
+    // operand type column-major / row-major.
     bool wide = false;
     int W = 0, NBW = 0, ell = 0, lp = 0;
     int64_t PS = 0;
-    void *blas = nullptr;                                                 // cublasHandle_t
-    void *WLi = nullptr, *WUi = nullptr, *WZ = nullptr, *WY = nullptr;   // [p][NBW][W x W]
-    void *WS = nullptr, *WB = nullptr, *WC = nullptr, *WT = nullptr;     // [p][W x W] work
-    void *WX1 = nullptr, *WX2 = nullptr;   // spike panels [p][PS x 2W]
-    void *WG = nullptr;                    // [2p][W x W] Gram matrices of the spikes
-    void *WOm = nullptr, *WYk = nullptr, *WQk = nullptr, *WTk = nullptr;  // [2p][W x lp]
-    void *WH = nullptr, *WE = nullptr;     // [2p][lp x lp]
-    double *WHd = nullptr, *Wsg = nullptr; // [2p][lp x lp] FP64 copy, [2p][lp]
-    void *WV1 = nullptr, *WV2 = nullptr;   // vector panels [p][PS x 16]
-    void **Wptr = nullptr;                 // device pointer arrays of the grouped GEMMs
+    int gpath = 0;
+    size_t osize = 8;        // operand element size of the block products
+    int dcs = 0;             // CTAs per partition (cluster size) of the last D-stage launch
+    // factor tiles, kinds 0..3 = L_JJ^{-1}, U_JJ^{-1}, Z_J = U_{J,J+1}, Y_J = L_{J+1,J},
+    // each [p][NBW][W x W]; layouts f, fr, oc, orow
+    void *WF[4] = {}, *WFr[4] = {}, *WFoc[4] = {}, *WFor[4] = {};
+    // block-step work [p][W x W] (layouts f, fr, oc, orow): Schur complement,
+    // A_{J,J+1}, A_{J+1,J}, recursion temporary
+    void *WSm[4] = {}, *WBm[4] = {}, *WCm[4] = {}, *WTm[4] = {};
+    void *WX1 = nullptr, *WX2 = nullptr;    // spike panels [p][PS x 2W], working precision
+    void *WX1c = nullptr, *WX2c = nullptr;  // operand-type copies (BF16 only)
+    void *WXr = nullptr;                    // operand-type row-major final spikes [p][2][PS][W]
+    void *WOm = nullptr;                    // sketches [2p][W x lp] (operand type)
+    void *WYk = nullptr, *WQk = nullptr;    // [2p][PS x lp]: range basis iterates (working)
+    void *WQc = nullptr;                    // operand-type copy of the basis (BF16 only)
+    void *WZk = nullptr, *WZc = nullptr;    // [2p][W x lp]: T^T Q (working / operand BF16)
+    void *WG = nullptr;                     // [2p][lp x lp] Gram (working)
+    double *WGd = nullptr;                  // [2p][lp x lp] FP64 Gram
+    void *WRi = nullptr;                    // [2p][lp x lp] R^{-1} of the CholeskyQR pass
+    void *WE = nullptr;                     // [2p][r][lp] leading eigenvectors
+    void *WV1 = nullptr, *WV2 = nullptr;    // vector panels [p][PS x 16]
+    int *gemm_err = nullptr;                // tensor-core GEMM wait-limit flag
     int *diag_list = nullptr;              // band rows holding a nonzero (residual), or NULL
     int ndiag = 0;
 
@@ -220,7 +240,8 @@ struct GemmOperand {
 };
 // Outputs (each nullable): f, FP32 column-major f[m + n ldf + b sf] (beta
 // reads it); row, operand type, row-major row[(n % rsplit) + (n / rsplit) rss
-// + m ldr + b sr] (rsplit 0 = no split); col, operand type, column-major.
+// + m ldr + b sr] (rsplit 0 = no split); frow, FP32 with the same row-major
+// map; col, operand type, column-major.
 struct GemmOutput {
     float *f = nullptr;
     int64_t ldf = 0, sf = 0;
@@ -230,7 +251,12 @@ struct GemmOutput {
     int64_t rss = 0;
     void *col = nullptr;
     int64_t ldc = 0, sc = 0;
+    float *frow = nullptr;
 };
+// A tiled TMA tensor map (no swizzle, zero fill out of range) through the
+// driver's encoder; false with *err set when the encoder refuses it.
+bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
+                       const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *estr, std::string *err);
 bool tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, int batch, float alpha, const GemmOperand &A,
              const GemmOperand &B, float beta, const GemmOutput &C, int *err_dev, std::string *err);
 // error text returned by lrspike_last_error(NULL)

@@ -68,7 +68,8 @@ struct TcParams {
     int64_t rss;
     void *col;
     int64_t ldc, sc;
-    int vec_row;  // 1: the row-major copy may be written with 16-byte stores
+    float *frow;  // FP32 row-major copy (same index map as row)
+    int vec_row;  // 1: the row-major copies may be written with 16-byte stores
     int *err;
 };
 
@@ -181,6 +182,43 @@ template <>
 __device__ __forceinline__ float to_op<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Columns nb .. nb+nv-1 of row m (values v) into a row-major copy:
+// dst[(n % rsplit) + (n / rsplit) rss + m ldr + b sr].
+template <typename OutT>
+__device__ __forceinline__ void store_row(OutT *base, const TcParams &P, int b, int m, int nb, int nv,
+                                          const float (&v)[32]) {
+    OutT *rp = base + (int64_t)b * P.sr + (int64_t)m * P.ldr;
+    if (P.vec_row && nv == 32) {
+        OutT *dst = rp + (nb % P.rsplit) + (int64_t)(nb / P.rsplit) * P.rss;
+        if constexpr (sizeof(OutT) == 2) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(v[j], v[j + 1]);
+                __nv_bfloat162 h1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
+                __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
+                __nv_bfloat162 h3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
+                uint4 u;
+                u.x = *reinterpret_cast<uint32_t *>(&h0);
+                u.y = *reinterpret_cast<uint32_t *>(&h1);
+                u.z = *reinterpret_cast<uint32_t *>(&h2);
+                u.w = *reinterpret_cast<uint32_t *>(&h3);
+                *reinterpret_cast<uint4 *>(dst + j) = u;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < nv) {
+                const int n = nb + j;
+                rp[(n % P.rsplit) + (int64_t)(n / P.rsplit) * P.rss] = to_op<OutT>(v[j]);
+            }
+    }
+}
 
 template <bool BF16>
 __global__ void __launch_bounds__(TTHREADS, 2)
@@ -301,38 +339,8 @@ __global__ void __launch_bounds__(TTHREADS, 2)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] *= P.alpha;
                 }
-                if (P.row) {
-                    OpT *rp = reinterpret_cast<OpT *>(P.row) + (int64_t)b * P.sr + (int64_t)m * P.ldr;
-                    if (P.vec_row && nv == 32) {
-                        OpT *dst = rp + (nb % P.rsplit) + (int64_t)(nb / P.rsplit) * P.rss;
-                        if constexpr (BF16) {
-#pragma unroll
-                            for (int j = 0; j < 32; j += 8) {
-                                __nv_bfloat162 h0 = __floats2bfloat162_rn(v[j], v[j + 1]);
-                                __nv_bfloat162 h1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
-                                __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
-                                __nv_bfloat162 h3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
-                                uint4 u;
-                                u.x = *reinterpret_cast<uint32_t *>(&h0);
-                                u.y = *reinterpret_cast<uint32_t *>(&h1);
-                                u.z = *reinterpret_cast<uint32_t *>(&h2);
-                                u.w = *reinterpret_cast<uint32_t *>(&h3);
-                                *reinterpret_cast<uint4 *>(dst + j) = u;
-                            }
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; j += 4)
-                                *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j < nv) {
-                                const int n = nb + j;
-                                rp[(n % P.rsplit) + (int64_t)(n / P.rsplit) * P.rss] = to_op<OpT>(v[j]);
-                            }
-                    }
-                }
+                if (P.row) store_row<OpT>(reinterpret_cast<OpT *>(P.row), P, b, m, nb, nv, v);
+                if (P.frow) store_row<float>(P.frow, P, b, m, nb, nv, v);
                 if (P.col) {
                     OpT *cp = reinterpret_cast<OpT *>(P.col) + (int64_t)b * P.sc + m;
 #pragma unroll
@@ -400,6 +408,27 @@ bool make_map(CUtensorMap *map, bool bf16, const GemmOperand &o, int K, int rows
 
 }  // namespace
 
+bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
+                       const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *estr, std::string *err) {
+    auto fn = encode_fn();
+    if (!fn) {
+        *err = "cuTensorMapEncodeTiled is not available from the driver";
+        return false;
+    }
+    if (reinterpret_cast<uintptr_t>(base) & 15) {
+        *err = "tensor map base is not 16-byte aligned";
+        return false;
+    }
+    const CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *err = "cuTensorMapEncodeTiled failed with status " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
 bool tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, int batch, float alpha, const GemmOperand &A,
              const GemmOperand &B, float beta, const GemmOutput &C, int *err_dev, std::string *err) {
     if (M <= 0 || N <= 0 || batch <= 0) return true;
@@ -428,10 +457,13 @@ bool tc_gemm(cudaStream_t st, bool bf16, int M, int N, int K, int batch, float a
     P.col = C.col;
     P.ldc = C.ldc;
     P.sc = C.sc;
-    P.vec_row = (C.row && (reinterpret_cast<uintptr_t>(C.row) & 15) == 0 && (C.ldr * es) % 16 == 0 &&
-                 (C.sr * es) % 16 == 0 && (C.rsplit <= 0 || (C.rsplit % 32 == 0 && (C.rss * es) % 16 == 0)))
-                    ? 1
-                    : 0;
+    P.frow = C.frow;
+    // 16-byte row stores need every row start 16-byte aligned in both copies
+    auto vec_ok = [&](const void *ptr, int64_t e) {
+        return !ptr || ((reinterpret_cast<uintptr_t>(ptr) & 15) == 0 && (C.ldr * e) % 16 == 0 && (C.sr * e) % 16 == 0 &&
+                        (C.rsplit <= 0 || (C.rsplit % 32 == 0 && (C.rss * e) % 16 == 0)));
+    };
+    P.vec_row = (vec_ok(C.row, es) && vec_ok(C.frow, 4)) ? 1 : 0;
     P.err = err_dev;
     const dim3 grid((unsigned)((M + TBM - 1) / TBM), (unsigned)((N + TBN - 1) / TBN), (unsigned)batch);
     // the shared-memory opt-in is a per-device attribute of each kernel

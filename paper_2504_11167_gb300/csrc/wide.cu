@@ -3,27 +3,42 @@
 //
 // Every partition A_i is cut into blocks of W = 64 ceil(k/64) >= k rows, so it
 // is block tridiagonal with W x W blocks; partitions are padded to NBW blocks
-// with identity rows.  The block operations are dense contractions of order
-// W (up to 1024), run as batched GEMMs over the p partitions (cuBLAS; FP64,
-// FP32, or TF32 tensor cores with FP32 accumulation for LRSPIKE_MIXED_TF32):
+// with identity rows.  The block operations are dense contractions of order W
+// (up to 1024), batched over the p partitions.  They run on the 5th-generation
+// tensor cores (tc_gemm.cu; TF32 operands, or BF16 operands for
+// LRSPIKE_MIXED_BF16, FP32 accumulation) or, in the FP64 and FP32 modes, as
+// SIMT GEMMs in the working precision (k_simt_gemm):
 //
 //   factor, block step J (all partitions at once):
-//     S_J = A_JJ - Y_{J-1} Z_{J-1};  S_J = L U with L^{-1}, U^{-1} by
-//     recursive halving (64 x 64 base blocks in k_lu_inv64);
+//     S_J = A_JJ - Y_{J-1} Z_{J-1};  S_J = L U with L^{-1}, U^{-1} by recursive
+//     halving (64 x 64 base blocks in k_lu_inv64);
 //     Z_J = L_JJ^{-1} A_{J,J+1} (= U_{J,J+1}),  Y_J = A_{J+1,J} U_JJ^{-1} (= L_{J+1,J})
 //   spikes [T_i | W_i] = A_i^{-1} [[0; B_i] | [C_i; 0]] (eq. 'Veqn') by the
 //     forward and backward block recurrences on a 2W-column panel
 //   compression: the randomized SVD the paper uses for wide bands (section
-//     3.1, Halko-Martinsson-Tropp proto-algorithm), on the right singular
-//     subspace through G = T^T T: Y = G Omega, power passes with
-//     re-orthonormalisation, Rayleigh-Ritz on Q^T G Q; u = T V_r, P = V_r^T
-//   D-stage and its transpose: the same block recurrences on nrhs columns.
+//     3.1, Halko-Martinsson-Tropp proto-algorithm) on each spike T:
+//       Y = T Omega;  Q = orth(Y);  q times: Y = T (T^T Q), Q = orth(Y);
+//       B^T = T^T Q;  B B^T = U_B diag(sigma^2) U_B^T (cyclic Jacobi);
+//       u = Q U_B,r,  P = U_B,r^T B = sigma_r V_r^T.
+//     orth() is shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto
+//     and Yanagisawa, 2020): three passes G = Y^T Y, G (+ s I) = R^T R,
+//     Y <- Y R^{-1}, the first with the shift s = 11 (m l + l(l+1)) u ||Y||_F^2;
+//     it spans the same subspace as the Householder QR of the oracle.
+//   D-stage and its transpose: one cluster of CTAs per partition walks both
+//     block recurrences (k_wide_dstage), reading only the nonzero triangles of
+//     the factor tiles.
 //
-// Layouts: column-major W x W tiles; factor tiles [p][NBW][W x W]; panels
-// [p][PS x cols] with PS = NBW W rows (leading dimension PS).
-#include <cublas_v2.h>
+// Layouts: W x W tiles [p][NBW][W x W]; panels [p][PS x cols] column-major with
+// PS = NBW W rows (leading dimension PS).  A matrix that is a left factor of a
+// tensor-core product is also kept row-major in the operand type, a right
+// factor column-major in the operand type (K-contiguous operands for the MMA);
+// the epilogue of the product that makes a matrix writes those copies.
+#include <cooperative_groups.h>
+#include <cuda.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -35,17 +50,180 @@ namespace lrs {
 
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int VP = 16;  // columns of the vector panels (max nrhs)
 
+// A batch of matrices in the layouts products read; element (a, b) of entry i:
+//   f    working precision, column-major  f[a + b ld + i s]
+//   fr   working precision, row-major     fr[b + a ldr + i sr]
+//   oc   operand type, column-major       oc[a + b ld + i s]
+//   orow operand type, row-major          orow[b + a ldr + i sr]
+// Absent layouts are NULL.  In TF32 mode the operand type is the working type
+// and oc / orow alias f / fr.
+struct WMat {
+    void *f = nullptr, *fr = nullptr, *oc = nullptr, *orow = nullptr;
+    int64_t ld = 0, s = 0, ldr = 0, sr = 0;
+};
+
+inline void *elem(void *base, int64_t e, size_t sz) {
+    return base ? static_cast<void *>(static_cast<char *>(base) + e * (int64_t)sz) : nullptr;
+}
+
+WMat view(const Ctx *c, const WMat &m, int64_t a0, int64_t b0) {
+    WMat v = m;
+    v.f = elem(m.f, a0 + b0 * m.ld, c->tsize);
+    v.oc = elem(m.oc, a0 + b0 * m.ld, c->osize);
+    v.fr = elem(m.fr, b0 + a0 * m.ldr, c->tsize);
+    v.orow = elem(m.orow, b0 + a0 * m.ldr, c->osize);
+    return v;
+}
+
+WMat square(void *const (&arr)[4], int64_t W, int64_t stride) {
+    WMat m;
+    m.f = arr[0];
+    m.fr = arr[1];
+    m.oc = arr[2];
+    m.orow = arr[3];
+    m.ld = m.ldr = W;
+    m.s = m.sr = stride;
+    return m;
+}
+
 // ---------------------------------------------------------------------------
-// A_JJ (S), A_{J,J+1} (B), A_{J+1,J} (C) of every partition, W x W column-major.
-// One CTA per 32 x 32 tile: it reads the tile along band diagonals (consecutive
-// columns are consecutive band addresses) and writes it column by column.
+// SIMT GEMM (FP64 / FP32 modes):  C = alpha A' B'^T + beta C over the batch,
+// A'(m, k) = A[m am + k ak + b as], B'(n, k) = B[n bn + k bk + b bs];
+// C column-major (ldc, sc) and optionally a row-major copy Cr (ldr, sr).
+// 64 x 64 tile per CTA, 16-deep K slabs in shared memory, 4 x 4 per thread.
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_wide_gather(const double *__restrict__ band, int64_t ld, int k, Parts P, int W, int J, T *__restrict__ S,
-                  T *__restrict__ B, T *__restrict__ C) {
-    __shared__ T tile[32][33];
+    k_simt_gemm(int M, int N, int K, T alpha, T beta, const T *__restrict__ A, int64_t am, int64_t ak, int64_t as,
+                const T *__restrict__ B, int64_t bn, int64_t bk, int64_t bs, T *C, int64_t ldc, int64_t sc,
+                T *Cr, int64_t ldr, int64_t sr) {
+    __shared__ T As[16][65], Bs[16][65];
+    const int b = blockIdx.z, m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    A += b * as;
+    B += b * bs;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const bool a1 = (ak == 1), b1 = (bk == 1);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 1024; e += 256) {
+            int kk = a1 ? (e & 15) : (e >> 6), mm = a1 ? (e >> 4) : (e & 63);
+            int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? A[gm * am + gk * ak] : T(0);
+            kk = b1 ? (e & 15) : (e >> 6);
+            const int nn = b1 ? (e >> 4) : (e & 63);
+            const int gn = n0 + nn;
+            gk = k0 + kk;
+            Bs[kk][nn] = (gn < N && gk < K) ? B[gn * bn + gk * bk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + tx + 16 * i, n = n0 + ty + 16 * j;
+            if (m < M && n < N) {
+                T v = alpha * acc[i][j];
+                const int64_t ci = (int64_t)b * sc + m + (int64_t)n * ldc;
+                if (beta != T(0)) v = fma(beta, C[ci], v);
+                if (C) C[ci] = v;
+                if (Cr) Cr[(int64_t)b * sr + n + (int64_t)m * ldr] = v;
+            }
+        }
+}
+
+// C = alpha op(X) op(Y) + beta C over the batch; op(X) is M x K, op(Y) K x N.
+// rsplit / rss: the row-major operand copy of C splits its columns into
+// blocks of rsplit placed rss apart (0 = no split).
+bool gemm(Ctx *c, int M, int N, int K, double alpha, const WMat &X, bool tx, const WMat &Y, bool ty, double beta,
+          const WMat &C, int batch, int rsplit = 0, int64_t rss = 0) {
+    if (M <= 0 || N <= 0 || batch <= 0) return true;
+    if (c->gpath == 0) {
+        const int64_t am = tx ? X.ld : 1, ak = tx ? 1 : X.ld;
+        const int64_t bn = ty ? 1 : Y.ld, bk = ty ? Y.ld : 1;
+        const dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)batch);
+        return launch(c, KID_WIDE_GEMM, [&] {
+            if (c->fp64)
+                k_simt_gemm<double><<<grid, 256, 0, c->stream>>>(
+                    M, N, K, alpha, beta, (const double *)X.f, am, ak, X.s, (const double *)Y.f, bn, bk, Y.s,
+                    (double *)C.f, C.ld, C.s, (double *)C.fr, C.ldr, C.sr);
+            else
+                k_simt_gemm<float><<<grid, 256, 0, c->stream>>>(
+                    M, N, K, (float)alpha, (float)beta, (const float *)X.f, am, ak, X.s, (const float *)Y.f, bn, bk,
+                    Y.s, (float *)C.f, C.ld, C.s, (float *)C.fr, C.ldr, C.sr);
+        });
+    }
+    GemmOperand A, B;
+    if (!tx) A = {X.orow, X.ldr, X.sr};
+    else A = {X.oc, X.ld, X.s};
+    if (!ty) B = {Y.oc, Y.ld, Y.s};
+    else B = {Y.orow, Y.ldr, Y.sr};
+    if (!A.p || !B.p) {
+        c->err = "wide-band product: an operand layout is missing";
+        return false;
+    }
+    GemmOutput o;
+    o.f = static_cast<float *>(C.f);
+    o.ldf = C.ld;
+    o.sf = C.s;
+    o.row = C.orow;
+    o.ldr = C.ldr;
+    o.sr = C.sr;
+    o.rsplit = rsplit;
+    o.rss = rss;
+    o.col = (C.oc != C.f) ? C.oc : nullptr;
+    o.ldc = C.ld;
+    o.sc = C.s;
+    o.frow = (C.fr != C.orow) ? static_cast<float *>(C.fr) : nullptr;
+    std::string err;
+    bool ok = true;
+    const bool launched = launch(c, KID_WIDE_TC, [&] {
+        ok = tc_gemm(c->stream, c->gpath == 2, M, N, K, batch, (float)alpha, A, B, (float)beta, o, c->gemm_err, &err);
+    });
+    if (!ok) {
+        c->err = err;
+        return false;
+    }
+    return launched;
+}
+
+// ---------------------------------------------------------------------------
+template <typename O>
+__device__ __forceinline__ O cvtd(double v) {
+    if constexpr (sizeof(O) == 2) return __float2bfloat16_rn((float)v);
+    else return (O)v;
+}
+
+// A_JJ (S), A_{J,J+1} (B), A_{J+1,J} (C) of every partition, W x W, in the
+// layouts their products read (null pointers are skipped).  One CTA per
+// 32 x 32 tile: it reads the tile along band diagonals (consecutive columns
+// are consecutive band addresses) and writes it column by column (column-major
+// layouts) and row by row (row-major layouts).
+template <typename T, typename O>
+__global__ void __launch_bounds__(256)
+    k_wide_gather(const double *__restrict__ band, int64_t ld, int k, Parts P, int W, int J, T *Sf, T *Sfr, O *Soc,
+                  O *Sor, T *Bf, O *Boc, T *Cf, O *Cor) {
+    __shared__ double tile[32][33];
     const int which = blockIdx.z % 3, part = blockIdx.z / 3;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int a0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
@@ -55,37 +233,70 @@ __global__ void __launch_bounds__(256)
         const int dd = e / 32 - 31, b = e % 32, a = b + dd;
         if (a < 0 || a >= 32) continue;
         const int64_t lr = rb + a0 + a, lc = cb + b0 + b;
-        T v = T(0);
+        double v = 0.0;
         if (lr < ni && lc < ni) {
             const int64_t d = k + lr - lc;
-            if (d >= 0 && d <= 2 * k) v = (T)band[d * ld + s + lc];
+            if (d >= 0 && d <= 2 * k) v = band[d * ld + s + lc];
         } else if (which == 0 && lr == lc) {
-            v = T(1);  // padding rows carry the identity
+            v = 1.0;  // padding rows carry the identity
         }
         tile[a][b] = v;
     }
     __syncthreads();
-    T *out = (which == 0 ? S : which == 1 ? B : C) + (int64_t)part * W * W;
+    const int64_t off = (int64_t)part * W * W;
+    T *f = which == 0 ? Sf : which == 1 ? Bf : Cf;
+    T *fr = which == 0 ? Sfr : nullptr;
+    O *oc = which == 0 ? Soc : which == 1 ? Boc : nullptr;
+    O *orow = which == 0 ? Sor : which == 2 ? Cor : nullptr;
     const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-    for (int b = ty; b < 32; b += 8) out[(int64_t)(b0 + b) * W + a0 + tx] = tile[tx][b];
+    for (int b = ty; b < 32; b += 8) {
+        const int64_t ci = off + (int64_t)(b0 + b) * W + a0 + tx;   // column-major: column b0+b, row a0+tx
+        const int64_t ri = off + (int64_t)(a0 + b) * W + b0 + tx;   // row-major: row a0+b, column b0+tx
+        if (f) f[ci] = (T)tile[tx][b];
+        if (oc) oc[ci] = cvtd<O>(tile[tx][b]);
+        if (fr) fr[ri] = (T)tile[b][tx];
+        if (orow) orow[ri] = cvtd<O>(tile[b][tx]);
+    }
+}
+
+// Layout copies of the n x n leading view of each partition's matrix (f,
+// leading dimension ld, stride s) into fr / oc / orow (nullable).
+template <typename T, typename O>
+__global__ void k_wide_layouts(const T *__restrict__ f, int n, int64_t ld, int64_t s, T *fr, O *oc, O *orow) {
+    const int part = blockIdx.y;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+        const int a = e % n, b = e / n;
+        const T v = f[(int64_t)part * s + a + (int64_t)b * ld];
+        if (oc) oc[(int64_t)part * s + a + (int64_t)b * ld] = cvtd<O>((double)v);
+        if (fr) fr[(int64_t)part * s + b + (int64_t)a * ld] = v;
+        if (orow) orow[(int64_t)part * s + b + (int64_t)a * ld] = cvtd<O>((double)v);
+    }
 }
 
 // Spike right-hand sides on the zeroed panel X [PS x 2W]: [0; B_i] in columns
-// 0..k-1 (rows n_i-k..n_i-1) and [C_i; 0] in columns W..W+k-1 (rows 0..k-1).
-template <typename T>
+// 0..k-1 (rows n_i-k..n_i-1) and [C_i; 0] in columns W..W+k-1 (rows 0..k-1);
+// Xc (nullable) is the operand-type copy.
+template <typename T, typename O>
 __global__ void k_wide_spike_rhs(const double *__restrict__ band, int64_t ld, int k, Parts P, int W, int64_t PS,
-                                 T *__restrict__ X) {
+                                 T *__restrict__ X, O *Xc) {
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
-    T *x = X + (int64_t)part * PS * 2 * W;
+    const int64_t base = (int64_t)part * PS * 2 * W;
     for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) {
         const int a = (int)(e % k), b = (int)(e / k);
         if (part < P.p - 1) {  // B_i[a][b] = A[s+n_i-k+a][s+n_i+b], nonzero for b <= a
             const int64_t sn = s + ni;
-            x[(int64_t)b * PS + ni - k + a] = (b <= a) ? (T)band[(int64_t)(a - b) * ld + sn + b] : T(0);
+            const double v = (b <= a) ? band[(int64_t)(a - b) * ld + sn + b] : 0.0;
+            const int64_t xi = base + (int64_t)b * PS + ni - k + a;
+            X[xi] = (T)v;
+            if (Xc) Xc[xi] = cvtd<O>(v);
         }
-        if (part > 0)  // C_i[a][b] = A[s+a][s-k+b], nonzero for a <= b
-            x[(int64_t)(W + b) * PS + a] = (a <= b) ? (T)band[(int64_t)(2 * k + a - b) * ld + s - k + b] : T(0);
+        if (part > 0) {  // C_i[a][b] = A[s+a][s-k+b], nonzero for a <= b
+            const double v = (a <= b) ? band[(int64_t)(2 * k + a - b) * ld + s - k + b] : 0.0;
+            const int64_t xi = base + (int64_t)(W + b) * PS + a;
+            X[xi] = (T)v;
+            if (Xc) Xc[xi] = cvtd<O>(v);
+        }
     }
 }
 
@@ -100,8 +311,8 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
 // Gaussian sketches Omega_b (W x lp, column-major), b = 2 i + side: entry
 // (a, j), a < k, j < ell, is the Box-Muller normal of SplitMix64 outputs 2c,
 // 2c+1 at c = a ell + j with seed + b; zero elsewhere.
-template <typename T>
-__global__ void k_wide_sketch(T *__restrict__ Om, int W, int k, int ell, int lp, unsigned long long seed,
+template <typename O>
+__global__ void k_wide_sketch(O *__restrict__ Om, int W, int k, int ell, int lp, unsigned long long seed,
                               int nmat) {
     const int64_t per = (int64_t)W * lp, total = per * nmat;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -109,14 +320,14 @@ __global__ void k_wide_sketch(T *__restrict__ Om, int W, int k, int ell, int lp,
         const int b = (int)(e / per);
         const int64_t rem = e % per;
         const int j = (int)(rem / W), a = (int)(rem % W);
-        T v = T(0);
+        double v = 0.0;
         if (a < k && j < ell) {
             const unsigned long long cidx = (unsigned long long)a * ell + j, sd = seed + (unsigned long long)b;
             const double u1 = ((double)(splitmix64(sd, 2 * cidx) >> 11) + 0.5) * 0x1p-53;
             const double u2 = (double)(splitmix64(sd, 2 * cidx + 1) >> 11) * 0x1p-53;
-            v = (T)(sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2));
+            v = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
         }
-        Om[e] = v;
+        Om[e] = cvtd<O>(v);
     }
 }
 
@@ -127,16 +338,115 @@ __global__ void k_to_f64(const T *__restrict__ in, double *__restrict__ out, int
         out[e] = (double)in[e];
 }
 
-// Columns c of E_b (lp x lp, column-major) scaled by 1 / sigma_{b,c} (0 where sigma is 0).
+template <typename T, typename O>
+__global__ void k_to_op(const T *__restrict__ in, O *__restrict__ out, int64_t count) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = cvtd<O>((double)in[e]);
+}
+
+// One CholeskyQR pass on the n x n leading block of each Gram matrix G_b
+// (FP64, lp x lp column-major): G (+ s I) = R^T R by right-looking Cholesky,
+// then R^{-1} (upper triangular, in place, column by column) written as
+// Rinv_b (working precision, lp x lp column-major, zero outside).  The shift
+// (shifted = 1) is s = 11 (rows n + n (n+1)) u trace(G).  A pivot at or below
+// n u max_j G_jj (after the shift) marks a direction that the columns already
+// span: its row of R is set to the unit row and its row and column of R^{-1}
+// to zero, so that column of Q = Y R^{-1} is zero and no other column uses it.
 template <typename T>
-__global__ void k_scale_cols(T *__restrict__ E, const double *__restrict__ sg, int lp, int nmat) {
-    const int64_t total = (int64_t)nmat * lp * lp;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = e / ((int64_t)lp * lp);
-        const int c = (int)((e % ((int64_t)lp * lp)) / lp);
-        const double sv = sg[b * lp + c];
-        E[e] = (sv > 0.0) ? (T)((double)E[e] / sv) : T(0);
+__global__ void __launch_bounds__(256)
+    k_chol_inv(const double *__restrict__ G, int lp, int n, int64_t rows, double u, int shifted, T *__restrict__ Rinv) {
+    extern __shared__ double csm[];
+    const int LD = n + 1;
+    double *A = csm, *tmp = A + n * LD;
+    __shared__ int dropped[128];
+    __shared__ double s_shift, s_maxd;
+    const int b = blockIdx.x;
+    const double *g = G + (int64_t)b * lp * lp;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e % n, j = e / n;
+        A[i * LD + j] = g[i + (int64_t)j * lp];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < n; ++i) tr += A[i * LD + i];
+        s_shift = shifted ? 11.0 * ((double)rows * n + (double)n * (n + 1)) * u * tr : 0.0;
+        double md = 0.0;
+        for (int i = 0; i < n; ++i) md = fmax(md, A[i * LD + i] + s_shift);
+        s_maxd = md;
+    }
+    __syncthreads();
+    if (threadIdx.x < n) A[threadIdx.x * LD + threadIdx.x] += s_shift;
+    __syncthreads();
+    const double tol = (double)n * u * s_maxd;
+    for (int j = 0; j < n; ++j) {
+        const double d = A[j * LD + j];
+        const bool drop = !(d > tol);
+        const double piv = drop ? 0.0 : sqrt(d);
+        __syncthreads();
+        for (int jj = j + 1 + threadIdx.x; jj < n; jj += blockDim.x) A[j * LD + jj] = drop ? 0.0 : A[j * LD + jj] / piv;
+        if (threadIdx.x == 0) {
+            A[j * LD + j] = drop ? 1.0 : piv;
+            dropped[j] = drop;
+        }
+        __syncthreads();
+        const int m = n - j - 1;  // trailing (i, i2), j < i <= i2
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = j + 1 + e / m, i2 = j + 1 + e % m;
+            if (i <= i2) A[i * LD + i2] -= A[j * LD + i] * A[j * LD + i2];
+        }
+        __syncthreads();
+    }
+    // R^{-1} in place: column j from the finished leading block
+    for (int j = 0; j < n; ++j) {
+        const double rjj = A[j * LD + j];
+        for (int i = threadIdx.x; i < j; i += blockDim.x) tmp[i] = A[i * LD + j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            double acc = 0.0;
+            for (int l = i; l < j; ++l) acc += A[i * LD + l] * tmp[l];
+            A[i * LD + j] = dropped[j] ? 0.0 : -acc / rjj;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) A[j * LD + j] = dropped[j] ? 0.0 : 1.0 / rjj;
+        __syncthreads();
+    }
+    T *out = Rinv + (int64_t)b * lp * lp;
+    for (int e = threadIdx.x; e < lp * lp; e += blockDim.x) {
+        const int i = e % lp, j = e / lp;
+        out[e] = (i < n && j < n && i <= j) ? (T)A[i * LD + j] : T(0);
+    }
+}
+
+// u-factors: Ucat[(s_i + row) 2r + side r + j] = sum_q Q_b[row, q] E_b[j, q]
+// (b = 2 i + side, rows < n_i), E_b the leading eigenvectors (r x lp).
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_wide_u(const T *__restrict__ Q, int64_t PS, int lp, const T *__restrict__ E, int r, Parts P, T *__restrict__ Ucat) {
+    extern __shared__ __align__(16) unsigned char usm[];
+    T *Es = reinterpret_cast<T *>(usm);  // r x lp
+    const int b = blockIdx.y, part = b / 2, side = b % 2;
+    for (int e = threadIdx.x; e < r * lp; e += blockDim.x) Es[e] = E[(int64_t)b * r * lp + e];
+    __syncthreads();
+    const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (row >= ni) return;
+    const T *q = Q + (int64_t)b * PS * lp + row;
+    T *out = Ucat + (s + row) * 2 * r + side * r;
+    for (int j0 = 0; j0 < r; j0 += 16) {
+        T acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = T(0);
+        for (int l = 0; l < lp; ++l) {
+            const T qv = q[(int64_t)l * PS];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j0 + j < r) acc[j] = fma(qv, Es[(j0 + j) * lp + l], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j0 + j < r) out[j0 + j] = acc[j];
     }
 }
 
@@ -242,217 +552,730 @@ __global__ void k_nonzero_diags(const double *__restrict__ band, int64_t ld, int
 }
 
 // ---------------------------------------------------------------------------
-inline char *at(void *base, int64_t elems, int tsz) { return static_cast<char *>(base) + elems * tsz; }
+// D-stage (and its transpose) of the wide-band factors: one cluster of CS
+// CTAs per partition walks the forward and the backward block recurrence
+//   forward  t = b_J - Lo_{J-1} y_{J-1},  y_J = D_J t
+//   backward t = y_J - Up_J x_{J+1},      x_J = E_J t
+// (A: Lo = L_{J,J-1}, D = L_JJ^{-1}, Up = U_{J,J+1}, E = U_JJ^{-1};
+//  A^T: Lo = U_{J-1,J}^T, D = U_JJ^{-T}, Up = L_{J+1,J}^T, E = L_JJ^{-T}).
+// Every product is a set of dot products of "lines" of a factor tile with the
+// gathered vector: rows of the row-major tiles (A) or columns of the
+// column-major tiles (A^T), both contiguous in memory.  Line a of Lo and E
+// holds its nonzeros in [a, W) ("tail"), of D and Up in [0, a] ("head").
+//
+// CTA c of a cluster owns lines a = c + CS t, sixteen at a time (a group).  A
+// 4-D tensor map views each tile kind as [tile][t][phase c][column], so one
+// TMA load (cp.async.bulk.tensor) brings a box of a group's 16 lines x
+// DS_BC columns (16 KB) into a shared-memory slot; only the boxes that meet
+// the group's nonzero columns are loaded (the rest of the triangle is never
+// read; zeros inside a loaded box are multiplied as they are).  Warp 16
+// (producer) streams the boxes of every product in order into a ring of
+// slots, completion counted on the slot's mbarrier, running ahead of the
+// consumers across products (the tiles do not depend on the vectors).  Warps
+// 0..15 (consumers) take (group, quarter) items in turn and their boxes in
+// order (the four quarters of a box free its slot together): per box and
+// quarter of the group (four lines), lanes over 4-entry pieces, the four lines
+// at once so each vector entry read from shared memory serves four lines, and
+// a butterfly reduce-scatter at the end.
+// After each product the CTAs exchange their slices of the result through
+// distributed shared memory (double-buffered, one cluster barrier per
+// product).  Input b in V1, y in V2, result x in V1 (panel column c at c PS).
+// Waits on the ring are bounded; one that runs out sets *err and the CTA
+// keeps walking the barrier sequence without computing, so the cluster ends.
+constexpr int DS_CONSUMERS = 16;
+constexpr int DS_THREADS = 32 * (DS_CONSUMERS + 1);
+constexpr int DS_GL = 16;  // lines per group (one TMA box)
+constexpr long long kDsSpin = 1ll << 26;
 
-bool gemm(Ctx *c, bool ta, bool tb, int m, int n, int kk, double alpha, const void *A, int lda, int64_t sA,
-          const void *B, int ldb, int64_t sB, double beta, void *C, int ldc, int64_t sC, int batch) {
-    cublasHandle_t h = static_cast<cublasHandle_t>(c->blas);
-    const cudaDataType dt = c->fp64 ? CUDA_R_64F : CUDA_R_32F;
-    const cublasComputeType_t ct = c->fp64 ? CUBLAS_COMPUTE_64F
-                                   : (c->opt.precision == LRSPIKE_MIXED_TF32) ? CUBLAS_COMPUTE_32F_FAST_TF32
-                                                                               : CUBLAS_COMPUTE_32F;
-    const float af = (float)alpha, bf = (float)beta;
-    const void *pa = c->fp64 ? static_cast<const void *>(&alpha) : static_cast<const void *>(&af);
-    const void *pb = c->fp64 ? static_cast<const void *>(&beta) : static_cast<const void *>(&bf);
-    cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
-    const bool ok = launch(c, KID_WIDE_GEMM, [&] {
-        st = cublasGemmStridedBatchedEx(h, ta ? CUBLAS_OP_T : CUBLAS_OP_N, tb ? CUBLAS_OP_T : CUBLAS_OP_N, m, n, kk,
-                                        pa, A, dt, lda, sA, B, dt, ldb, sB, pb, C, dt, ldc, sC, batch, ct,
-                                        CUBLAS_GEMM_DEFAULT);
+__device__ __forceinline__ uint32_t ds_smem(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool ds_wait(uint64_t *bar, uint32_t parity) {
+    for (long long i = 0; i < kDsSpin; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(ds_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (i >= 64) __nanosleep(32);
+    }
+    return false;
+}
+template <typename T>
+struct V4 {
+    T x, y, z, w;
+};
+// four consecutive shared-memory values (16-byte aligned), one vector load
+template <typename T>
+__device__ __forceinline__ V4<T> lds4(const T *p) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        return {v.x, v.y, v.z, v.w};
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        return {a.x, a.y, b.x, b.y};
+    }
+}
+// Butterfly reduce-scatter of N values (N a power of two, 4 <= N <= 16) over
+// the 32 lanes: at step o = 16, 8, .. each lane keeps the half of its values
+// selected by bit o of its lane and adds the partner's copy of that half;
+// N - 1 + log2(32 / N) shuffles leave in v[0] the warp sum of the value index
+// returned, in every lane.
+template <typename T, int N>
+__device__ __forceinline__ int butterfly_reduce(T (&v)[N], int lane) {
+    int j = 0;
+#pragma unroll
+    for (int half = N / 2, o = 16; half >= 1; half /= 2, o /= 2) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            const T keep = up ? v[q + half] : v[q];
+            const T send = up ? v[q] : v[q + half];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        if (up) j += half;
+    }
+#pragma unroll
+    for (int o = 32 / N / 2; o >= 1; o /= 2) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    return j;
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"r"(32 * DS_CONSUMERS) : "memory"); }
+
+// Product k of the 4 NB products: forward J = k/2 (sub 0: Lo_{J-1}, sub 1:
+// D_J), backward J = NB-1-(k-2NB)/2 (sub 0: Up_J, sub 1: E_J).  Products 0
+// and 2NB read no tile (they copy b_0 and y_{NB-1}).  kind: 0 Lo, 1 D, 2 Up, 3 E.
+struct DsProduct {
+    int J, sub, kind, blk;
+    bool fwd, tile, head;
+};
+__device__ __forceinline__ DsProduct ds_product(int k, int NB) {
+    DsProduct d;
+    d.fwd = k < 2 * NB;
+    const int q = d.fwd ? k : k - 2 * NB;
+    d.sub = q & 1;
+    d.J = d.fwd ? q / 2 : NB - 1 - q / 2;
+    d.tile = !(q == 0);
+    d.head = d.fwd ? (d.sub == 1) : (d.sub == 0);
+    d.kind = d.fwd ? d.sub : 2 + d.sub;
+    d.blk = (d.fwd && d.sub == 0) ? d.J - 1 : d.J;
+    return d;
+}
+// first and one-past-last box column index of group g (boxes of BC columns)
+__device__ __forceinline__ void ds_boxes(bool head, int cr, int CS, int g, int W, int BC, int &b0, int &b1) {
+    if (head) {
+        b0 = 0;
+        b1 = (cr + CS * (DS_GL * g + DS_GL - 1)) / BC + 1;  // through the last line's diagonal
+    } else {
+        b0 = (cr + CS * (DS_GL * g)) / BC;
+        b1 = (W + BC - 1) / BC;
+    }
+}
+
+struct DsMaps {
+    CUtensorMap m[4];
+};
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(DS_THREADS, 1)
+    k_wide_dstage(const __grid_constant__ DsMaps maps, int W, int NB, int64_t PS, int c0, int S, int BC, T *V1,
+                  T *V2, int *err) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int CS = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+    const int part = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int owned = W / CS, G = owned / DS_GL, nprod = 4 * NB, nbc = (W + BC - 1) / BC;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(dsm), *empty = full + S;
+    // boxes the producer has posted (byte count on the slot's barrier): a
+    // consumer waits for its box to be posted before it waits on the slot's
+    // phase, so the parity it tests cannot belong to an older use of the slot
+    volatile long long *posted = reinterpret_cast<volatile long long *>(empty + S);
+    int *pre = reinterpret_cast<int *>(dsm + 2 * S * 8 + 8);  // box prefix per group: head G+1, tail G+1
+    // TMA box destinations: 128-byte aligned slots after the header
+    T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(dsm) + 2 * S * 8 + 8 + 8 * (G + 1) + 1023) &
+                                    ~(uintptr_t)1023);
+    T *vin = ring + (int64_t)S * DS_GL * BC;  // NR columns of W
+    T *slice0 = vin + (int64_t)W * NR, *slice1 = slice0 + (int64_t)owned * NR;
+    T *v1 = V1 + ((int64_t)part * VP + c0) * PS, *v2 = V2 + ((int64_t)part * VP + c0) * PS;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ds_smem(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(ds_smem(&empty[s])) : "memory");
+        }
+        *posted = 0;
+        for (int h = 0; h < 2; ++h) {
+            int acc = 0;
+            for (int g = 0; g < G; ++g) {
+                pre[h * (G + 1) + g] = acc;
+                int b0, b1;
+                ds_boxes(h == 0, cr, CS, g, W, BC, b0, b1);
+                acc += b1 - b0;
+            }
+            pre[h * (G + 1) + G] = acc;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    (void)nbc;
+
+    if (warp == DS_CONSUMERS) {
+        // producer (lane 0): the boxes of every product in order, then the
+        // product's barrier (whole warp)
+        bool ok = true;
+        int64_t seq = 0;
+        for (int k = 0; k < nprod; ++k) {
+            const DsProduct d = ds_product(k, NB);
+            if (d.tile && lane == 0) {
+                const CUtensorMap *map = &maps.m[d.kind];
+                const int tix = part * NB + d.blk;
+                for (int g = 0; g < G; ++g) {
+                    int b0, b1;
+                    ds_boxes(d.head, cr, CS, g, W, BC, b0, b1);
+                    for (int bx = b0; bx < b1; ++bx, ++seq) {
+                        if (!ok) continue;
+                        const int slot = (int)(seq % S);
+                        const uint32_t par = (uint32_t)((seq / S) & 1);
+                        if (!ds_wait(&empty[slot], par ^ 1u)) {
+                            ok = false;
+                            atomicExch(err, 1);
+                            continue;
+                        }
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                         ds_smem(&full[slot])),
+                                     "r"((uint32_t)(DS_GL * BC * sizeof(T)))
+                                     : "memory");
+                        asm volatile(
+                            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                            "[%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(ds_smem(ring + (int64_t)slot * DS_GL * BC)),
+                            "l"(reinterpret_cast<uint64_t>(map)), "r"(ds_smem(&full[slot])), "r"(bx * BC), "r"(cr),
+                            "r"(DS_GL * g), "r"(tix)
+                            : "memory");
+                        __threadfence_block();
+                        *posted = seq + 1;
+                    }
+                }
+            }
+            __syncwarp();
+            if (k > 0) cluster_wait();
+            cluster_arrive();
+        }
+        // every copy issued has landed before the CTA may leave (bounded)
+        if (lane == 0)
+            for (int64_t q = (seq > S ? seq - S : 0); q < seq; ++q) ds_wait(&full[q % S], (uint32_t)((q / S) & 1));
+        __syncwarp();
+        cluster_wait();
+        return;
+    }
+
+    // consumers
+    bool ok = true;
+    int64_t base = 0;  // sequence number of the first box of this product
+    for (int k = 0; k < nprod; ++k) {
+        const DsProduct d = ds_product(k, NB);
+        T *sl = (k & 1) ? slice1 : slice0;
+        const int64_t rowJ = (int64_t)d.J * W;
+        if (!d.tile) {
+            const T *src = d.fwd ? v1 : v2;
+            for (int e = threadIdx.x; e < owned * NR; e += 32 * DS_CONSUMERS) {
+                const int t = e / NR, c = e % NR;
+                sl[e] = src[(int64_t)c * PS + rowJ + cr + CS * t];
+            }
+        } else {
+            const int *pf = pre + (d.head ? 0 : G + 1);
+            const T *bsrc = (d.sub == 0) ? (d.fwd ? v1 : v2) + rowJ : nullptr;
+            T *gout = (d.sub == 1) ? (d.fwd ? v2 : v1) + rowJ : nullptr;
+            // work items (group g, quarter q = four of its lines), round-robin
+            // over the warps; the four quarters of a box free its slot together
+            for (int item = warp; item < 4 * G; item += DS_CONSUMERS) {
+                const int g = item >> 2, q = item & 3;
+                int b0, b1;
+                ds_boxes(d.head, cr, CS, g, W, BC, b0, b1);
+                T acc[4 * NR];
+#pragma unroll
+                for (int j = 0; j < 4 * NR; ++j) acc[j] = T(0);
+                int64_t s = base + pf[g];
+                for (int bx = b0; bx < b1; ++bx, ++s) {
+                    const int slot = (int)(s % S);
+                    const uint32_t par = (uint32_t)((s / S) & 1);
+                    bool ready = ok;
+                    if (ready && lane == 0) {
+                        long long i = 0;
+                        while (*posted <= s && i < kDsSpin)
+                            if (++i >= 64) __nanosleep(32);
+                        ready = *posted > s;
+                        __threadfence_block();
+                    }
+                    ready = __shfl_sync(0xffffffffu, ready ? 1 : 0, 0) != 0;
+                    ready = ready && ds_wait(&full[slot], par);
+                    ready = __all_sync(0xffffffffu, ready);
+                    if (!ready) {
+                        if (ok && lane == 0) atomicExch(err, 1);
+                        ok = false;
+                        continue;
+                    }
+                    const T *buf = ring + (int64_t)slot * DS_GL * BC + (int64_t)(4 * q) * BC;
+                    const int col0 = bx * BC, len = min(BC, W - col0);
+                    for (int e = 4 * lane; e < len; e += 128) {
+                        V4<T> v[NR];
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) v[c] = lds4(vin + (int64_t)c * W + col0 + e);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const V4<T> m = lds4(buf + i * BC + e);
+#pragma unroll
+                            for (int c = 0; c < NR; ++c) {
+                                T t = acc[i * NR + c];
+                                t = fma(m.x, v[c].x, t);
+                                t = fma(m.y, v[c].y, t);
+                                t = fma(m.z, v[c].z, t);
+                                t = fma(m.w, v[c].w, t);
+                                acc[i * NR + c] = t;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ds_smem(&empty[slot]))
+                                     : "memory");
+                }
+                // reduce-scatter of the 4 NR sums over the warp
+                const int j = butterfly_reduce<T, 4 * NR>(acc, lane);
+                if ((lane & (32 / (4 * NR) - 1)) == 0) {
+                    const int i = j / NR, c = j % NR;
+                    const int t = DS_GL * g + 4 * q + i, ai = cr + CS * t;
+                    T val = acc[0];
+                    if (bsrc) val = bsrc[(int64_t)c * PS + ai] - val;
+                    sl[t * NR + c] = val;
+                    if (gout) gout[(int64_t)c * PS + ai] = val;
+                }
+            }
+            base += pf[G];
+        }
+        // exchange: every CTA's slice of this product into vin (line a = r' + CS t)
+        cluster_arrive();
+        cluster_wait();
+        if (k + 1 < nprod) {
+            constexpr int U = 4;
+            for (int a0 = threadIdx.x; a0 < W; a0 += U * 32 * DS_CONSUMERS) {
+                T buf[U][NR];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int a = a0 + u * 32 * DS_CONSUMERS;
+                    if (a < W) {
+                        const T *remote = cl.map_shared_rank(sl, a % CS) + (a / CS) * NR;
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) buf[u][c] = remote[c];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int a = a0 + u * 32 * DS_CONSUMERS;
+                    if (a < W)
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) vin[(int64_t)c * W + a] = buf[u][c];
+                }
+            }
+            consumers_sync();
+        }
+    }
+}
+
+template <typename T, int NR>
+size_t dstage_smem(int W, int cs, int S, int BC) {
+    const int G = W / cs / DS_GL;
+    // header, alignment of the ring to 1024 bytes, ring, vector, two slices
+    return (2 * (size_t)S * 8 + 8 + 8 * (G + 1)) + 1024 + (size_t)S * DS_GL * BC * sizeof(T) +
+           (size_t)W * NR * sizeof(T) + 2 * (size_t)(W / cs) * NR * sizeof(T);
+}
+
+// Cluster size: the largest CS <= 8 (16-line groups) for which all p
+// clusters are resident at once; otherwise the one that keeps the most CTAs
+// resident.
+template <typename T, int NR>
+int dstage_cluster(Ctx *c, int S, int BC) {
+    int best = 0, fallback = 0;
+    int64_t fallback_ctas = 0;
+    for (int cs = 1; cs <= 8; cs *= 2) {
+        if (c->W % (DS_GL * cs)) break;
+        const size_t smem = dstage_smem<T, NR>(c->W, cs, S, BC);
+        if (smem > (227u << 10)) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cs, (unsigned)c->p, 1);
+        cfg.blockDim = dim3(DS_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, k_wide_dstage<T, NR>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (active >= c->p) best = cs;
+        if (active > 0 && (int64_t)std::min(active, c->p) * cs > fallback_ctas) {
+            fallback_ctas = (int64_t)std::min(active, c->p) * cs;
+            fallback = cs;
+        }
+    }
+    return best ? best : fallback;
+}
+
+// 4-D view of a tile kind for the D-stage's boxes: [tile][t][phase][column]
+// with line a = phase + CS t; box 16 lines (t) x BC columns.
+bool dstage_map(CUtensorMap *map, const void *base, bool fp64, int W, int CS, int64_t ntiles, int BC,
+                std::string *err) {
+    const int64_t es = fp64 ? 8 : 4;
+    cuuint64_t dims[4] = {(cuuint64_t)W, (cuuint64_t)CS, (cuuint64_t)(W / CS), (cuuint64_t)ntiles};
+    cuuint64_t strides[3] = {(cuuint64_t)(W * es), (cuuint64_t)(CS * W * es), (cuuint64_t)((int64_t)W * W * es)};
+    cuuint32_t box[4] = {(cuuint32_t)BC, 1u, (cuuint32_t)DS_GL, 1u};
+    cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    return encode_tensor_map(map, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base,
+                             dims, strides, box, estr, err);
+}
+
+template <typename T, int NR>
+bool launch_dstage(Ctx *c, bool trans, int c0) {
+    const int W = c->W;
+    const int BC = std::min(W, (int)(1024 / sizeof(T)));  // box columns: at most 1 KB per line
+    // A: row-major tiles (lines = rows); A^T: column-major tiles (lines = columns)
+    void *const *src = trans ? c->WF : c->WFr;
+    const void *kinds[4] = {trans ? src[2] : src[3],   // Lo: U_{J-1,J}^T / L_{J,J-1}
+                            trans ? src[1] : src[0],   // D: U_JJ^{-T} / L_JJ^{-1}
+                            trans ? src[3] : src[2],   // Up: L_{J+1,J}^T / U_{J,J+1}
+                            trans ? src[0] : src[1]};  // E: L_JJ^{-T} / U_JJ^{-1}
+    const int S = (int)std::min<size_t>(16, (160u << 10) / ((size_t)DS_GL * BC * sizeof(T)));  // ring slots
+    cudaFuncSetAttribute(k_wide_dstage<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10);
+    const int CS = dstage_cluster<T, NR>(c, S, BC);
+    if (CS == 0) {
+        c->err = "no cluster shape of the wide D-stage fits on this GPU";
+        return false;
+    }
+    DsMaps maps;
+    for (int q = 0; q < 4; ++q)
+        if (!dstage_map(&maps.m[q], kinds[q], sizeof(T) == 8, W, CS, (int64_t)c->p * c->NBW, BC, &c->err))
+            return false;
+    const size_t smem = dstage_smem<T, NR>(W, CS, S, BC);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)CS, (unsigned)c->p, 1);
+    cfg.blockDim = dim3(DS_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    c->dcs = CS;
+    cudaError_t e = cudaSuccess;
+    const bool ok = launch(c, KID_WIDE_DSTAGE, [&] {
+        e = cudaLaunchKernelEx(&cfg, k_wide_dstage<T, NR>, maps, W, c->NBW, c->PS, c0, S, BC, (T *)c->WV1,
+                               (T *)c->WV2, c->gemm_err);
     });
-    if (st != CUBLAS_STATUS_SUCCESS) {
-        c->err = "cuBLAS batched GEMM failed with status " + std::to_string((int)st);
+    if (e != cudaSuccess) {
+        c->err = std::string("cluster launch of the wide D-stage failed: ") + cudaGetErrorString(e);
         return false;
     }
     return ok;
 }
 
-// In-place recursive LU with both inverses of the n x n leading view of A
-// (column-major, leading dimension W, one matrix per partition at stride sA):
-// Li = L^{-1}, Ui = U^{-1} (views at stride sO), Tm is workspace (stride sT).
-// Halves: A11 = L11 U11; U12 = L11^{-1} A12; L21 = A21 U11^{-1};
-// A22 -= L21 U12 = L22 U22; (L^{-1})_21 = -L22^{-1} L21 L11^{-1},
-// (U^{-1})_12 = -U11^{-1} U12 U22^{-1}.  The zero triangles of Li, Ui must be
-// zero on entry.
-bool luinv(Ctx *c, void *A, void *Li, void *Ui, void *Tm, int n, int64_t sA, int64_t sO, int64_t sT, int64_t row0) {
-    const int W = c->W, tz = c->tsize, p = c->p;
-    if (n == 64) return run_lu_inv64(c, A, W, sA, Li, Ui, W, sO, row0);
-    const int h = n / 2;
-    auto q12 = [&](void *b) { return at(b, (int64_t)h * W, tz); };
-    auto q21 = [&](void *b) { return at(b, h, tz); };
-    auto q22 = [&](void *b) { return at(b, (int64_t)h * W + h, tz); };
-    if (!luinv(c, A, Li, Ui, Tm, h, sA, sO, sT, row0)) return false;
-    return gemm(c, false, false, h, h, h, 1.0, Li, W, sO, q12(A), W, sA, 0.0, q12(Tm), W, sT, p) &&      // U12
-           gemm(c, false, false, h, h, h, 1.0, q21(A), W, sA, Ui, W, sO, 0.0, q21(Tm), W, sT, p) &&      // L21
-           gemm(c, false, false, h, h, h, -1.0, q21(Tm), W, sT, q12(Tm), W, sT, 1.0, q22(A), W, sA, p) &&  // A22 -= L21 U12
-           luinv(c, q22(A), q22(Li), q22(Ui), q22(Tm), h, sA, sO, sT, row0 + h) &&
-           gemm(c, false, false, h, h, h, 1.0, q21(Tm), W, sT, Li, W, sO, 0.0, q21(A), W, sA, p) &&      // L21 L11^{-1}
-           gemm(c, false, false, h, h, h, -1.0, q22(Li), W, sO, q21(A), W, sA, 0.0, q21(Li), W, sO, p) &&
-           gemm(c, false, false, h, h, h, 1.0, q12(Tm), W, sT, q22(Ui), W, sO, 0.0, q12(A), W, sA, p) &&  // U12 U22^{-1}
-           gemm(c, false, false, h, h, h, -1.0, Ui, W, sO, q12(A), W, sA, 0.0, q12(Ui), W, sO, p);
+template <typename T>
+bool run_dstage_chain(Ctx *c, int nrhs, bool trans) {
+    for (int c0 = 0; c0 < nrhs; c0 += 4) {
+        // three columns run as four: the fourth panel column is independent of
+        // the others and never read back
+        const int nc = std::min(4, nrhs - c0);
+        const bool ok = nc == 1   ? launch_dstage<T, 1>(c, trans, c0)
+                        : nc == 2 ? launch_dstage<T, 2>(c, trans, c0)
+                                  : launch_dstage<T, 4>(c, trans, c0);
+        if (!ok) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// In-place recursive LU with both inverses of the n x n leading view of S
+// (n a multiple of 64): Li = L^{-1}, Ui = U^{-1}; Tm is workspace.  Split
+// n = h + n2 with h = 64 ceil(n / 128):
+//   A11 = L11 U11;  U12 = L11^{-1} A12;  L21 = A21 U11^{-1};
+//   A22 -= L21 U12 = L22 U22;  (L^{-1})_21 = -L22^{-1} (L21 L11^{-1}),
+//   (U^{-1})_12 = -U11^{-1} (U12 U22^{-1}).
+// The zero triangles of Li, Ui must be zero on entry.  Every product writes
+// the layouts its consumers read.
+bool luinv(Ctx *c, const WMat &S, const WMat &Li, const WMat &Ui, const WMat &Tm, int n, int64_t row0) {
+    const int p = c->p;
+    if (n % 64 != 0 || n < 64) {
+        c->err = "wide-band block LU: block order is not a multiple of 64";
+        return false;
+    }
+    if (n == 64) {
+        if (!run_lu_inv64(c, S.f, (int)S.ld, S.s, Li.f, Ui.f, (int)Li.ld, Li.s, row0)) return false;
+        // the other layouts of the two 64 x 64 inverses (row-major working copy
+        // for the D-stage, operand copies for the products)
+        const dim3 grid(8, p);
+        return launch(c, KID_WIDE_VEC, [&] {
+            for (const WMat *m : {&Li, &Ui}) {
+                if (c->gpath == 2)
+                    k_wide_layouts<float, __nv_bfloat16><<<grid, 256, 0, c->stream>>>(
+                        (const float *)m->f, 64, m->ld, m->s, (float *)m->fr, (__nv_bfloat16 *)m->oc,
+                        (__nv_bfloat16 *)m->orow);
+                else if (c->gpath == 1)  // TF32: oc / orow alias f / fr
+                    k_wide_layouts<float, float><<<grid, 256, 0, c->stream>>>((const float *)m->f, 64, m->ld, m->s,
+                                                                            (float *)m->fr, nullptr, nullptr);
+                else if (c->fp64)
+                    k_wide_layouts<double, double><<<grid, 256, 0, c->stream>>>(
+                        (const double *)m->f, 64, m->ld, m->s, (double *)m->fr, nullptr, nullptr);
+                else
+                    k_wide_layouts<float, float><<<grid, 256, 0, c->stream>>>((const float *)m->f, 64, m->ld, m->s,
+                                                                            (float *)m->fr, nullptr, nullptr);
+            }
+        });
+    }
+    const int h = 64 * ((n / 64 + 1) / 2), n2 = n - h;
+    auto q12 = [&](const WMat &m) { return view(c, m, 0, h); };
+    auto q21 = [&](const WMat &m) { return view(c, m, h, 0); };
+    auto q22 = [&](const WMat &m) { return view(c, m, h, h); };
+    if (!luinv(c, S, Li, Ui, Tm, h, row0)) return false;
+    return gemm(c, h, n2, h, 1.0, Li, false, q12(S), false, 0.0, q12(Tm), p) &&           // U12 = L11^{-1} A12
+           gemm(c, n2, h, h, 1.0, q21(S), false, Ui, false, 0.0, q21(Tm), p) &&           // L21 = A21 U11^{-1}
+           gemm(c, n2, n2, h, -1.0, q21(Tm), false, q12(Tm), false, 1.0, q22(S), p) &&    // A22 -= L21 U12
+           luinv(c, q22(S), q22(Li), q22(Ui), q22(Tm), n2, row0 + h) &&
+           gemm(c, n2, h, h, 1.0, q21(Tm), false, Li, false, 0.0, q21(S), p) &&           // L21 L11^{-1}
+           gemm(c, n2, h, n2, -1.0, q22(Li), false, q21(S), false, 0.0, q21(Li), p) &&
+           gemm(c, h, n2, n2, 1.0, q12(Tm), false, q22(Ui), false, 0.0, q12(S), p) &&     // U12 U22^{-1}
+           gemm(c, h, n2, h, -1.0, Ui, false, q12(S), false, 0.0, q12(Ui), p);
+}
+
+// Orthonormal basis of the columns of the 2p iterates in Y (PS x lp, first
+// ell columns live) by shifted CholeskyQR3; the result lands in Qout.
+template <typename T>
+bool cholqr3(Ctx *c, void *Y, void *Qout) {
+    const int lp = c->lp, ell = c->ell, nm = 2 * c->p;
+    const int64_t PS = c->PS, sY = PS * lp, sG = (int64_t)lp * lp;
+    const double u = c->fp64 ? 0x1p-53 : 0x1p-24;
+    const size_t smem = ((size_t)ell * (ell + 1) + ell) * sizeof(double);
+    cudaFuncSetAttribute(k_chol_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int pass = 0; pass < 3; ++pass) {
+        // pass 0: Y -> Qout (shifted); 1: Qout -> Y; 2: Y -> Qout
+        void *src = (pass == 1) ? Qout : Y, *dst = (pass == 1) ? Y : Qout;
+        const dim3 gg((unsigned)((lp + 63) / 64), (unsigned)((lp + 63) / 64), (unsigned)nm);
+        const dim3 gq((unsigned)((PS + 63) / 64), (unsigned)((lp + 63) / 64), (unsigned)nm);
+        const bool ok =
+            launch(c, KID_WIDE_CHOLQR, [&] {
+                k_simt_gemm<T><<<gg, 256, 0, c->stream>>>(lp, lp, (int)PS, T(1), T(0), (const T *)src, PS, 1, sY,
+                                                          (const T *)src, PS, 1, sY, (T *)c->WG, lp, sG, nullptr, 0,
+                                                          0);
+            }) &&
+            launch(c, KID_WIDE_CHOLQR, [&] {
+                k_to_f64<T><<<64, 256, 0, c->stream>>>((const T *)c->WG, c->WGd, nm * sG);
+            }) &&
+            launch(c, KID_WIDE_CHOLQR, [&] {
+                k_chol_inv<T><<<nm, 256, smem, c->stream>>>(c->WGd, lp, ell, PS, u, pass == 0 ? 1 : 0, (T *)c->WRi);
+            }) &&
+            launch(c, KID_WIDE_CHOLQR, [&] {
+                k_simt_gemm<T><<<gq, 256, 0, c->stream>>>((int)PS, lp, lp, T(1), T(0), (const T *)src, 1, PS, sY,
+                                                          (const T *)c->WRi, lp, 1, sG, (T *)dst, PS, sY, nullptr, 0,
+                                                          0);
+            });
+        if (!ok) return false;
+    }
+    return true;
 }
 
 template <typename T>
 bool wide_factor_t(Ctx *c) {
-    const int W = c->W, NB = c->NBW, p = c->p, tz = c->tsize;
+    const int W = c->W, NB = c->NBW, p = c->p;
     const int64_t WW = (int64_t)W * W, sF = NB * WW, PS = c->PS;
+    const bool tc = c->gpath != 0, bf = c->gpath == 2;
     Parts P{c->off_d, c->boff_d, p};
-    const size_t tiles = (size_t)p * sF * tz;
-    if (cudaMemsetAsync(c->WLi, 0, tiles, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->WUi, 0, tiles, c->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(c->gemm_err, 0, sizeof(int), c->stream) != cudaSuccess) {
         c->err = "cudaMemsetAsync failed";
         return false;
     }
+    // the zero triangles of the diagonal-block inverses (every layout)
+    for (int kind = 0; kind < 2; ++kind) {
+        void *arrs[4] = {c->WF[kind], c->WFr[kind], c->WFoc[kind], c->WFor[kind]};
+        const size_t szs[4] = {c->tsize, c->tsize, c->osize, c->osize};
+        for (int l = 0; l < 4; ++l)
+            if (arrs[l] && cudaMemsetAsync(arrs[l], 0, (size_t)p * sF * szs[l], c->stream) != cudaSuccess) {
+                c->err = "cudaMemsetAsync failed";
+                return false;
+            }
+    }
+    WMat S = square(c->WSm, W, WW), Bm = square(c->WBm, W, WW), Cm = square(c->WCm, W, WW),
+         Tm = square(c->WTm, W, WW);
+    auto tile = [&](int kind, int J) {  // factor tile J of the given kind, all partitions
+        return WMat{elem(c->WF[kind], J * WW, c->tsize), elem(c->WFr[kind], J * WW, c->tsize),
+                    elem(c->WFoc[kind], J * WW, c->osize), elem(c->WFor[kind], J * WW, c->osize), W, sF, W, sF};
+    };
     for (int J = 0; J < NB; ++J) {
         if (!launch(c, KID_WIDE_GATHER, [&] {
-                k_wide_gather<T><<<dim3(W / 32, W / 32, 3 * p), 256, 0, c->stream>>>(
-                    c->band, c->ld, c->k, P, W, J, (T *)c->WS, (T *)c->WB, (T *)c->WC);
+                const dim3 grid(W / 32, W / 32, 3 * p);
+                if (bf)
+                    k_wide_gather<float, __nv_bfloat16><<<grid, 256, 0, c->stream>>>(
+                        c->band, c->ld, c->k, P, W, J, (float *)S.f, nullptr, (__nv_bfloat16 *)S.oc,
+                        (__nv_bfloat16 *)S.orow, (float *)Bm.f, (__nv_bfloat16 *)Bm.oc, (float *)Cm.f,
+                        (__nv_bfloat16 *)Cm.orow);
+                else if (tc)
+                    k_wide_gather<float, float><<<grid, 256, 0, c->stream>>>(
+                        c->band, c->ld, c->k, P, W, J, (float *)S.f, nullptr, nullptr, (float *)S.orow, (float *)Bm.f,
+                        nullptr, (float *)Cm.f, (float *)Cm.orow);
+                else
+                    k_wide_gather<T, T><<<grid, 256, 0, c->stream>>>(c->band, c->ld, c->k, P, W, J, (T *)S.f,
+                                                                     nullptr, nullptr, nullptr, (T *)Bm.f, nullptr,
+                                                                     (T *)Cm.f, nullptr);
             }))
             return false;
-        void *Li = at(c->WLi, J * WW, tz), *Ui = at(c->WUi, J * WW, tz);
-        void *Z = at(c->WZ, J * WW, tz), *Y = at(c->WY, J * WW, tz);
-        if (J > 0 && !gemm(c, false, false, W, W, W, -1.0, at(c->WY, (J - 1) * WW, tz), W, sF,
-                           at(c->WZ, (J - 1) * WW, tz), W, sF, 1.0, c->WS, W, WW, p))
-            return false;
-        if (!luinv(c, c->WS, Li, Ui, c->WT, W, WW, sF, WW, (int64_t)J * W)) return false;
-        if (!gemm(c, false, false, W, W, W, 1.0, Li, W, sF, c->WB, W, WW, 0.0, Z, W, sF, p) ||
-            !gemm(c, false, false, W, W, W, 1.0, c->WC, W, WW, Ui, W, sF, 0.0, Y, W, sF, p))
+        const WMat Li = tile(0, J), Ui = tile(1, J), Z = tile(2, J), Y = tile(3, J);
+        if (J > 0 && !gemm(c, W, W, W, -1.0, tile(3, J - 1), false, tile(2, J - 1), false, 1.0, S, p)) return false;
+        if (!luinv(c, S, Li, Ui, Tm, W, (int64_t)J * W)) return false;
+        if (!gemm(c, W, W, W, 1.0, Li, false, Bm, false, 0.0, Z, p) ||
+            !gemm(c, W, W, W, 1.0, Cm, false, Ui, false, 0.0, Y, p))
             return false;
     }
     if (p < 2 || c->r == 0) return true;
 
     // spikes [T | W] on the panel X1 (forward results in X2, solution back in X1)
     const int64_t sX = PS * 2 * W;
-    const size_t panel = (size_t)p * sX * tz;
-    if (cudaMemsetAsync(c->WX1, 0, panel, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->WX2, 0, panel, c->stream) != cudaSuccess) {
-        c->err = "cudaMemsetAsync failed";
-        return false;
-    }
+    const size_t panel = (size_t)p * sX;
+    for (void *q : {c->WX1, c->WX2})
+        if (cudaMemsetAsync(q, 0, panel * c->tsize, c->stream) != cudaSuccess) return false;
+    for (void *q : {c->WX1c, c->WX2c})
+        if (q && cudaMemsetAsync(q, 0, panel * c->osize, c->stream) != cudaSuccess) return false;
     if (!launch(c, KID_SPIKE_RHS, [&] {
-            k_wide_spike_rhs<T><<<p, 256, 0, c->stream>>>(c->band, c->ld, c->k, P, W, PS, (T *)c->WX1);
+            if (bf)
+                k_wide_spike_rhs<float, __nv_bfloat16><<<p, 256, 0, c->stream>>>(
+                    c->band, c->ld, c->k, P, W, PS, (float *)c->WX1, (__nv_bfloat16 *)c->WX1c);
+            else
+                k_wide_spike_rhs<T, T><<<p, 256, 0, c->stream>>>(c->band, c->ld, c->k, P, W, PS, (T *)c->WX1,
+                                                                 nullptr);
         }))
         return false;
+    // panel views: column-major PS x 2W (operand copy for BF16), rows of block J
+    auto pan = [&](void *f, void *oc, int64_t col0, int64_t J) {
+        WMat m;
+        m.f = elem(f, col0 * PS + J * W, c->tsize);
+        m.oc = bf ? elem(oc, col0 * PS + J * W, c->osize) : m.f;
+        m.ld = PS;
+        m.s = sX;
+        return m;
+    };
     // the T columns are zero above the block holding the first row of B_i
     int64_t jt0 = NB;
     for (int i = 0; i < p; ++i) jt0 = std::min<int64_t>(jt0, (c->off_h[i + 1] - c->off_h[i] - c->k) / W);
     for (int J = 0; J < NB; ++J) {
         const int c0 = (J < jt0) ? W : 0, nc = 2 * W - c0;
-        void *x1 = at(c->WX1, (int64_t)c0 * PS + (int64_t)J * W, tz);
-        void *x2 = at(c->WX2, (int64_t)c0 * PS + (int64_t)J * W, tz);
-        if (J > 0 && !gemm(c, false, false, W, nc, W, -1.0, at(c->WY, (J - 1) * WW, tz), W, sF,
-                           at(c->WX2, (int64_t)c0 * PS + (int64_t)(J - 1) * W, tz), (int)PS, sX, 1.0, x1, (int)PS,
-                           sX, p))
+        const WMat x1 = pan(c->WX1, c->WX1c, c0, J), x2 = pan(c->WX2, c->WX2c, c0, J);
+        if (J > 0 && !gemm(c, W, nc, W, -1.0, tile(3, J - 1), false, pan(c->WX2, c->WX2c, c0, J - 1), false, 1.0, x1,
+                           p))
             return false;
-        if (!gemm(c, false, false, W, nc, W, 1.0, at(c->WLi, J * WW, tz), W, sF, x1, (int)PS, sX, 0.0, x2, (int)PS,
-                  sX, p))
-            return false;
+        if (!gemm(c, W, nc, W, 1.0, tile(0, J), false, x1, false, 0.0, x2, p)) return false;
     }
     for (int J = NB - 1; J >= 0; --J) {
-        void *x1 = at(c->WX1, (int64_t)J * W, tz), *x2 = at(c->WX2, (int64_t)J * W, tz);
-        if (J < NB - 1 && !gemm(c, false, false, W, 2 * W, W, -1.0, at(c->WZ, J * WW, tz), W, sF,
-                                at(c->WX1, (int64_t)(J + 1) * W, tz), (int)PS, sX, 1.0, x2, (int)PS, sX, p))
+        const WMat x2 = pan(c->WX2, c->WX2c, 0, J);
+        WMat x1 = pan(c->WX1, c->WX1c, 0, J);
+        if (J < NB - 1 && !gemm(c, W, 2 * W, W, -1.0, tile(2, J), false, pan(c->WX1, c->WX1c, 0, J + 1), false, 1.0,
+                                x2, p))
             return false;
-        if (!gemm(c, false, false, W, 2 * W, W, 1.0, at(c->WUi, J * WW, tz), W, sF, x2, (int)PS, sX, 0.0, x1, (int)PS,
-                  sX, p))
-            return false;
+        // the solved spikes, also row-major in the operand type ([p][side][PS][W])
+        x1.orow = tc ? elem(c->WXr, (int64_t)J * W * W, c->osize) : nullptr;
+        x1.ldr = W;
+        x1.sr = 2 * PS * W;
+        if (!gemm(c, W, 2 * W, W, 1.0, tile(1, J), false, x2, false, 0.0, x1, p, W, PS * W)) return false;
     }
 
-    // Gram matrices: G_{2i} = T_i^T T_i, G_{2i+1} = W_i^T W_i
-    for (int side = 0; side < 2; ++side) {
-        void *xs = at(c->WX1, (int64_t)side * W * PS, tz);
-        if (!gemm(c, true, false, W, W, (int)PS, 1.0, xs, (int)PS, sX, xs, (int)PS, sX, 0.0, at(c->WG, side * WW, tz), W,
-                  2 * WW, p))
-            return false;
-    }
-
-    // randomized subspace iteration on every Gram matrix (2p of them)
+    // randomized range finder on every spike (2p of them, b = 2 i + side)
     const int nm = 2 * p, lp = c->lp, ell = c->ell, r = c->r;
-    const int64_t sY = (int64_t)W * lp, sH = (int64_t)lp * lp;
-    const double orth_tol = c->fp64 ? 1e-7 : 1e-3;
+    const int64_t sQ = PS * lp, sZ = (int64_t)W * lp;
+    WMat Tsp;  // spike b: PS x W
+    Tsp.f = c->WX1;
+    Tsp.oc = bf ? c->WX1c : c->WX1;
+    Tsp.orow = tc ? c->WXr : nullptr;
+    Tsp.ld = PS;
+    Tsp.s = (int64_t)W * PS;
+    Tsp.ldr = W;
+    Tsp.sr = PS * W;
+    WMat Om;
+    Om.f = Om.oc = c->WOm;
+    Om.ld = W;
+    Om.s = sZ;
+    WMat Yk;
+    Yk.f = c->WYk;
+    Yk.ld = PS;
+    Yk.s = sQ;
+    WMat Qk;
+    Qk.f = c->WQk;
+    Qk.oc = bf ? c->WQc : c->WQk;
+    Qk.ld = PS;
+    Qk.s = sQ;
+    WMat Zk;
+    Zk.f = c->WZk;
+    Zk.oc = bf ? c->WZc : c->WZk;
+    Zk.ld = W;
+    Zk.s = sZ;
     if (!launch(c, KID_WIDE_VEC, [&] {
-            k_wide_sketch<T><<<1024, 256, 0, c->stream>>>((T *)c->WOm, W, c->k, ell, lp, c->opt.seed, nm);
+            if (bf)
+                k_wide_sketch<__nv_bfloat16><<<1024, 256, 0, c->stream>>>((__nv_bfloat16 *)c->WOm, W, c->k, ell, lp,
+                                                                         c->opt.seed, nm);
+            else
+                k_wide_sketch<T><<<1024, 256, 0, c->stream>>>((T *)c->WOm, W, c->k, ell, lp, c->opt.seed, nm);
         }))
         return false;
-    auto orth = [&](void *Y, void *Q) {  // Q = Y V Lambda^{-1/2} from Y^T Y = V Lambda V^T
-        return gemm(c, true, false, lp, lp, W, 1.0, Y, W, sY, Y, W, sY, 0.0, c->WH, lp, sH, nm) &&
-               launch(c, KID_WIDE_VEC, [&] {
-                   k_to_f64<T><<<64, 256, 0, c->stream>>>((const T *)c->WH, c->WHd, nm * sH);
-               }) &&
-               run_jacobi_batch(c, lp, c->WHd, nm, lp, orth_tol, c->WE, c->Wsg) &&
-               launch(c, KID_WIDE_VEC, [&] {
-                   k_scale_cols<T><<<64, 256, 0, c->stream>>>((T *)c->WE, c->Wsg, lp, nm);
-               }) &&
-               gemm(c, false, false, W, lp, lp, 1.0, Y, W, sY, c->WE, lp, sH, 0.0, Q, W, sY, nm);
+    auto orth = [&]() {  // Y (in WYk) -> Q (in WQk), and its operand copy
+        if (!cholqr3<T>(c, c->WYk, c->WQk)) return false;
+        if (!bf) return true;
+        return launch(c, KID_WIDE_VEC, [&] {
+            k_to_op<float, __nv_bfloat16><<<1024, 256, 0, c->stream>>>((const float *)c->WQk, (__nv_bfloat16 *)c->WQc,
+                                                                      (int64_t)nm * sQ);
+        });
     };
-    if (!gemm(c, false, false, W, lp, W, 1.0, c->WG, W, WW, c->WOm, W, sY, 0.0, c->WYk, W, sY, nm)) return false;
+    if (!gemm(c, (int)PS, lp, W, 1.0, Tsp, false, Om, false, 0.0, Yk, nm) || !orth()) return false;
     for (int it = 0; it < c->opt.power_iters; ++it)
-        if (!orth(c->WYk, c->WQk) ||
-            !gemm(c, false, false, W, lp, W, 1.0, c->WG, W, WW, c->WQk, W, sY, 0.0, c->WYk, W, sY, nm))
+        if (!gemm(c, W, lp, (int)PS, 1.0, Tsp, true, Qk, false, 0.0, Zk, nm) ||
+            !gemm(c, (int)PS, lp, W, 1.0, Tsp, false, Zk, false, 0.0, Yk, nm) || !orth())
             return false;
-    if (!orth(c->WYk, c->WQk) ||
-        !gemm(c, false, false, W, lp, W, 1.0, c->WG, W, WW, c->WQk, W, sY, 0.0, c->WTk, W, sY, nm) ||
-        !gemm(c, true, false, lp, lp, W, 1.0, c->WQk, W, sY, c->WTk, W, sY, 0.0, c->WH, lp, sH, nm) ||
-        !launch(c, KID_WIDE_VEC, [&] {
-            k_to_f64<T><<<64, 256, 0, c->stream>>>((const T *)c->WH, c->WHd, nm * sH);
+    // B^T = T^T Q (W x lp) in the working precision; H = B B^T = Z^T Z (FP64 for the eigensolver)
+    WMat Zf = Zk;
+    Zf.oc = bf ? nullptr : Zk.f;
+    if (!gemm(c, W, lp, (int)PS, 1.0, Tsp, true, Qk, false, 0.0, Zf, nm)) return false;
+    const dim3 gg((unsigned)((lp + 63) / 64), (unsigned)((lp + 63) / 64), (unsigned)nm);
+    if (!launch(c, KID_WIDE_CHOLQR, [&] {
+            k_simt_gemm<T><<<gg, 256, 0, c->stream>>>(lp, lp, W, T(1), T(0), (const T *)c->WZk, W, 1, sZ,
+                                                      (const T *)c->WZk, W, 1, sZ, (T *)c->WG, lp, (int64_t)lp * lp,
+                                                      nullptr, 0, 0);
         }) ||
-        !run_jacobi_batch(c, lp, c->WHd, nm, r, c->opt.rank_tol, c->WE, c->sigma))
+        !launch(c, KID_WIDE_VEC, [&] {
+            k_to_f64<T><<<64, 256, 0, c->stream>>>((const T *)c->WG, c->WGd, (int64_t)nm * lp * lp);
+        }) ||
+        !run_jacobi_batch(c, lp, c->WGd, nm, r, c->opt.rank_tol, c->WE, c->sigma))
         return false;
-    // P^T = V_r = Q E_r (W x r, leading dimension W): PQ holds P row-major r x W;
-    // E_r of matrix b (r eigenvectors of length lp) starts at b r lp
-    if (!gemm(c, false, false, W, r, lp, 1.0, c->WQk, W, sY, c->WE, lp, (int64_t)r * lp, 0.0, c->PQ, W,
-              (int64_t)r * W, nm))
+    // P_b^T = Z_b U_B,r (W x r, leading dimension W): PQ holds P row-major r x W
+    const dim3 gp((unsigned)((W + 63) / 64), (unsigned)((r + 63) / 64), (unsigned)nm);
+    if (!launch(c, KID_WIDE_VEC, [&] {
+            k_simt_gemm<T><<<gp, 256, 0, c->stream>>>(W, r, lp, T(1), T(0), (const T *)c->WZk, 1, W, sZ,
+                                                      (const T *)c->WE, lp, 1, (int64_t)r * lp, (T *)c->PQ, W,
+                                                      (int64_t)r * W, nullptr, 0, 0);
+        }))
         return false;
-
-    // u = X V_r into Ucat (row-major n x 2r): u^T (r x n_i, leading dimension 2r)
-    // = V_r^T X^T, partitions grouped by n_i for pointer-array batches
-    std::vector<std::pair<int64_t, std::vector<int>>> groups;
-    for (int i = 0; i < p; ++i) {
-        const int64_t ni = c->off_h[i + 1] - c->off_h[i];
-        auto g = std::find_if(groups.begin(), groups.end(), [&](const auto &x) { return x.first == ni; });
-        if (g == groups.end()) groups.push_back({ni, {i}});
-        else g->second.push_back(i);
-    }
-    // per (group, side): [A pointers][B pointers][C pointers]
-    std::vector<const void *> hp;
-    for (auto &g : groups)
-        for (int side = 0; side < 2; ++side) {
-            for (int i : g.second) hp.push_back(at(c->PQ, (int64_t)(2 * i + side) * r * W, tz));
-            for (int i : g.second) hp.push_back(at(c->WX1, (int64_t)i * sX + (int64_t)side * W * PS, tz));
-            for (int i : g.second) hp.push_back(at(c->Ucat, c->off_h[i] * 2 * r + side * r, tz));
-        }
-    // the pointer arrays are read by the GEMMs of this factorisation only
-    if (cudaMemcpyAsync(c->Wptr, hp.data(), hp.size() * sizeof(void *), cudaMemcpyHostToDevice, c->stream) !=
-        cudaSuccess) {
-        c->err = "pointer array copy failed";
-        return false;
-    }
-    cublasHandle_t hb = static_cast<cublasHandle_t>(c->blas);
-    const cudaDataType dt = c->fp64 ? CUDA_R_64F : CUDA_R_32F;
-    const cublasComputeType_t ct = c->fp64 ? CUBLAS_COMPUTE_64F
-                                   : (c->opt.precision == LRSPIKE_MIXED_TF32) ? CUBLAS_COMPUTE_32F_FAST_TF32
-                                                                               : CUBLAS_COMPUTE_32F;
-    const double one = 1.0, zero = 0.0;
-    const float onef = 1.0f, zerof = 0.0f;
-    size_t off = 0;
-    for (auto &g : groups)
-        for (int side = 0; side < 2; ++side) {
-            const int cnt = (int)g.second.size();
-            void **base = c->Wptr + off;
-            cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
-            const bool ok = launch(c, KID_WIDE_GEMM, [&] {
-                st = cublasGemmBatchedEx(hb, CUBLAS_OP_T, CUBLAS_OP_T, r, (int)g.first, W,
-                                         c->fp64 ? (const void *)&one : (const void *)&onef, base, dt, W, base + cnt,
-                                         dt, (int)PS, c->fp64 ? (const void *)&zero : (const void *)&zerof,
-                                         base + 2 * cnt, dt, 2 * r, cnt, ct, CUBLAS_GEMM_DEFAULT);
-            });
-            if (!ok || st != CUBLAS_STATUS_SUCCESS) {
-                if (c->err.empty()) c->err = "cuBLAS batched GEMM (u-factors) failed";
-                return false;
-            }
-            off += 3 * (size_t)cnt;
-        }
-    return true;
+    // u_b = Q_b U_B,r into Ucat
+    const size_t usm = (size_t)r * lp * sizeof(T);
+    cudaFuncSetAttribute(k_wide_u<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usm);
+    return launch(c, KID_WIDE_VEC, [&] {
+        k_wide_u<T><<<dim3((unsigned)((PS + 127) / 128), nm), 128, usm, c->stream>>>((const T *)c->WQk, PS, lp,
+                                                                                     (const T *)c->WE, r, P,
+                                                                                     (T *)c->Ucat);
+    });
 }
 
 }  // namespace
@@ -465,38 +1288,77 @@ bool wide_setup(Ctx *c) {
     c->NBW = (int)nbw;
     c->PS = nbw * c->W;
     c->ell = std::min(k, r + c->opt.oversample);
-    c->lp = c->ell <= 16 ? 16 : c->ell <= 32 ? 32 : 64;
-    const size_t tz = c->tsize, W = c->W, WW = W * W, NB = c->NBW, PS = c->PS, lp = c->lp;
+    c->lp = c->ell <= 16 ? 16 : c->ell <= 32 ? 32 : c->ell <= 64 ? 64 : 128;
+    c->gpath = (c->opt.precision == LRSPIKE_MIXED_TF32) ? 1 : (c->opt.precision == LRSPIKE_MIXED_BF16) ? 2 : 0;
+    c->osize = (c->gpath == 2) ? 2 : c->tsize;
+    const size_t tz = c->tsize, oz = c->osize, W = c->W, WW = W * W, NB = c->NBW, PS = c->PS, lp = c->lp;
+    const bool tc = c->gpath != 0, bf = c->gpath == 2;
     auto al = [&](void **ptr, size_t bytes) { return cudaMalloc(ptr, bytes) == cudaSuccess; };
-    bool ok = al(&c->WLi, p * NB * WW * tz) && al(&c->WUi, p * NB * WW * tz) && al(&c->WZ, p * NB * WW * tz) &&
-              al(&c->WY, p * NB * WW * tz) && al(&c->WS, p * WW * tz) && al(&c->WB, p * WW * tz) &&
-              al(&c->WC, p * WW * tz) && al(&c->WT, p * WW * tz) && al(&c->WV1, p * PS * VP * tz) &&
-              al(&c->WV2, p * PS * VP * tz) && al((void **)&c->diag_list, (2 * k + 1) * sizeof(int));
-    if (ok && p > 1 && r > 0)
-        ok = al(&c->WX1, p * PS * 2 * W * tz) && al(&c->WX2, p * PS * 2 * W * tz) && al(&c->WG, 2 * p * WW * tz) &&
-             al(&c->WOm, 2 * p * W * lp * tz) && al(&c->WYk, 2 * p * W * lp * tz) &&
-             al(&c->WQk, 2 * p * W * lp * tz) && al(&c->WTk, 2 * p * W * lp * tz) &&
-             al(&c->WH, 2 * p * lp * lp * tz) && al(&c->WE, 2 * p * lp * lp * tz) &&
-             al((void **)&c->WHd, 2 * p * lp * lp * 8) && al((void **)&c->Wsg, 2 * p * lp * 8) &&
-             al((void **)&c->Wptr, 6 * (size_t)p * sizeof(void *));
+    bool ok = true;
+    // factor tiles: f and fr always (the D-stage reads fr for A, f for A^T);
+    // operand copies in BF16 mode (TF32: they alias f / fr)
+    for (int kind = 0; kind < 4 && ok; ++kind) {
+        ok = al(&c->WF[kind], p * NB * WW * tz) && al(&c->WFr[kind], p * NB * WW * tz);
+        if (ok && bf) ok = al(&c->WFoc[kind], p * NB * WW * oz) && al(&c->WFor[kind], p * NB * WW * oz);
+        if (ok && !bf && tc) {
+            c->WFoc[kind] = c->WF[kind];
+            c->WFor[kind] = c->WFr[kind];
+        }
+    }
+    // block-step work: f always; operand layouts in the tensor-core modes
+    void **work[4] = {c->WSm, c->WBm, c->WCm, c->WTm};
+    for (int w = 0; w < 4 && ok; ++w) {
+        ok = al(&work[w][0], p * WW * tz);
+        if (ok && tc) {
+            if (bf) ok = al(&work[w][2], p * WW * oz) && al(&work[w][3], p * WW * oz);
+            else {
+                work[w][2] = work[w][0];
+                ok = al(&work[w][3], p * WW * oz);
+            }
+        }
+    }
+    ok = ok && al(&c->WV1, p * PS * VP * tz) && al(&c->WV2, p * PS * VP * tz) &&
+         al((void **)&c->diag_list, (2 * k + 1) * sizeof(int)) && al((void **)&c->gemm_err, sizeof(int));
+    if (ok && p > 1 && r > 0) {
+        ok = al(&c->WX1, p * PS * 2 * W * tz) && al(&c->WX2, p * PS * 2 * W * tz) &&
+             al(&c->WOm, 2 * p * W * lp * (tc ? oz : tz)) && al(&c->WYk, 2 * p * PS * lp * tz) &&
+             al(&c->WQk, 2 * p * PS * lp * tz) && al(&c->WZk, 2 * p * W * lp * tz) &&
+             al(&c->WG, 2 * p * lp * lp * tz) && al((void **)&c->WGd, 2 * p * lp * lp * 8) &&
+             al(&c->WRi, 2 * p * lp * lp * tz) && al(&c->WE, 2 * p * (size_t)std::max(r, 1) * lp * tz);
+        if (ok && tc) ok = al(&c->WXr, p * PS * 2 * W * oz);
+        if (ok && bf)
+            ok = al(&c->WX1c, p * PS * 2 * W * oz) && al(&c->WX2c, p * PS * 2 * W * oz) &&
+                 al(&c->WQc, 2 * p * PS * lp * oz) && al(&c->WZc, 2 * p * W * lp * oz);
+    }
     if (!ok) {
         cudaGetLastError();
         return false;
     }
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return false;
-    c->blas = h;
-    return cublasSetStream(h, c->stream) == CUBLAS_STATUS_SUCCESS;
+    return true;
 }
 
 void wide_free(Ctx *c) {
-    void *ptrs[] = {c->WLi, c->WUi, c->WZ,  c->WY,  c->WS,  c->WB,   c->WC,  c->WT,    c->WX1,
-                    c->WX2, c->WG,  c->WOm, c->WYk, c->WQk, c->WTk,  c->WH,  c->WE,    c->WHd,
-                    c->Wsg, c->WV1, c->WV2, c->Wptr, c->diag_list};
+    std::vector<void *> ptrs;
+    for (int kind = 0; kind < 4; ++kind) {
+        ptrs.push_back(c->WF[kind]);
+        ptrs.push_back(c->WFr[kind]);
+        if (c->WFoc[kind] != c->WF[kind]) ptrs.push_back(c->WFoc[kind]);
+        if (c->WFor[kind] != c->WFr[kind]) ptrs.push_back(c->WFor[kind]);
+        c->WF[kind] = c->WFr[kind] = c->WFoc[kind] = c->WFor[kind] = nullptr;
+    }
+    void **work[4] = {c->WSm, c->WBm, c->WCm, c->WTm};
+    for (auto w : work) {
+        ptrs.push_back(w[0]);
+        ptrs.push_back(w[1]);
+        if (w[2] != w[0]) ptrs.push_back(w[2]);
+        ptrs.push_back(w[3]);
+        w[0] = w[1] = w[2] = w[3] = nullptr;
+    }
+    for (void *q : {c->WX1, c->WX2, c->WX1c, c->WX2c, c->WXr, c->WOm, c->WYk, c->WQk, c->WQc, c->WZk, c->WZc, c->WG,
+                    (void *)c->WGd, c->WRi, c->WE, c->WV1, c->WV2, (void *)c->diag_list, (void *)c->gemm_err})
+        ptrs.push_back(q);
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    if (c->blas) cublasDestroy(static_cast<cublasHandle_t>(c->blas));
-    c->blas = nullptr;
 }
 
 bool run_wide_factor(Ctx *c) {
@@ -511,10 +1373,16 @@ bool run_wide_factor(Ctx *c) {
         }))
         return false;
     std::vector<int> flag(nd), list;
+    int gerr = 0;
     if (cudaMemcpyAsync(flag.data(), c->diag_list, nd * sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess ||
+        cudaMemcpyAsync(&gerr, c->gemm_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return false;
+    if (gerr) {
+        c->err = "a tensor-core block product gave up waiting on its pipeline";
+        return false;
+    }
     for (int d = 0; d < nd; ++d)
         if (flag[d]) list.push_back(d);
     if (list.empty()) list.push_back(c->k);
@@ -526,8 +1394,8 @@ bool run_wide_factor(Ctx *c) {
 
 template <typename T>
 static bool wide_dstage_t(Ctx *c, const double *rin, int nrhs, bool trans, double *x, int64_t ldx, bool acc) {
-    const int W = c->W, NB = c->NBW, p = c->p, tz = c->tsize;
-    const int64_t WW = (int64_t)W * W, sF = NB * WW, PS = c->PS, sV = PS * VP;
+    const int W = c->W, p = c->p;
+    const int64_t PS = c->PS;
     Parts P{c->off_d, c->boff_d, p};
     const dim3 grid((unsigned)((PS + 255) / 256), p);
     const double *inv = c->nrm + 2 * c->opt.max_nrhs;
@@ -539,27 +1407,7 @@ static bool wide_dstage_t(Ctx *c, const double *rin, int nrhs, bool trans, doubl
                 k_wide_pack<T><<<grid, 256, 0, c->stream>>>(rin, inv, c->n, P, PS, nrhs, (T *)c->WV1);
         }))
         return false;
-    auto v1 = [&](int J) { return at(c->WV1, (int64_t)J * W, tz); };
-    auto v2 = [&](int J) { return at(c->WV2, (int64_t)J * W, tz); };
-    auto tile = [&](void *base, int J) { return at(base, J * WW, tz); };
-    // forward: y_J = L_JJ^{-1}(b_J - L_{J,J-1} y_{J-1})   (transposed: U^T)
-    void *Lo = trans ? c->WZ : c->WY, *Di = trans ? c->WUi : c->WLi;
-    for (int J = 0; J < NB; ++J) {
-        if (J > 0 && !gemm(c, trans, false, W, nrhs, W, -1.0, tile(Lo, J - 1), W, sF, v2(J - 1), (int)PS, sV, 1.0,
-                           v1(J), (int)PS, sV, p))
-            return false;
-        if (!gemm(c, trans, false, W, nrhs, W, 1.0, tile(Di, J), W, sF, v1(J), (int)PS, sV, 0.0, v2(J), (int)PS, sV, p))
-            return false;
-    }
-    // backward: x_J = U_JJ^{-1}(y_J - U_{J,J+1} x_{J+1})   (transposed: L^T)
-    void *Up = trans ? c->WY : c->WZ, *Dj = trans ? c->WLi : c->WUi;
-    for (int J = NB - 1; J >= 0; --J) {
-        if (J < NB - 1 && !gemm(c, trans, false, W, nrhs, W, -1.0, tile(Up, J), W, sF, v1(J + 1), (int)PS, sV, 1.0,
-                                v2(J), (int)PS, sV, p))
-            return false;
-        if (!gemm(c, trans, false, W, nrhs, W, 1.0, tile(Dj, J), W, sF, v2(J), (int)PS, sV, 0.0, v1(J), (int)PS, sV, p))
-            return false;
-    }
+    if (!run_dstage_chain<T>(c, nrhs, trans)) return false;
     if (trans)
         return launch(c, KID_WIDE_VEC, [&] {
             k_wide_unpack_t<T><<<grid, 256, 0, c->stream>>>((const T *)c->WV1, c->nrm + c->opt.max_nrhs, P, PS, nrhs,

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(PKG, "liblrspike.so")
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "OOM", 4: "CUDA", 5: "SINGULAR",
           6: "NOT_CONVERGED", 7: "UNSUPPORTED"}
-PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 COMPRESS = {"spike": 0, "coupling": 1}
 REDUCED = {"full": 0, "truncated": 1, "otf": 2}
 OUTER = {"ir": 0, "bicgstab": 1, "none": 2}

@@ -1,6 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Tolerances:
+Tolerances (each also checked per partition in the max-norm at ten times
+the bound, tests/_parity.py):
   FP64, one preconditioner application: ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-12.
   Mixed (FP32 working precision), one application: <= 5e-5.  Derivation: the
     FP32 unit roundoff is 6e-8; a block sweep over a partition accumulates
@@ -17,6 +18,7 @@ import scipy.linalg
 
 from oracle import lrspike_oracle as O
 from paper_2504_11167_gb300 import inputs
+from _parity import check
 
 pytestmark = pytest.mark.gpu
 
@@ -87,7 +89,7 @@ def test_preconditioner_parity_fp64(torch_cuda, case):
     want = O.apply(fac, np.asarray(f))
     got, _, sig = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced=reduced,
                             outer="none", precision="fp64")
-    assert rel(got, want) <= 1e-12
+    check(got, want, n, p, 1e-12)
     if r == k and reduced == "full":
         assert rel(got, scipy.linalg.solve_banded((k, k), ab, f)) <= 1e-11
     # kept singular values (unique, unlike the singular vectors); the Gram
@@ -101,7 +103,7 @@ def test_preconditioner_parity_fp64(torch_cuda, case):
     # transposed operator
     gotT, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced=reduced,
                            outer="none", precision="fp64", transpose=True)
-    assert rel(gotT, O.apply_T(fac, np.asarray(f))) <= 1e-12
+    check(gotT, O.apply_T(fac, np.asarray(f)), n, p, 1e-12)
 
 
 @pytest.mark.parametrize("case", CASES[:7], ids=[case_id(c) for c in CASES[:7]])
@@ -113,10 +115,10 @@ def test_preconditioner_parity_mixed(torch_cuda, case):
     fac = O.factor(ab, k, p, r, compress=compress, reduced=reduced)
     got, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced=reduced,
                           outer="none", precision="fp32")
-    assert rel(got, O.apply(fac, np.asarray(f))) <= MIXED_TOL
+    check(got, O.apply(fac, np.asarray(f)), n, p, MIXED_TOL)
     gotT, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced=reduced,
                            outer="none", precision="fp32", transpose=True)
-    assert rel(gotT, O.apply_T(fac, np.asarray(f))) <= MIXED_TOL
+    check(gotT, O.apply_T(fac, np.asarray(f)), n, p, MIXED_TOL)
 
 
 # FP32, KB = 64, COUPLING with 2r <= 32: the balanced spike sweep writes the
@@ -135,7 +137,7 @@ def test_coupling_u_factors_written_by_the_sweep(torch_cuda, case):
     fac = O.factor(ab, k, p, r, compress="coupling", reduced="truncated")
     got, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress="coupling", reduced="truncated",
                           outer="none", precision="fp32")
-    assert rel(got, O.apply(fac, np.asarray(f))) <= MIXED_TOL
+    check(got, O.apply(fac, np.asarray(f)), n, p, MIXED_TOL)
     x, info, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress="coupling", precision="fp32", tol=1e-10)
     assert info["converged"]
     res = np.asarray(f) - O.band_matvec(ab, k, x)
@@ -214,7 +216,7 @@ def test_config1_full_size_fp64(torch_cuda):
     for reduced in ("full", "truncated"):
         fac = O.factor(ab, k, p, r, reduced=reduced)
         got, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced=reduced, outer="none")
-        assert rel(got, O.apply(fac, np.asarray(f))) <= 1e-12
+        check(got, O.apply(fac, np.asarray(f)), n, p, 1e-12)
         x, info, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced=reduced, tol=1e-12)
         res = np.asarray(f) - O.band_matvec(ab, k, x)
         assert np.linalg.norm(res) / np.linalg.norm(f) <= 1e-12
@@ -250,9 +252,33 @@ def test_tf32_band_lu(torch_cuda, compress):
     fac = O.factor(ab, k, p, r, compress=compress, reduced="truncated")
     got, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced="truncated", outer="none",
                           precision="tf32")
-    assert rel(got, O.apply(fac, np.asarray(f))) <= 1e-3
+    check(got, O.apply(fac, np.asarray(f)), n, p, 1e-3)
     x, info, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced="truncated", precision="tf32",
                            tol=1e-10)
     assert info["converged"]
     res = np.asarray(f) - O.band_matvec(ab, k, x)
     assert (np.linalg.norm(res, axis=0) / np.linalg.norm(f, axis=0)).max() <= 1.01e-10
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", MIXED_TOL), ("fp64", 1e-12)])
+def test_bench_partition_geometry(torch_cuda, precision, tol):
+    """The large banded workload's partition shape: n_i = 16,384 rows, k = 64,
+    r = 16, COUPLING compression, TRUNCATED reduced system, p = 8 (n = 131,072),
+    so the column band LU, the balanced spike sweep and the D-stage run their
+    full-length chains.  One application against the oracle (2-norm and
+    per-partition max-norm), then the IR solve, whose refinement steps fuse
+    each retrieval into the next residual (mixed mode), to its tolerance."""
+    n, k, p, r = 8 * 16384, 64, 8, 16
+    seed = inputs.SEED_BASE + 2
+    ab = inputs.dominant_band(n, k, 1.1, seed)
+    f = inputs.rhs(n, 1, seed)
+    fac = O.factor(ab, k, p, r, compress="coupling", reduced="truncated", threads=8)
+    got, _, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress="coupling", reduced="truncated", outer="none",
+                          precision=precision)
+    check(got, O.apply(fac, np.asarray(f)), n, p, tol)
+    ir_tol = 1e-12 if precision == "fp64" else 1e-10
+    x, info, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress="coupling", reduced="truncated",
+                           precision=precision, tol=ir_tol)
+    assert info["converged"]
+    res = np.asarray(f) - O.band_matvec(ab, k, x)
+    assert np.linalg.norm(res) / np.linalg.norm(f) <= ir_tol * 1.01

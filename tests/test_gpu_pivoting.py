@@ -13,6 +13,7 @@ import scipy.linalg
 
 from oracle import lrspike_oracle as O
 from paper_2504_11167_gb300 import inputs
+from _parity import check
 
 pytestmark = pytest.mark.gpu
 
@@ -73,10 +74,10 @@ def test_pivoted_preconditioner_parity_fp64(torch_cuda, case):
         f = f[:, 0]
     fac = O.factor(ab, k, p, r, compress=compress, reduced=reduced, pivoting=True)
     got, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced=reduced, outer="none")
-    assert rel(got, O.apply(fac, np.asarray(f))) <= 1e-12
+    check(got, O.apply(fac, np.asarray(f)), n, p, 1e-12)
     gotT, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced=reduced, outer="none",
                         transpose=True)
-    assert rel(gotT, O.apply_T(fac, np.asarray(f))) <= 1e-12
+    check(gotT, O.apply_T(fac, np.asarray(f)), n, p, 1e-12)
 
 
 @pytest.mark.parametrize("case", CASES[:5], ids=[case_id(c) for c in CASES[:5]])
@@ -88,10 +89,10 @@ def test_pivoted_preconditioner_parity_mixed(torch_cuda, case):
     fac = O.factor(ab, k, p, r, compress=compress, reduced=reduced, pivoting=True)
     got, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced=reduced, outer="none",
                        precision="fp32")
-    assert rel(got, O.apply(fac, np.asarray(f))) <= MIXED_TOL
+    check(got, O.apply(fac, np.asarray(f)), n, p, MIXED_TOL)
     gotT, _ = gpu_solve(torch_cuda, ab, f, k, p, r, compress=compress, reduced=reduced, outer="none",
                         precision="fp32", transpose=True)
-    assert rel(gotT, O.apply_T(fac, np.asarray(f))) <= MIXED_TOL
+    check(gotT, O.apply_T(fac, np.asarray(f)), n, p, MIXED_TOL)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-10)])

@@ -1,14 +1,16 @@
 """Wide bands (64 < k <= 1024) on the GPU: blocks of W = 64 ceil(k/64), block
-products as batched GEMMs, randomized truncation of the spikes.
+products batched over the partitions (SIMT GEMMs in FP64 / FP32, tcgen05
+tensor cores with TF32 or BF16 operands), the randomized truncation of the
+spikes by the HMT proto-algorithm on each spike, the cluster D-stage.
 
 Parity: one FP64 preconditioner application against the oracle with the same
 randomized truncation (same sketches: SplitMix64 + Box-Muller, seeds
-0x4C52535049 + 2i + side, ell = 2r, two power passes, orthonormalisation cut
-1e-7).  The two sides agree to rounding except where the Gram route's
-resolution (~1e-4 sigma_1, see the oracle's pins) lets rounding differences
-into the weakest kept directions, so the bound is 1e-9 instead of 1e-12.
-Mixed FP32 and TF32 solves: relative residual <= 1e-10 per column (IR, or
-BiCGStab where IR stalls), recomputed with the oracle's FP64 band product.
+0x4C52535049 + 2i + side, ell = 2r, two power passes).  The oracle
+orthonormalises with Householder QR, the GPU with shifted CholeskyQR3; both
+span the same range to rounding, so the bound is the FP64 one-application
+bound of the narrow path, 1e-12 (2-norm), 1e-11 per partition (max-norm).
+Mixed FP32 / TF32 / BF16 solves: relative residual <= 1e-10 per column (IR,
+or BiCGStab where IR stalls), recomputed with the oracle's FP64 band product.
 """
 import numpy as np
 import pytest
@@ -16,6 +18,7 @@ import scipy.linalg
 
 from oracle import lrspike_oracle as O
 from paper_2504_11167_gb300 import inputs
+from _parity import check, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -42,16 +45,14 @@ def gpu_solve(torch, ab, f, k, p, r, transpose=False, allow_unconverged=False, *
     return out.reshape(f.shape), info
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
-
-
 CASES = [
     # n, k, p, r, dom, reduced, nrhs
     (6000, 96, 4, 8, 1.2, "truncated", 1),     # W = 128
     (5000, 70, 3, 6, 1.3, "full", 2),          # W = 128 > k, ragged partitions
     (20000, 200, 5, 16, 1.1, "truncated", 3),  # W = 256: two levels of recursive halving
+    (9000, 130, 3, 10, 1.2, "full", 5),        # W = 192: unequal split 128 + 64, nrhs > 4
     (3000, 100, 1, 4, 1.5, "full", 1),         # p = 1: the wide band LU alone
+    (6200, 1024, 3, 16, 1.1, "truncated", 4),  # W = 1024: the convection-diffusion block size
 ]
 
 
@@ -65,14 +66,14 @@ def test_wide_preconditioner_parity_fp64(torch_cuda, case):
     seed = 2000 + n + k
     ab = inputs.dominant_band(n, k, dom, seed)
     f = inputs.rhs(n, nrhs, seed)
-    fac = O.factor(ab, k, p, r, reduced=reduced)          # k > 64: randomized truncation
+    fac = O.factor(ab, k, p, r, reduced=reduced, threads=p)   # k > 64: randomized truncation
     got, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced=reduced, outer="none")
-    assert rel(got, O.apply(fac, np.asarray(f))) <= 1e-9
+    check(got, O.apply(fac, np.asarray(f)), n, p, 1e-12)
     gotT, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced=reduced, outer="none", transpose=True)
-    assert rel(gotT, O.apply_T(fac, np.asarray(f))) <= 1e-9
+    check(gotT, O.apply_T(fac, np.asarray(f)), n, p, 1e-12)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16", "fp64"])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_wide_solve_reaches_tolerance(torch_cuda, precision, transpose):
     n, k, p, r, nrhs = 24000, 128, 6, 16, 2
@@ -89,14 +90,31 @@ def test_wide_solve_reaches_tolerance(torch_cuda, precision, transpose):
         assert rel(x, xs) <= 1e4 * tol
 
 
-def test_wide_convection_diffusion_bicgstab(torch_cuda):
+@pytest.mark.parametrize("precision,bound", [("tf32", 2e-3), ("bf16", 3e-2)])
+def test_wide_tensor_core_preconditioner_error(torch_cuda, precision, bound):
+    """One application with tensor-core block products against the FP64
+    oracle.  TF32 keeps 10 mantissa bits (unit roundoff 2^-11 = 4.9e-4), BF16
+    7 (2^-8 = 3.9e-3); the rounding of the operands of a product of order W
+    enters M^{-1} f relatively at a few units of that roundoff through the
+    well-conditioned block chain of a dominant band, so the bounds are four
+    (TF32) and eight (BF16) times the operand roundoff."""
+    n, k, p, r = 12000, 128, 4, 16
+    ab = inputs.dominant_band(n, k, 1.2, 31)
+    f = inputs.rhs(n, 2, 31)
+    fac = O.factor(ab, k, p, r, reduced="truncated")
+    got, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced="truncated", outer="none", precision=precision)
+    assert rel(got, O.apply(fac, np.asarray(f))) <= bound
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_wide_convection_diffusion_bicgstab(torch_cuda, precision):
     """2-D convection-diffusion, 96 x 96 grid (k = 96, 5 nonzero diagonals of
-    193), Pe = 0.5: mixed TF32 factors with BiCGStab to 1e-10."""
+    193), Pe = 0.5: tensor-core factors with BiCGStab to 1e-10."""
     nx, p, r = 96, 8, 8
     ab = inputs.convection_diffusion_band(nx, 0.5)
     k, n = nx, ab.shape[1]
     f = inputs.rhs(n, 2, 17)
-    x, info = gpu_solve(torch_cuda, ab, f, k, p, r, precision="tf32", tol=1e-10, outer="bicgstab",
+    x, info = gpu_solve(torch_cuda, ab, f, k, p, r, precision=precision, tol=1e-10, outer="bicgstab",
                         reduced="truncated", max_iter=200)
     assert info["converged"]
     res = np.asarray(f) - O.band_matvec(ab, k, x)

@@ -76,8 +76,10 @@ def test_noalloc_rejects_oversized_and_host_arguments(torch_cuda):
     # the binding checks shapes and placement before it reaches the C call
     with pytest.raises(ValueError):
         residual_noalloc(band, k, f.cpu(), x, res, norms)
-    with pytest.raises(ValueError):
-        residual_noalloc(band, k, f, x, res[:, : n - 1], norms)
+    with pytest.raises(ValueError):                 # x not the shape of f
+        residual_noalloc(band, k, f, x[:, : n - 1], res, norms)
+    with pytest.raises(ValueError):                 # r with a second column f does not have
+        residual_noalloc(band, k, f, x, torch.empty(2, n, dtype=torch.float64, device="cuda"), norms)
     from paper_2504_11167_gb300.solver import load_library
     import ctypes
     lib = load_library()
