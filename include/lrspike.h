@@ -70,7 +70,7 @@ enum { LRSPIKE_COMPRESS_SPIKE = 0, LRSPIKE_COMPRESS_COUPLING = 1 };
 /* Reduced system (section 3.3, table 'solver-list'): FULL = the low-rank
  * reduced system of LR-SPIKE-I, solved directly; TRUNCATED = its truncated
  * block-diagonal form S~~_r of LR-SPIKE-T (eq. 'red_sys_prec_mid_2');
- * OTF = LR-SPIKE-OTF (section 2.1 "SPIKE-on-the-fly", eqs. OTF-1/OTF-2;
+ * OTF = LR-SPIKE-OTF (section 2.2 "SPIKE-on-the-fly", eqs. OTF-1/OTF-2;
  * section 3.3): the TRUE reduced system on the interface tips
  * [x_{i,b}; x_{i+1,t}] (2k per interface), solved by right-preconditioned
  * BiCGStab to otf_tol, its spike products formed on the fly by solves with

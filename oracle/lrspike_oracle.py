@@ -584,7 +584,7 @@ def bicgstab(ab, k, fac: Factor, f: np.ndarray, tol: float = 1e-12, max_iter: in
 
 
 # --------------------------------------------------------------------------
-# LR-SPIKE-OTF (section 2.1, "SPIKE-on-the-fly", eqs. 'OTF-1' and 'OTF-2';
+# LR-SPIKE-OTF (section 2.2, "SPIKE-on-the-fly", eqs. 'OTF-1' and 'OTF-2';
 # section 3.3: the truncated low-rank reduced system as its preconditioner).
 # The TRUE reduced system of the spike matrix S = D^{-1} A is solved
 # iteratively on the interface tips y_i = [x_{i,b} ; x_{i+1,t}] (2k per

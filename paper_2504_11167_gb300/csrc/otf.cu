@@ -1,4 +1,4 @@
-// LR-SPIKE-OTF (paper section 2.1, "SPIKE-on-the-fly", eqs. OTF-1 / OTF-2;
+// LR-SPIKE-OTF (paper section 2.2, "SPIKE-on-the-fly", eqs. OTF-1 / OTF-2;
 // section 3.3: the truncated low-rank reduced system S~~_r as its
 // preconditioner).  The TRUE reduced system of the spike matrix S = D^{-1} A is
 // solved iteratively on the interface tips.  Per interface i = 1..p-1 the

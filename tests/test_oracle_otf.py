@@ -1,4 +1,4 @@
-"""Pins of the oracle's LR-SPIKE-OTF (section 2.1 "SPIKE-on-the-fly", eqs.
+"""Pins of the oracle's LR-SPIKE-OTF (section 2.2 "SPIKE-on-the-fly", eqs.
 OTF-1/OTF-2; section 3.3, the truncated low-rank reduced system as its
 preconditioner) against quantities computed independently of it:
 
