@@ -164,8 +164,9 @@ lrspike_status lrspike_options_default(lrspike_options *opt, int64_t n, int32_t 
  * whose products are batched over the partitions: on the tensor cores
  * (tcgen05; TF32 or BF16 operands, FP32 accumulation) in the MIXED_TF32 and
  * MIXED_BF16 modes, as SIMT GEMMs in the working precision in the FP64 and
- * MIXED_FP32 modes; SPIKE compression, no pivoting, r <= 32, sketch width
- * min(k, r + oversample) <= 64 (FP64) or <= 128 (mixed modes).  The wide-band
+ * MIXED_FP32 modes; SPIKE compression, no pivoting, sketch width
+ * min(k, r + oversample) <= 64 (FP64) or <= 128 (mixed modes).  r <= 32,
+ * or r <= 64 for wide bands with the TRUNCATED reduced system.  The wide-band
  * D-stage runs one cluster of CTAs per partition (at most 8).
  * COUPLING compression with k <= 64, p > 1 and r > 0: the handle also owns a
  * second, non-blocking stream and two events; lrspike_factor runs the

@@ -179,7 +179,11 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
                     "min(k, r + oversample) sketch columns beyond 64 (FP64) / 128 (mixed) is not built");
     if (!wide && o.precision == LRSPIKE_MIXED_BF16)
         return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "BF16 operands are built for the wide-band path (k > 64)");
-    if (o.r > 32) return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED, "r > 32 is not built yet");
+    // reduced-system blocks of 2r x 2r: up to 64 (every path), up to 128 for
+    // wide bands with the truncated reduced system
+    if (o.r > 32 && !(wide && o.r <= 64 && o.reduced == LRSPIKE_REDUCED_TRUNCATED))
+        return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED,
+                    "r > 32 is built for k > 64 with the truncated reduced system (r <= 64)");
     if (o.reduced == LRSPIKE_REDUCED_OTF) {
         if (o.p < 2 || o.r < 1)
             return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "the OTF reduced system needs p >= 2 and r >= 1");

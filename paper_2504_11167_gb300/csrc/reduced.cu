@@ -159,6 +159,70 @@ __global__ void k_red_factor_trunc(const double *__restrict__ E, int n2, double 
     store_inv(aug, Rinv + (int64_t)i * n2 * n2, n2);
 }
 
+// The same inverse for blocks too large for [E | I] in shared memory (2r >
+// 64): Gauss-Jordan in place with partial pivoting.  Step c exchanges rows c
+// and the pivot row, scales row c (its diagonal becomes 1 / pivot) and
+// eliminates column c from every other row (column c then holds the
+// multiples of the eliminated identity column); the row exchanges are undone
+// at the end as column exchanges in reverse order.  Shared memory: n2^2 + n2
+// doubles (129 KB at 2r = 128).
+__global__ void k_red_factor_trunc_ip(const double *__restrict__ E, int n2, double *__restrict__ Rinv,
+                                      int64_t *status) {
+    extern __shared__ double sm[];
+    double *a = sm, *fac = a + n2 * n2;
+    __shared__ int perm[128];
+    __shared__ int pivrow;
+    const int blk = blockIdx.x;
+    const double *e = E + (int64_t)blk * n2 * n2;
+    for (int t = threadIdx.x; t < n2 * n2; t += blockDim.x) a[t] = e[t];
+    __syncthreads();
+    bool ok = true;
+    for (int c = 0; c < n2; ++c) {
+        if (threadIdx.x == 0) {
+            int best = c;
+            for (int i = c + 1; i < n2; ++i)
+                if (fabs(a[i * n2 + c]) > fabs(a[best * n2 + c])) best = i;
+            pivrow = best;
+            perm[c] = best;
+        }
+        __syncthreads();
+        const int pr = pivrow;
+        if (pr != c)
+            for (int j = threadIdx.x; j < n2; j += blockDim.x) {
+                const double t = a[c * n2 + j];
+                a[c * n2 + j] = a[pr * n2 + j];
+                a[pr * n2 + j] = t;
+            }
+        __syncthreads();
+        const double piv = a[c * n2 + c];
+        if (piv == 0.0 || !isfinite(piv)) ok = false;
+        const double pinv = (piv == 0.0) ? 1.0 : 1.0 / piv;
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) fac[i] = a[i * n2 + c];
+        __syncthreads();
+        for (int j = threadIdx.x; j < n2; j += blockDim.x) a[c * n2 + j] = (j == c) ? pinv : a[c * n2 + j] * pinv;
+        __syncthreads();
+        for (int t = threadIdx.x; t < n2 * n2; t += blockDim.x) {
+            const int i = t / n2, j = t % n2;
+            if (i == c) continue;
+            a[t] = (j == c) ? -fac[i] * pinv : a[t] - fac[i] * a[c * n2 + j];
+        }
+        __syncthreads();
+    }
+    for (int c = n2 - 1; c >= 0; --c) {
+        const int pc = perm[c];
+        if (pc != c)
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const double t = a[i * n2 + c];
+                a[i * n2 + c] = a[i * n2 + pc];
+                a[i * n2 + pc] = t;
+            }
+        __syncthreads();
+    }
+    if (!ok && threadIdx.x == 0) atomicMin((unsigned long long *)status, 0x7ffffffffffffffeULL);
+    double *out = Rinv + (int64_t)blk * n2 * n2;
+    for (int t = threadIdx.x; t < n2 * n2; t += blockDim.x) out[t] = a[t];
+}
+
 // Block LU of the block-tridiagonal R in one CTA (sequential over interfaces).
 __global__ void k_red_factor_full(const double *__restrict__ E, const double *__restrict__ F,
                                   const double *__restrict__ Gs, int n2, int ni,
@@ -320,6 +384,13 @@ bool run_reduced_build(Ctx *c) { return run_reduced_build_ld(c, c->KB); }
 bool run_reduced_factor(Ctx *c) {
     if (c->p < 2 || c->r == 0) return true;
     const int n2 = 2 * c->r, ni = c->p - 1;
+    if (c->opt.reduced == LRSPIKE_REDUCED_TRUNCATED && n2 > 64) {
+        const size_t smem = (size_t)(n2 * n2 + n2) * sizeof(double);
+        cudaFuncSetAttribute(k_red_factor_trunc_ip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return launch(c, KID_RED_FACTOR, [&] {
+            k_red_factor_trunc_ip<<<ni, 256, smem, c->stream>>>(c->E, n2, c->Rinv, c->status);
+        });
+    }
     if (c->opt.reduced == LRSPIKE_REDUCED_TRUNCATED) {
         const size_t smem = (2 * n2 * n2 + n2) * sizeof(double);
         cudaFuncSetAttribute(k_red_factor_trunc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

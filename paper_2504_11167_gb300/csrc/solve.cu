@@ -829,7 +829,8 @@ static bool retrieve_impl(Ctx *c, double *x, int64_t ld, int nrhs, int acc) {
         if (n2 <= 8) return retrieve1_nq<T, 8>(c, x, acc);
         if (n2 <= 16) return retrieve1_nq<T, 16>(c, x, acc);
         if (n2 <= 32) return retrieve1_nq<T, 32>(c, x, acc);
-        return retrieve1_nq<T, 64>(c, x, acc);
+        if (n2 <= 64) return retrieve1_nq<T, 64>(c, x, acc);
+        return retrieve1_nq<T, 128>(c, x, acc);
     }
     Parts P{c->off_d, c->boff_d, c->p};
     dim3 grid(row_blocks(c->maxni), c->p);

@@ -119,3 +119,20 @@ def test_wide_convection_diffusion_bicgstab(torch_cuda, precision):
     assert info["converged"]
     res = np.asarray(f) - O.band_matvec(ab, k, x)
     assert (np.linalg.norm(res, axis=0) / np.linalg.norm(f, axis=0)).max() <= 1.01e-10
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_wide_rank64(torch_cuda, precision):
+    """r = 64 (reduced-system blocks of 128 x 128, inverted in place; sketches
+    of ell = 128 columns): one application within the tensor-core bound of the
+    FP64 oracle, and the refinement to 1e-10."""
+    n, k, p, r = 20000, 192, 4, 64
+    ab = inputs.dominant_band(n, k, 1.2, 41)
+    f = inputs.rhs(n, 1, 41)
+    fac = O.factor(ab, k, p, r, reduced="truncated", threads=p)
+    got, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced="truncated", outer="none", precision=precision)
+    assert rel(got, O.apply(fac, np.asarray(f))) <= (2e-3 if precision == "tf32" else 3e-2)
+    x, info = gpu_solve(torch_cuda, ab, f, k, p, r, reduced="truncated", precision=precision, tol=1e-10)
+    assert info["converged"]
+    res = np.asarray(f) - O.band_matvec(ab, k, x)
+    assert np.linalg.norm(res) / np.linalg.norm(f) <= 1.01e-10
