@@ -20,13 +20,20 @@ Also on the same band: the weakly dominant variant (diagonal rescaled to
 dominance 0.6) with partial pivoting inside the partitions, and LR-SPIKE-OTF
 (the true reduced system solved by BiCGStab with on-the-fly spike products,
 preconditioned by the truncated low-rank system), reported under "variants";
-and the sparse-in-band PDE configuration: 2-D convection-diffusion
-on a 1024 x 1024 grid (n = 1,048,576, half-bandwidth 1024, cell Peclet number
-0.5), p = 64, r = 16, 4 right-hand sides, TF32 tensor-core factors with FP64
-BiCGStab to 1e-10 (iterative refinement stalls on it); and 512 independent
-systems of uneven n (log-uniform in [4096, 262144]) and k (8, 16, 32, 64),
-r = k/4, dominance 1.5, solved by one CUDA-graph launch with default and with
-autotuned partition / block shapes.
+the grid r in {8, 16, 32} x right-hand sides in {1, 16} x FP32 / TF32 of the
+same configuration; the plain FP64 configuration (n = 65,536, k = 16, p = 8,
+r = 4, IR to 1e-12); the sparse-in-band PDE configuration: 2-D
+convection-diffusion on a 1024 x 1024 grid (n = 1,048,576, half-bandwidth
+1024, cell Peclet number 0.5), p = 64, r in {16, 32, 64}, 4 right-hand sides,
+TF32 or BF16 tensor-core block products with FP64 BiCGStab to 1e-10
+(iterative refinement stalls on it), with the rooflines of the tensor-core
+products and of the D-stage; the differentiable solve (n = 1,048,576, k = 32,
+p = 128, r = 8, FP64, forward + backward); and 512 independent systems of
+uneven n (log-uniform in [4096, 262144]) and k (8, 16, 32, 64), r = k/4,
+dominance 1.5, solved by one CUDA-graph launch with default and with
+autotuned partition / block shapes.  The FP64 residual's roofline divides by
+the FP64 FMA rate measured by a probe kernel; the CPU baseline also reports
+the oracle on one thread and LAPACK's banded solve (scipy.solve_banded).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        python bench.py --profile-case   (one factor + solve at n = 1,048,576,
@@ -97,6 +104,23 @@ def cpu_sample(parts: int, threads: int):
     dt = time.perf_counter() - t0
     assert res.converged, res.rel_residual
     return n * NRHS / dt, dt, n, res.iterations
+
+
+def lapack_banded_rate(parts: int):
+    """scipy.linalg.solve_banded (LAPACK gbsv: band LU with partial pivoting
+    and the solve, p = 1, exact) on the same sample band, as a library CPU
+    reference for the plain banded solve."""
+    import scipy.linalg
+    from paper_2504_11167_gb300 import inputs
+    n = parts * (N // P)
+    seed = inputs.SEED_BASE + 2
+    ab = inputs.dominant_band(n, K, DOM, seed)
+    f = np.ascontiguousarray(inputs.rhs(n, NRHS, seed))
+    t0 = time.perf_counter()
+    scipy.linalg.solve_banded((K, K), ab, f)
+    dt = time.perf_counter() - t0
+    return {"value": n * NRHS / dt, "unit": UNIT, "sample": f"n={n}, k={K}, one right-hand side: {dt:.2f} s",
+            "threads": "LAPACK as linked by scipy"}
 
 
 def reference_arm(args, rank):
@@ -219,18 +243,24 @@ def cd_band_device(nx: int, peclet: float, dev):
     return ab
 
 
-def cd_variant(steps: int, warmup: int, dev):
-    """Steps of factor + BiCGStab solve on the convection-diffusion workload."""
+def cd_algorithmic_flops(n: int, k: int, r: int, q: int = 2):
+    """Algorithmic flops of the block products of one wide-band factorisation
+    (the sizes of the convection-diffusion workload): band LU 2 n k^2, the two
+    spikes 6 n k^2, and the randomized truncation, 2 + 2 q products of
+    2 n k ell per spike over two spikes (ell = 2 r)."""
+    ell = min(k, 2 * r)
+    return 2.0 * n * k * k + 6.0 * n * k * k + 2 * (2 + 2 * q) * 2.0 * n * k * ell
+
+
+def cd_variant(band, f, precision: str, r: int, steps: int, warmup: int, dev, peaks: dict):
+    """Steps of factor + BiCGStab solve on the convection-diffusion workload,
+    with the event-timed tensor-core products and D-stage reported against
+    their rooflines."""
     import torch
-    from paper_2504_11167_gb300 import inputs
     from paper_2504_11167_gb300.solver import LRSpike
-    small = cd_band_device(12, 0.5, dev).cpu().numpy()
-    assert np.array_equal(small, inputs.convection_diffusion_band(12, 0.5))
-    nx, p, r, nrhs = 1024, 64, 16, 4
-    n, k = nx * nx, nx
-    band = cd_band_device(nx, 0.5, dev)
-    f = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, nrhs, inputs.SEED_BASE + 3).T)).to(dev)
-    s = LRSpike(n, k, p, r, precision="tf32", reduced="truncated", outer="bicgstab", tol=TOL, max_iter=200,
+    nx, p = 1024, 64
+    n, k, nrhs = nx * nx, nx, f.shape[0]
+    s = LRSpike(n, k, p, r, precision=precision, reduced="truncated", outer="bicgstab", tol=TOL, max_iter=300,
                 max_nrhs=nrhs, profile=True)
     for _ in range(warmup):
         s.factor(band)
@@ -248,13 +278,129 @@ def cd_variant(steps: int, warmup: int, dev):
     ms = e0.elapsed_time(e1) / steps
     prof = s.profile()
     s.close()
+    tc_cnt, tc_ms = prof.get("wide_gemm_tc", (0, 0.0))
+    ds_cnt, ds_ms = prof.get("wide_dstage", (0, 0.0))
+    roof = {}
+    if tc_cnt:
+        # TF32 takes half the BF16 rate (the tensor cores' nominal ratio)
+        pk = peaks.get("bf16_tflops_sustained", 1688.4) * (0.5 if precision == "tf32" else 1.0)
+        ach = cd_algorithmic_flops(n, k, r) * steps / (tc_ms * 1e-3) / 1e12
+        roof["tensor_core_products"] = {
+            "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "peak_source": "measured bf16_tflops_sustained" + (" x 0.5 (TF32/BF16 nominal ratio)"
+                                                                 if precision == "tf32" else ""),
+            "work": "algorithmic: band LU 2nk^2 + spikes 6nk^2 + randomized truncation, per factorisation"}
+    if ds_cnt:
+        # nonzero triangles of the four W x W factor tiles per block step, FP32
+        W, NBW = 1024, 16
+        bytes_per = 4 * (W * (W + 1) // 2) * 4 * NBW * p + n * nrhs * 4 * 4
+        ach = bytes_per / (ds_ms / ds_cnt * 1e-3) / 1e9
+        pk = peaks.get("hbm_gbs", 6800.0)
+        roof["dstage"] = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+                          "peak_source": "measured hbm_gbs",
+                          "work": "nonzero triangles of L_JJ^-1, U_JJ^-1, Z_J, Y_J + vectors, per application"}
+    return {"value": n * nrhs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "iterations": info["iterations"],
+            "rel_residual": info["max_rel_residual"], "roofline": roof,
+            "config": {"workload": "2-D convection-diffusion 1024x1024, Pe 0.5", "n": n, "k": k, "p": p, "r": r,
+                       "nrhs": nrhs, "precision": precision, "outer": "bicgstab", "reduced": "truncated",
+                       "tol": TOL},
+            "kernels": {k_: {"launches": c_, "ms_total": round(t_, 3)} for k_, (c_, t_) in prof.items() if c_}}
+
+
+def cd_variants(dev, peaks: dict, steps=2, warmup=1):
+    """The convection-diffusion configuration in TF32 and BF16 operands at
+    r = 16, 32, 64 (4 right-hand sides, BiCGStab to 1e-10)."""
+    import torch
+    from paper_2504_11167_gb300 import inputs
+    small = cd_band_device(12, 0.5, dev).cpu().numpy()
+    assert np.array_equal(small, inputs.convection_diffusion_band(12, 0.5))
+    nx, nrhs = 1024, 4
+    band = cd_band_device(nx, 0.5, dev)
+    f = torch.from_numpy(np.ascontiguousarray(inputs.rhs(nx * nx, nrhs, inputs.SEED_BASE + 3).T)).to(dev)
+    out = {}
+    for precision in ("tf32", "bf16"):
+        for r in (16, 32, 64):
+            out[f"{precision}_r{r}"] = cd_variant(band, f, precision, r, steps, warmup, dev, peaks)
     del band, f
     torch.cuda.empty_cache()
-    return {"value": n * nrhs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "iterations": info["iterations"],
-            "rel_residual": info["max_rel_residual"],
-            "config": {"workload": "2-D convection-diffusion 1024x1024, Pe 0.5", "n": n, "k": k, "p": p, "r": r,
-                       "nrhs": nrhs, "precision": "tf32", "outer": "bicgstab", "reduced": "truncated", "tol": TOL},
-            "kernels": {k_: {"launches": c_, "ms_total": round(t_, 3)} for k_, (c_, t_) in prof.items() if c_}}
+    return out
+
+
+def config1_variant(dev, steps=5, warmup=3):
+    """The plain FP64 configuration: n = 65,536, k = 16, p = 8, r = 4,
+    dominance 1.5, one right-hand side, IR to 1e-12; both reduced systems."""
+    import torch
+    from paper_2504_11167_gb300 import inputs
+    from paper_2504_11167_gb300.solver import LRSpike
+    n, k, p, r = 65536, 16, 8, 4
+    seed = inputs.SEED_BASE + 1
+    band = torch.from_numpy(inputs.dominant_band(n, k, 1.5, seed)).to(dev)
+    f = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, 1, seed).T)).to(dev)
+    out = {}
+    for reduced in ("full", "truncated"):
+        s = LRSpike(n, k, p, r, precision="fp64", reduced=reduced, tol=1e-12)
+        for _ in range(warmup):
+            s.factor(band)
+            s.solve(f)
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            s.factor(band)
+            x, info = s.solve(f)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        s.close()
+        out[reduced] = {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "iterations": info["iterations"],
+                        "rel_residual": info["max_rel_residual"],
+                        "config": {"workload": "plain FP64 banded n=65536 k=16 p=8 r=4 dominance=1.5",
+                                   "precision": "fp64", "reduced": reduced, "tol": 1e-12}}
+    return out
+
+
+def autograd_variant(dev, steps=3, warmup=1):
+    """The differentiable solve: x = A(theta)^{-1} f, n = 1,048,576, k = 32,
+    p = 128, r = 8, FP64, L = 0.5 |x - x*|^2; one step = forward (factor +
+    solve) and backward (adjoint solve with the stored factors + band
+    gradient -lambda x^T)."""
+    import torch
+    from paper_2504_11167_gb300 import autograd, inputs
+    n, k, p, r = 1048576, 32, 128, 8
+    seed = inputs.SEED_BASE + 5
+    band = inputs.dominant_band_torch(n, k, 1.5, seed, device=dev).requires_grad_(True)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed + 1)
+    f = (torch.rand(1, n, generator=g, dtype=torch.float64, device=dev) * 2 - 1).requires_grad_(True)
+    xs = torch.rand(1, n, generator=g, dtype=torch.float64, device=dev) * 2 - 1
+
+    def step():
+        x = autograd.solve(band, f, k, p, r, precision="fp64", reduced="truncated", tol=1e-12)
+        loss = 0.5 * ((x - xs) ** 2).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(warmup):
+        step()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        band.grad = None
+        f.grad = None
+        loss = step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    ok = bool(torch.isfinite(band.grad).all().item()) and bool(torch.isfinite(f.grad).all().item())
+    del band, f, xs
+    torch.cuda.empty_cache()
+    return {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "loss": float(loss.item()),
+            "finite_gradients": ok,
+            "config": {"workload": "differentiable solve n=1048576 k=32 p=128 r=8 FP64, forward + backward",
+                       "precision": "fp64", "reduced": "truncated", "tol": 1e-12}}
 
 
 def batch_variant(dev, systems_count=512, steps=3, iterations=10):
@@ -317,6 +463,15 @@ def batch_variant(dev, systems_count=512, steps=3, iterations=10):
                                    "k in {8,16,32,64}, r = k/4, dominance 1.5",
                        "unknowns": total, "precision": "fp32", "refinement_steps": iterations,
                        "graph": "one CUDA graph per batch (factor + solve of every system)"}}
+
+
+def fp64_peak_measured():
+    """FP64 FMA rate of this GPU (TFLOP/s): the best of three probe runs."""
+    try:
+        from paper_2504_11167_gb300.solver import fp64_fma_tflops
+        return max(fp64_fma_tflops(1 << 16) for _ in range(3))
+    except Exception:  # reported as a derived peak by the caller
+        return None
 
 
 def whole_job_rate(ms_local: float, units_per_rank: float, world: int, dev=None):
@@ -393,13 +548,15 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def run(precision, steps, warmup, profile, A=None, pivoting=False, compress=COMPRESS, reduced="truncated"):
+    def run(precision, steps, warmup, profile, A=None, pivoting=False, compress=COMPRESS, reduced="truncated",
+            r=R, F=None):
         A = band if A is None else A
-        s = LRSpike(N, K, P, R, precision=precision, reduced=reduced, tol=TOL, max_nrhs=NRHS,
+        F = ft if F is None else F
+        s = LRSpike(N, K, P, r, precision=precision, reduced=reduced, tol=TOL, max_nrhs=F.shape[0],
                     profile=profile, pivoting=pivoting, compress=compress)
         for _ in range(warmup):
             s.factor(A)
-            s.solve(ft)
+            s.solve(F)
         s.profile_reset()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -409,7 +566,7 @@ def main():
             l0 = s.launch_count()
             for _ in range(steps):
                 s.factor(A)
-                x, info = s.solve(ft)
+                x, info = s.solve(F)
             e1.record(stream)
             barrier()
         ms = e0.elapsed_time(e1) / steps
@@ -453,11 +610,14 @@ def main():
             # the first launch of each solve starts from x = 0 and skips the band:
             # the work counted is that of the other launches, the time that of all
             busy = max(cnt - args.steps, 1)
-            fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12           # 2 FP64 FMA per SM per clock (1.25 TFLOP/s nominal)
+            fp64_peak, src = fp64_peak_measured(), "measured: FP64 FMA probe kernel (lrspike_fp64_fma_probe)"
+            if not fp64_peak:
+                fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+                src = "derived FP64: 152 SMs x 2 FMA x 2 x 2.07 GHz (the probe failed)"
             ach = busy * work / (tot * 1e-3) / 1e12
             roofline = {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak,
                         "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": NCU_TRAFFIC.get(name),
-                        "peak_source": "derived FP64: 152 SMs x 2 FMA x 2 x 2.07 GHz (GB300 nominal 1.25 TFLOP/s)"}
+                        "peak_source": src}
         elif bound == "alu":
             alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # FP32 FMA lanes x clock
             ach = work / per_launch_s / 1e12
@@ -500,8 +660,25 @@ def main():
             "rel_residual": infoo["max_rel_residual"],
             "reduced": "LR-SPIKE-OTF: reduced BiCGStab to 1e-8 per outer step, S~~_r preconditioner",
             "kernels": {k_: {"launches": c_, "ms_total": round(t_, 4)} for k_, (c_, t_) in profo.items() if c_}}
+        # the large banded configuration's grid: rank x right-hand sides x precision
+        f16 = torch.from_numpy(np.ascontiguousarray(inputs.rhs(N, 16, seed).T)).to(dev)
+        grid = {}
+        for precision in ("fp32", "tf32"):
+            for r in (8, 16, 32):
+                for nrhs, F in ((1, ft), (16, f16)):
+                    msg, _, _, infog, _, _ = run(precision, 2, 1, False, r=r, F=F)
+                    grid[f"{precision}_r{r}_nrhs{nrhs}"] = {
+                        "value": N * nrhs / (msg * 1e-3), "unit": UNIT, "ms_per_step": msg,
+                        "iterations": infog["iterations"], "rel_residual": infog["max_rel_residual"]}
+        variants["banded_grid_r_nrhs_precision"] = {
+            "config": {"workload": WORKLOAD.replace("r=16 nrhs=1", "r in {8,16,32} nrhs in {1,16}"),
+                       "compress": COMPRESS, "reduced": "truncated", "outer": "ir", "tol": TOL},
+            "points": grid}
+        del f16
         torch.cuda.empty_cache()
-        variants["convection_diffusion_k1024"] = cd_variant(2, 1, dev)
+        variants["plain_fp64_n65536_k16"] = config1_variant(dev)
+        variants["convection_diffusion_k1024"] = cd_variants(dev, peaks)
+        variants["differentiable_solve_n1048576_k32"] = autograd_variant(dev)
         variants["batched_512_uneven_systems"] = batch_variant(dev)
 
     # end to end through the C ABI with host buffers
@@ -536,6 +713,10 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{parts} partitions of the workload geometry (n={n_s}, k={K}, r={R}), "
                          f"factor + IR to {TOL}: {dt:.1f} s"}
+        v1, dt1, n1, _ = cpu_sample(4, 1)
+        cpu["one_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
+                             "sample": f"4 partitions (n={n1}), factor + IR to {TOL}: {dt1:.1f} s"}
+        cpu["lapack_solve_banded"] = lapack_banded_rate(parts)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -287,6 +287,16 @@ lrspike_status lrspike_band_outer(const double *lam, const double *x, int32_t nr
                                   int32_t k, double alpha, double *grad_band, int64_t ld_band,
                                   void *cuda_stream);
 
+/* ---- FP64 rate of the current GPU ------------------------------------------
+ * The paper has no counterpart to this entry point; it measures what bounds
+ * the FP64 residual r = f - A x (one FMA per band entry) on GPUs whose FP64
+ * units are scarce.  One kernel of independent FMA chains on every SM, iters
+ * iterations of 16 chains per thread, timed with CUDA events on cuda_stream
+ * (NULL = legacy default stream); the call waits for it.  *tflops receives
+ * 2 x FMAs / elapsed time in TFLOP/s.  Errors (INVALID_ARG for iters < 1 or
+ * a NULL output, CUDA) are described by lrspike_last_error(NULL). */
+lrspike_status lrspike_fp64_fma_probe(int64_t iters, double *tflops, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

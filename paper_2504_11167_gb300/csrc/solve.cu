@@ -514,8 +514,11 @@ __global__ void __launch_bounds__(Geo<KB>::NT, 2)
         dstage_body<T, KB, Split::COLS, NBUF>(LT, UT, DI, PQ, P, k, r, n, rin, inv, nrhs, Yv, Gv, psi, smem_raw);
 }
 
-// x (+)= nrm * (g - u_T zeta - u_W omega) for one partition's rows.
-template <typename T>
+// x (+)= nrm * (g - u_T zeta - u_W omega) for one partition's rows.  Each
+// thread reads its row of u once and updates all NC (>= nrhs) columns in
+// registers; per column the expression is the same as in the one-column
+// form (d -= u_j z_j + u_j+1 z_j+1 + ...), so the rounding is unchanged.
+template <typename T, int NC>
 __global__ void __launch_bounds__(RBS)
     k_retrieve(const T *__restrict__ Gv, const T *__restrict__ Ucat, const double *__restrict__ zr,
                Parts P, int r, int64_t n, int nrhs, const double *__restrict__ nrm, double *__restrict__ x,
@@ -535,22 +538,34 @@ __global__ void __launch_bounds__(RBS)
     const int64_t row = blockIdx.x * (int64_t)RBS + threadIdx.x;
     if (row >= ni) return;
     const int64_t gi = s + row;
-    for (int c = 0; c < nrhs; ++c) {
-        T d = Gv[c * n + gi];
-        const T *u = Ucat + gi * n2;
-        int j = 0;
-        if constexpr (sizeof(T) == 4) {
-            if ((n2 & 3) == 0)
-                for (; j < n2; j += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(u + j);
-                    d -= v.x * (T)zs[j * nrhs + c] + v.y * (T)zs[(j + 1) * nrhs + c] +
-                         v.z * (T)zs[(j + 2) * nrhs + c] + v.w * (T)zs[(j + 3) * nrhs + c];
-                }
-        }
-        for (; j < n2; ++j) d -= u[j] * (T)zs[j * nrhs + c];
-        const double upd = nrm[c] * (double)d;
-        x[c * ld + gi] = accumulate ? x[c * ld + gi] + upd : upd;
+    T d[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) d[c] = (c < nrhs) ? Gv[c * n + gi] : T(0);
+    const T *u = Ucat + gi * n2;
+    int j = 0;
+    if constexpr (sizeof(T) == 4) {
+        if ((n2 & 3) == 0)
+            for (; j < n2; j += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(u + j);
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (c < nrhs)
+                        d[c] -= v.x * (T)zs[j * nrhs + c] + v.y * (T)zs[(j + 1) * nrhs + c] +
+                                v.z * (T)zs[(j + 2) * nrhs + c] + v.w * (T)zs[(j + 3) * nrhs + c];
+            }
     }
+    for (; j < n2; ++j) {
+        const T uj = u[j];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (c < nrhs) d[c] -= uj * (T)zs[j * nrhs + c];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+        if (c < nrhs) {
+            const double upd = nrm[c] * (double)d[c];
+            x[c * ld + gi] = accumulate ? x[c * ld + gi] + upd : upd;
+        }
 }
 
 // One right-hand side: zeta and omega of the partition (2r <= NQ values) sit
@@ -836,8 +851,15 @@ static bool retrieve_impl(Ctx *c, double *x, int64_t ld, int nrhs, int acc) {
     dim3 grid(row_blocks(c->maxni), c->p);
     const size_t smem = (size_t)(2 * c->r * nrhs + 1) * sizeof(double);
     return launch(c, KID_RETRIEVE, [&] {
-        k_retrieve<T><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r,
-                                                     c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc);
+        if (nrhs <= 4)
+            k_retrieve<T, 4><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r,
+                                                            c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc);
+        else if (nrhs <= 8)
+            k_retrieve<T, 8><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r,
+                                                            c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc);
+        else
+            k_retrieve<T, 16><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P,
+                                                             c->r, c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc);
     });
 }
 

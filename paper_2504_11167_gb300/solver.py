@@ -56,7 +56,8 @@ _lib = None
 EXPORTS = ["lrspike_options_default", "lrspike_create", "lrspike_factor", "lrspike_solve",
            "lrspike_solve_transpose", "lrspike_destroy", "lrspike_last_error",
            "lrspike_launch_count", "lrspike_profile_get", "lrspike_profile_reset",
-           "lrspike_get_reduced", "lrspike_residual_noalloc", "lrspike_band_outer", "lrspike_finish"]
+           "lrspike_get_reduced", "lrspike_residual_noalloc", "lrspike_band_outer", "lrspike_finish",
+           "lrspike_fp64_fma_probe"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.lrspike_band_outer.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                                         ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                         ctypes.c_int64, ctypes.c_void_p]
+    lib.lrspike_fp64_fma_probe.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     for name in EXPORTS:
         if name not in ("lrspike_last_error", "lrspike_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
@@ -138,6 +140,20 @@ def residual_noalloc(band, k: int, f, x, r, norms, stream=None) -> None:
                                       ctypes.c_void_p(stream.cuda_stream))
     if st != 0:
         raise LRSpikeError(st, lib.lrspike_last_error(None).decode(errors="replace"))
+
+
+def fp64_fma_tflops(iters: int = 1 << 16, stream=None) -> float:
+    """Measured FP64 FMA rate of the current GPU in TFLOP/s (one probe
+    kernel timed with CUDA events on ``stream``, default torch's current)."""
+    import torch
+    lib = load_library()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = ctypes.c_double(0.0)
+    st = lib.lrspike_fp64_fma_probe(int(iters), ctypes.byref(out), ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise LRSpikeError(st, lib.lrspike_last_error(None).decode(errors="replace"))
+    return float(out.value)
 
 
 def band_outer(lam, x, k: int, alpha: float, grad_band, stream=None) -> None:

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "lrspike.h")).read()
-    return sorted(set(re.findall(r"\b(lrspike_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lrspike_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +51,10 @@ def test_defaults(lib):
     dict(n=20000, k=100, r=8, pivoting=1),                 # wide bands: no pivoting
     dict(n=20000, k=100, r=8, compress=1),                 # wide bands: SPIKE compression only
     dict(n=20000, k=100, r=8, oversample=60),              # more than 64 sketch columns
-    dict(n=20000, k=100, r=33),                            # r > 32
+    dict(n=20000, k=100, r=33),                            # r > 32 with the FULL reduced system
+    dict(n=20000, k=100, r=65, reduced=1, precision=2),    # r > 64
+    dict(n=20000, k=200, r=16, oversample=120, precision=2),  # more than 128 sketch columns (mixed)
+    dict(precision=3),                                     # BF16 operands: wide bands only
     dict(reduced=2, pivoting=1),                           # OTF: no pivoting
     dict(reduced=2, outer=1),                              # OTF: outer IR or NONE
     dict(reduced=2, graph_safe=1),                         # OTF: not graph_safe
@@ -107,3 +110,9 @@ def test_missing_library_raises(tmp_path, monkeypatch):
     monkeypatch.setattr(solver, "_lib", None)
     with pytest.raises(solver.LRSpikeError):
         solver.load_library(str(tmp_path / "nope.so"))
+
+
+def test_fp64_probe_rejects_bad_arguments(lib):
+    out = ctypes.c_double(0.0)
+    assert lib.lrspike_fp64_fma_probe(0, ctypes.byref(out), None) == 1
+    assert lib.lrspike_fp64_fma_probe(100, None, None) == 1
