@@ -260,12 +260,13 @@ def cd_variant(band, f, precision: str, r: int, steps: int, warmup: int, dev, pe
     from paper_2504_11167_gb300.solver import LRSpike
     nx, p = 1024, 64
     n, k, nrhs = nx * nx, nx, f.shape[0]
+    # timed without per-kernel events (the factorisation then replays as one
+    # CUDA graph); the kernel breakdown comes from one profiled step after
     s = LRSpike(n, k, p, r, precision=precision, reduced="truncated", outer="bicgstab", tol=TOL, max_iter=300,
-                max_nrhs=nrhs, profile=True)
+                max_nrhs=nrhs)
     for _ in range(warmup):
         s.factor(band)
         s.solve(f)
-    s.profile_reset()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(dev)
@@ -276,8 +277,18 @@ def cd_variant(band, f, precision: str, r: int, steps: int, warmup: int, dev, pe
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
+    launches = s.launch_count()
+    s.close()
+    s = LRSpike(n, k, p, r, precision=precision, reduced="truncated", outer="bicgstab", tol=TOL, max_iter=300,
+                max_nrhs=nrhs, profile=True)
+    s.factor(band)
+    s.solve(f)
+    s.profile_reset()
+    s.factor(band)
+    s.solve(f)
     prof = s.profile()
     s.close()
+    steps = 1  # the profile covers one step
     tc_cnt, tc_ms = prof.get("wide_gemm_tc", (0, 0.0))
     ds_cnt, ds_ms = prof.get("wide_dstage", (0, 0.0))
     roof = {}

@@ -133,12 +133,15 @@ struct Ctx {
     // block-step work [p][W x W] (layouts f, fr, oc, orow): Schur complement,
     // A_{J,J+1}, A_{J+1,J}, recursion temporary
     void *WSm[4] = {}, *WBm[4] = {}, *WCm[4] = {}, *WTm[4] = {};
-    void *WX1 = nullptr, *WX2 = nullptr;    // spike panels [p][PS x 2W], working precision
-    void *WX1c = nullptr, *WX2c = nullptr;  // operand-type copies (BF16 only)
-    void *WXr = nullptr;                    // operand-type row-major final spikes [p][2][PS][W]
+    // randomized truncation without explicit spikes: the range finder's
+    // products T X = A_i^{-1}[0; B_i X] and T^T Q = [0; B_i]^T A_i^{-T} Q are
+    // block solves on panels of 2 lp columns (T side, W side)
+    void *WCpl[4] = {};                     // coupling tiles B_i / C_i [2p][W x W] (layouts f, fr, oc, orow)
+    void *WP1 = nullptr, *WP2 = nullptr;    // solve panels [p][PS x 2lp], working precision
+    void *WP1c = nullptr, *WP2c = nullptr;  // their operand-type copies (BF16 only)
+    void *WTip = nullptr, *WTipc = nullptr; // panel tips [2p][W x lp] (working / operand BF16)
     void *WOm = nullptr;                    // sketches [2p][W x lp] (operand type)
-    void *WYk = nullptr, *WQk = nullptr;    // [2p][PS x lp]: range basis iterates (working)
-    void *WQc = nullptr;                    // operand-type copy of the basis (BF16 only)
+    void *WQk = nullptr;                    // [2p][PS x lp]: orthonormal range basis (working)
     void *WZk = nullptr, *WZc = nullptr;    // [2p][W x lp]: T^T Q (working / operand BF16)
     void *WG = nullptr;                     // [2p][lp x lp] Gram (working)
     double *WGd = nullptr;                  // [2p][lp x lp] FP64 Gram
@@ -146,6 +149,14 @@ struct Ctx {
     void *WE = nullptr;                     // [2p][r][lp] leading eigenvectors
     void *WV1 = nullptr, *WV2 = nullptr;    // vector panels [p][PS x 16]
     int *gemm_err = nullptr;                // tensor-core GEMM wait-limit flag
+    // the device work of a wide-band factorisation, captured once into a CUDA
+    // graph (on a private stream) and replayed while the band's address and
+    // leading dimension stay the same; not used when profiling
+    cudaStream_t wcap = nullptr;
+    cudaGraphExec_t wgraph = nullptr;
+    const double *wgraph_band = nullptr;
+    int64_t wgraph_ld = 0, wgraph_launches = 0;
+    bool wgraph_failed = false;  // capture refused: launches run eagerly
     int *diag_list = nullptr;              // band rows holding a nonzero (residual), or NULL
     int ndiag = 0;
 

@@ -13,10 +13,11 @@
 //     S_J = A_JJ - Y_{J-1} Z_{J-1};  S_J = L U with L^{-1}, U^{-1} by recursive
 //     halving (64 x 64 base blocks in k_lu_inv64);
 //     Z_J = L_JJ^{-1} A_{J,J+1} (= U_{J,J+1}),  Y_J = A_{J+1,J} U_JJ^{-1} (= L_{J+1,J})
-//   spikes [T_i | W_i] = A_i^{-1} [[0; B_i] | [C_i; 0]] (eq. 'Veqn') by the
-//     forward and backward block recurrences on a 2W-column panel
 //   compression: the randomized SVD the paper uses for wide bands (section
-//     3.1, Halko-Martinsson-Tropp proto-algorithm) on each spike T:
+//     3.1, Halko-Martinsson-Tropp proto-algorithm) on each spike
+//     T = A_i^{-1}[0; B_i] (eq. 'Veqn'; W_i = A_i^{-1}[C_i; 0] likewise),
+//     never formed: its products are block solves with the factors on panels
+//     of 2 lp columns, T X = A_i^{-1}[0; B_i X], T^T Q = B_i^T (A_i^{-T} Q)_bottom;
 //       Y = T Omega;  Q = orth(Y);  q times: Y = T (T^T Q), Q = orth(Y);
 //       B^T = T^T Q;  B B^T = U_B diag(sigma^2) U_B^T (cyclic Jacobi);
 //       u = Q U_B,r,  P = U_B,r^T B = sigma_r V_r^T.
@@ -28,8 +29,8 @@
 //     block recurrences (k_wide_dstage), reading only the nonzero triangles of
 //     the factor tiles.
 //
-// Layouts: W x W tiles [p][NBW][W x W]; panels [p][PS x cols] column-major with
-// PS = NBW W rows (leading dimension PS).  A matrix that is a left factor of a
+// Layouts: W x W tiles [p][NBW][W x W]; panels [p][PS x 2 lp] column-major
+// with PS = NBW W rows (leading dimension PS).  A matrix that is a left factor of a
 // tensor-core product is also kept row-major in the operand type, a right
 // factor column-major in the operand type (K-contiguous operands for the MMA);
 // the epilogue of the product that makes a matrix writes those copies.
@@ -297,6 +298,75 @@ __global__ void k_wide_spike_rhs(const double *__restrict__ band, int64_t ld, in
             X[xi] = (T)v;
             if (Xc) Xc[xi] = cvtd<O>(v);
         }
+    }
+}
+
+// Coupling blocks as W x W tiles, b = 2 i + side (zero beyond k and where the
+// block does not exist): side 0 B_i[a][b] = A[s_{i+1}-k+a][s_{i+1}+b]
+// (nonzero for b <= a, i < p-1), side 1 C_i[a][b] = A[s_i+a][s_i-k+b]
+// (nonzero for a <= b, i > 0).  Threads walk the band along its diagonals
+// (consecutive threads, consecutive band addresses); layouts as WMat.
+template <typename T, typename O>
+__global__ void k_wide_couple_gather(const double *__restrict__ band, int64_t ld, int k, Parts P, int W, T *f,
+                                     O *oc, O *orow) {
+    const int b = blockIdx.y, part = b / 2, side = b % 2;
+    const bool live = side == 0 ? (part < P.p - 1) : (part > 0);
+    const int64_t tile = (int64_t)b * W * W;
+    const int64_t s = P.off[part], sn = P.off[part + 1];
+    // entry e: diagonal d = e / k (0..k-1), position q = e % k
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * k;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(e / k), q = (int)(e % k);
+        int a, c;
+        double v = 0.0;
+        if (side == 0) {  // a - c = d >= 0
+            c = q;
+            a = q + d;
+            if (a < k && live) v = band[(int64_t)d * ld + sn + c];
+        } else {          // c - a = d >= 0
+            a = q;
+            c = q + d;
+            if (c < k && live) v = band[(int64_t)(2 * k - d) * ld + s - k + c];
+        }
+        if (a >= k || c >= k) continue;
+        if (f) f[tile + a + (int64_t)c * W] = (T)v;
+        if (oc) oc[tile + a + (int64_t)c * W] = cvtd<O>(v);
+        if (orow) orow[tile + c + (int64_t)a * W] = cvtd<O>(v);
+    }
+}
+
+// Tips of the 2 lp-column panels [p][PS x 2lp] as [2p][W x lp] tiles: side 0
+// the last k rows of the first lp columns, side 1 the first k rows of the
+// last lp columns (rows k..W-1 zero).
+template <typename T, typename O>
+__global__ void k_tips_gather(const T *__restrict__ Pf, Parts P, int k, int W, int64_t PS, int lp, T *Xf, O *Xoc) {
+    const int b = blockIdx.y, part = b / 2, side = b % 2;
+    const int64_t ni = P.off[part + 1] - P.off[part];
+    const T *pan = Pf + (int64_t)part * PS * 2 * lp;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < W * lp; e += gridDim.x * blockDim.x) {
+        const int a = e % W, j = e / W;
+        T v = T(0);
+        if (a < k) v = side == 0 ? pan[(ni - k + a) + (int64_t)j * PS] : pan[a + (int64_t)(lp + j) * PS];
+        Xf[(int64_t)b * W * lp + e] = v;
+        if (Xoc) Xoc[(int64_t)b * W * lp + e] = cvtd<O>((double)v);
+    }
+}
+
+// The reverse: [2p][W x lp] (first k rows) into the zeroed panels, side 0 at
+// rows n_i-k.. of the first lp columns, side 1 at rows 0.. of the last lp
+// (only where the spike exists).
+template <typename T, typename O>
+__global__ void k_tips_scatter(const T *__restrict__ Xf, Parts P, int k, int W, int64_t PS, int lp, T *Pf, O *Poc) {
+    const int b = blockIdx.y, part = b / 2, side = b % 2;
+    if (side == 0 ? part >= P.p - 1 : part == 0) return;
+    const int64_t ni = P.off[part + 1] - P.off[part];
+    const int64_t base = (int64_t)part * PS * 2 * lp;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * lp; e += gridDim.x * blockDim.x) {
+        const int a = e % k, j = e / k;
+        const T v = Xf[(int64_t)b * W * lp + a + (int64_t)j * W];
+        const int64_t pi = base + (side == 0 ? (ni - k + a) + (int64_t)j * PS : a + (int64_t)(lp + j) * PS);
+        Pf[pi] = v;
+        if (Poc) Poc[pi] = cvtd<O>((double)v);
     }
 }
 
@@ -1094,9 +1164,12 @@ bool cholqr3(Ctx *c, void *Y, void *Qout) {
 }
 
 template <typename T>
+bool wide_compress_t(Ctx *c);
+
+template <typename T>
 bool wide_factor_t(Ctx *c) {
     const int W = c->W, NB = c->NBW, p = c->p;
-    const int64_t WW = (int64_t)W * W, sF = NB * WW, PS = c->PS;
+    const int64_t WW = (int64_t)W * W, sF = NB * WW;
     const bool tc = c->gpath != 0, bf = c->gpath == 2;
     Parts P{c->off_d, c->boff_d, p};
     if (cudaMemsetAsync(c->gemm_err, 0, sizeof(int), c->stream) != cudaSuccess) {
@@ -1146,85 +1219,132 @@ bool wide_factor_t(Ctx *c) {
     }
     if (p < 2 || c->r == 0) return true;
 
-    // spikes [T | W] on the panel X1 (forward results in X2, solution back in X1)
-    const int64_t sX = PS * 2 * W;
-    const size_t panel = (size_t)p * sX;
-    for (void *q : {c->WX1, c->WX2})
-        if (cudaMemsetAsync(q, 0, panel * c->tsize, c->stream) != cudaSuccess) return false;
-    for (void *q : {c->WX1c, c->WX2c})
-        if (q && cudaMemsetAsync(q, 0, panel * c->osize, c->stream) != cudaSuccess) return false;
-    if (!launch(c, KID_SPIKE_RHS, [&] {
-            if (bf)
-                k_wide_spike_rhs<float, __nv_bfloat16><<<p, 256, 0, c->stream>>>(
-                    c->band, c->ld, c->k, P, W, PS, (float *)c->WX1, (__nv_bfloat16 *)c->WX1c);
-            else
-                k_wide_spike_rhs<T, T><<<p, 256, 0, c->stream>>>(c->band, c->ld, c->k, P, W, PS, (T *)c->WX1,
-                                                                 nullptr);
-        }))
-        return false;
-    // panel views: column-major PS x 2W (operand copy for BF16), rows of block J
-    auto pan = [&](void *f, void *oc, int64_t col0, int64_t J) {
+    return wide_compress_t<T>(c);
+}
+
+// Rank-r truncation of every spike by the HMT proto-algorithm (section 3.1)
+// without forming the spikes: with T = A_i^{-1}[0; B_i] and W = A_i^{-1}[C_i; 0]
+// every product the range finder needs is a block solve with the factors on
+// a panel of 2 lp columns (T side, W side):
+//   T X   = A_i^{-1} [0; B_i X],        W X   = A_i^{-1} [C_i X; 0]
+//   T^T Q = B_i^T (A_i^{-T} Q)_bottom,   W^T Q = C_i^T (A_i^{-T} Q)_top
+// Y = T Omega, Q = orth(Y); q times Y = T (T^T Q), Q = orth(Y); B^T = T^T Q;
+// then the eigenvectors U_B of B B^T, u = Q U_B,r and P = U_B,r^T B as before.
+template <typename T>
+bool wide_compress_t(Ctx *c) {
+    const int W = c->W, NB = c->NBW, p = c->p, lp = c->lp, ell = c->ell, r = c->r, nm = 2 * p;
+    const int64_t WW = (int64_t)W * W, sF = NB * WW, PS = c->PS, sP = PS * 2 * lp, sQ = PS * lp,
+                  sZ = (int64_t)W * lp;
+    const bool tc = c->gpath != 0, bf = c->gpath == 2;
+    const size_t tz = c->tsize, oz = c->osize;
+    Parts P{c->off_d, c->boff_d, p};
+    auto tile = [&](int kind, int J) {
+        return WMat{elem(c->WF[kind], J * WW, tz), elem(c->WFr[kind], J * WW, tz), elem(c->WFoc[kind], J * WW, oz),
+                    elem(c->WFor[kind], J * WW, oz), W, sF, W, sF};
+    };
+    // panel rows of block J (both sides), column-major PS x 2lp
+    auto pv = [&](void *f, void *oc, int64_t J) {
         WMat m;
-        m.f = elem(f, col0 * PS + J * W, c->tsize);
-        m.oc = bf ? elem(oc, col0 * PS + J * W, c->osize) : m.f;
+        m.f = elem(f, J * W, tz);
+        m.oc = bf ? elem(oc, J * W, oz) : m.f;
         m.ld = PS;
-        m.s = sX;
+        m.s = sP;
         return m;
     };
-    // the T columns are zero above the block holding the first row of B_i
-    int64_t jt0 = NB;
-    for (int i = 0; i < p; ++i) jt0 = std::min<int64_t>(jt0, (c->off_h[i + 1] - c->off_h[i] - c->k) / W);
-    for (int J = 0; J < NB; ++J) {
-        const int c0 = (J < jt0) ? W : 0, nc = 2 * W - c0;
-        const WMat x1 = pan(c->WX1, c->WX1c, c0, J), x2 = pan(c->WX2, c->WX2c, c0, J);
-        if (J > 0 && !gemm(c, W, nc, W, -1.0, tile(3, J - 1), false, pan(c->WX2, c->WX2c, c0, J - 1), false, 1.0, x1,
-                           p))
-            return false;
-        if (!gemm(c, W, nc, W, 1.0, tile(0, J), false, x1, false, 0.0, x2, p)) return false;
-    }
-    for (int J = NB - 1; J >= 0; --J) {
-        const WMat x2 = pan(c->WX2, c->WX2c, 0, J);
-        WMat x1 = pan(c->WX1, c->WX1c, 0, J);
-        if (J < NB - 1 && !gemm(c, W, 2 * W, W, -1.0, tile(2, J), false, pan(c->WX1, c->WX1c, 0, J + 1), false, 1.0,
-                                x2, p))
-            return false;
-        // the solved spikes, also row-major in the operand type ([p][side][PS][W])
-        x1.orow = tc ? elem(c->WXr, (int64_t)J * W * W, c->osize) : nullptr;
-        x1.ldr = W;
-        x1.sr = 2 * PS * W;
-        if (!gemm(c, W, 2 * W, W, 1.0, tile(1, J), false, x2, false, 0.0, x1, p, W, PS * W)) return false;
-    }
-
-    // randomized range finder on every spike (2p of them, b = 2 i + side)
-    const int nm = 2 * p, lp = c->lp, ell = c->ell, r = c->r;
-    const int64_t sQ = PS * lp, sZ = (int64_t)W * lp;
-    WMat Tsp;  // spike b: PS x W
-    Tsp.f = c->WX1;
-    Tsp.oc = bf ? c->WX1c : c->WX1;
-    Tsp.orow = tc ? c->WXr : nullptr;
-    Tsp.ld = PS;
-    Tsp.s = (int64_t)W * PS;
-    Tsp.ldr = W;
-    Tsp.sr = PS * W;
+    // P1 <- A^{-1} P1 (or A^{-T} P1): forward then backward block recurrence
+    auto solve = [&](bool trans) {
+        for (int J = 0; J < NB; ++J) {
+            const WMat x1 = pv(c->WP1, c->WP1c, J), x2 = pv(c->WP2, c->WP2c, J);
+            if (J > 0 && !gemm(c, W, 2 * lp, W, -1.0, tile(trans ? 2 : 3, J - 1), trans,
+                               pv(c->WP2, c->WP2c, J - 1), false, 1.0, x1, p))
+                return false;
+            if (!gemm(c, W, 2 * lp, W, 1.0, tile(trans ? 1 : 0, J), trans, x1, false, 0.0, x2, p)) return false;
+        }
+        for (int J = NB - 1; J >= 0; --J) {
+            const WMat x2 = pv(c->WP2, c->WP2c, J), x1 = pv(c->WP1, c->WP1c, J);
+            if (J < NB - 1 && !gemm(c, W, 2 * lp, W, -1.0, tile(trans ? 3 : 2, J), trans,
+                                    pv(c->WP1, c->WP1c, J + 1), false, 1.0, x2, p))
+                return false;
+            if (!gemm(c, W, 2 * lp, W, 1.0, tile(trans ? 0 : 1, J), trans, x2, false, 0.0, x1, p)) return false;
+        }
+        return true;
+    };
+    const WMat Cpl = square(c->WCpl, W, WW);
     WMat Om;
     Om.f = Om.oc = c->WOm;
     Om.ld = W;
     Om.s = sZ;
-    WMat Yk;
-    Yk.f = c->WYk;
-    Yk.ld = PS;
-    Yk.s = sQ;
-    WMat Qk;
-    Qk.f = c->WQk;
-    Qk.oc = bf ? c->WQc : c->WQk;
-    Qk.ld = PS;
-    Qk.s = sQ;
+    WMat Tip;
+    Tip.f = c->WTip;
+    Tip.oc = bf ? c->WTipc : c->WTip;
+    Tip.ld = W;
+    Tip.s = sZ;
     WMat Zk;
     Zk.f = c->WZk;
     Zk.oc = bf ? c->WZc : c->WZk;
     Zk.ld = W;
     Zk.s = sZ;
-    if (!launch(c, KID_WIDE_VEC, [&] {
+    const size_t panel_bytes = (size_t)p * sP;
+    auto clear_panel = [&]() {
+        return cudaMemsetAsync(c->WP1, 0, panel_bytes * tz, c->stream) == cudaSuccess &&
+               (!bf || cudaMemsetAsync(c->WP1c, 0, panel_bytes * oz, c->stream) == cudaSuccess);
+    };
+    // P1 <- the right-hand sides [0; B_i X_T | C_i X_W; 0]
+    auto couple = [&](const WMat &X) {
+        if (!clear_panel() || !gemm(c, W, lp, W, 1.0, Cpl, false, X, false, 0.0, Tip, nm)) return false;
+        return launch(c, KID_WIDE_VEC, [&] {
+            const dim3 g(64, nm);
+            if (bf)
+                k_tips_scatter<float, __nv_bfloat16><<<g, 256, 0, c->stream>>>(
+                    (const float *)c->WTip, P, c->k, W, PS, lp, (float *)c->WP1, (__nv_bfloat16 *)c->WP1c);
+            else
+                k_tips_scatter<T, T><<<g, 256, 0, c->stream>>>((const T *)c->WTip, P, c->k, W, PS, lp,
+                                                               (T *)c->WP1, nullptr);
+        });
+    };
+    // Zk <- [B_i^T (P1)_bottom | C_i^T (P1)_top]
+    auto couple_t = [&]() {
+        if (!launch(c, KID_WIDE_VEC, [&] {
+                const dim3 g(64, nm);
+                if (bf)
+                    k_tips_gather<float, __nv_bfloat16><<<g, 256, 0, c->stream>>>(
+                        (const float *)c->WP1, P, c->k, W, PS, lp, (float *)c->WTip, (__nv_bfloat16 *)c->WTipc);
+                else
+                    k_tips_gather<T, T><<<g, 256, 0, c->stream>>>((const T *)c->WP1, P, c->k, W, PS, lp,
+                                                                  (T *)c->WTip, nullptr);
+            }))
+            return false;
+        return gemm(c, W, lp, W, 1.0, Cpl, true, Tip, false, 0.0, Zk, nm);
+    };
+    // Q <- orth(Y) for the Y in P1 (2p matrices PS x lp); Q stays in WQk and is
+    // copied back into P1 (and its operand copy) for the next solve
+    auto orth = [&]() {
+        if (!cholqr3<T>(c, c->WP1, c->WQk)) return false;
+        if (cudaMemcpyAsync(c->WP1, c->WQk, (size_t)nm * sQ * tz, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            return false;
+        if (!bf) return true;
+        return launch(c, KID_WIDE_VEC, [&] {
+            k_to_op<float, __nv_bfloat16><<<1024, 256, 0, c->stream>>>((const float *)c->WQk, (__nv_bfloat16 *)c->WP1c,
+                                                                      (int64_t)nm * sQ);
+        });
+    };
+    // coupling tiles and the sketches
+    if (!launch(c, KID_WIDE_GATHER, [&] {
+            const dim3 g((unsigned)std::min<int64_t>(1024, ((int64_t)c->k * c->k + 255) / 256), nm);
+            for (int l = 0; l < 4; ++l) {
+                void *q = c->WCpl[l];
+                const size_t sz = (l < 2) ? tz : oz;
+                if (q) cudaMemsetAsync(q, 0, (size_t)nm * WW * sz, c->stream);
+            }
+            if (bf)
+                k_wide_couple_gather<float, __nv_bfloat16><<<g, 256, 0, c->stream>>>(
+                    c->band, c->ld, c->k, P, W, (float *)Cpl.f, (__nv_bfloat16 *)Cpl.oc, (__nv_bfloat16 *)Cpl.orow);
+            else if (tc)
+                k_wide_couple_gather<float, float><<<g, 256, 0, c->stream>>>(c->band, c->ld, c->k, P, W,
+                                                                           (float *)Cpl.f, nullptr, (float *)Cpl.orow);
+            else
+                k_wide_couple_gather<T, T><<<g, 256, 0, c->stream>>>(c->band, c->ld, c->k, P, W, (T *)Cpl.f, nullptr,
+                                                                   nullptr);
             if (bf)
                 k_wide_sketch<__nv_bfloat16><<<1024, 256, 0, c->stream>>>((__nv_bfloat16 *)c->WOm, W, c->k, ell, lp,
                                                                          c->opt.seed, nm);
@@ -1232,23 +1352,11 @@ bool wide_factor_t(Ctx *c) {
                 k_wide_sketch<T><<<1024, 256, 0, c->stream>>>((T *)c->WOm, W, c->k, ell, lp, c->opt.seed, nm);
         }))
         return false;
-    auto orth = [&]() {  // Y (in WYk) -> Q (in WQk), and its operand copy
-        if (!cholqr3<T>(c, c->WYk, c->WQk)) return false;
-        if (!bf) return true;
-        return launch(c, KID_WIDE_VEC, [&] {
-            k_to_op<float, __nv_bfloat16><<<1024, 256, 0, c->stream>>>((const float *)c->WQk, (__nv_bfloat16 *)c->WQc,
-                                                                      (int64_t)nm * sQ);
-        });
-    };
-    if (!gemm(c, (int)PS, lp, W, 1.0, Tsp, false, Om, false, 0.0, Yk, nm) || !orth()) return false;
+    if (!couple(Om) || !solve(false) || !orth()) return false;
     for (int it = 0; it < c->opt.power_iters; ++it)
-        if (!gemm(c, W, lp, (int)PS, 1.0, Tsp, true, Qk, false, 0.0, Zk, nm) ||
-            !gemm(c, (int)PS, lp, W, 1.0, Tsp, false, Zk, false, 0.0, Yk, nm) || !orth())
-            return false;
-    // B^T = T^T Q (W x lp) in the working precision; H = B B^T = Z^T Z (FP64 for the eigensolver)
-    WMat Zf = Zk;
-    Zf.oc = bf ? nullptr : Zk.f;
-    if (!gemm(c, W, lp, (int)PS, 1.0, Tsp, true, Qk, false, 0.0, Zf, nm)) return false;
+        if (!solve(true) || !couple_t() || !couple(Zk) || !solve(false) || !orth()) return false;
+    // B^T = T^T Q (W x lp); H = B B^T = Z^T Z (FP64 for the eigensolver)
+    if (!solve(true) || !couple_t()) return false;
     const dim3 gg((unsigned)((lp + 63) / 64), (unsigned)((lp + 63) / 64), (unsigned)nm);
     if (!launch(c, KID_WIDE_CHOLQR, [&] {
             k_simt_gemm<T><<<gg, 256, 0, c->stream>>>(lp, lp, W, T(1), T(0), (const T *)c->WZk, W, 1, sZ,
@@ -1320,15 +1428,22 @@ bool wide_setup(Ctx *c) {
     ok = ok && al(&c->WV1, p * PS * VP * tz) && al(&c->WV2, p * PS * VP * tz) &&
          al((void **)&c->diag_list, (2 * k + 1) * sizeof(int)) && al((void **)&c->gemm_err, sizeof(int));
     if (ok && p > 1 && r > 0) {
-        ok = al(&c->WX1, p * PS * 2 * W * tz) && al(&c->WX2, p * PS * 2 * W * tz) &&
-             al(&c->WOm, 2 * p * W * lp * (tc ? oz : tz)) && al(&c->WYk, 2 * p * PS * lp * tz) &&
-             al(&c->WQk, 2 * p * PS * lp * tz) && al(&c->WZk, 2 * p * W * lp * tz) &&
-             al(&c->WG, 2 * p * lp * lp * tz) && al((void **)&c->WGd, 2 * p * lp * lp * 8) &&
-             al(&c->WRi, 2 * p * lp * lp * tz) && al(&c->WE, 2 * p * (size_t)std::max(r, 1) * lp * tz);
-        if (ok && tc) ok = al(&c->WXr, p * PS * 2 * W * oz);
+        const size_t WL = W * lp, panel = p * PS * 2 * lp;
+        ok = al(&c->WP1, panel * tz) && al(&c->WP2, panel * tz) && al(&c->WTip, 2 * p * WL * tz) &&
+             al(&c->WOm, 2 * p * WL * (tc ? oz : tz)) && al(&c->WQk, 2 * p * PS * lp * tz) &&
+             al(&c->WZk, 2 * p * WL * tz) && al(&c->WG, 2 * p * lp * lp * tz) &&
+             al((void **)&c->WGd, 2 * p * lp * lp * 8) && al(&c->WRi, 2 * p * lp * lp * tz) &&
+             al(&c->WE, 2 * p * (size_t)std::max(r, 1) * lp * tz) && al(&c->WCpl[0], 2 * p * WW * tz);
+        if (ok && tc) {
+            if (bf) ok = al(&c->WCpl[2], 2 * p * WW * oz) && al(&c->WCpl[3], 2 * p * WW * oz);
+            else {
+                c->WCpl[2] = c->WCpl[0];
+                ok = al(&c->WCpl[3], 2 * p * WW * oz);
+            }
+        }
         if (ok && bf)
-            ok = al(&c->WX1c, p * PS * 2 * W * oz) && al(&c->WX2c, p * PS * 2 * W * oz) &&
-                 al(&c->WQc, 2 * p * PS * lp * oz) && al(&c->WZc, 2 * p * W * lp * oz);
+            ok = al(&c->WP1c, panel * oz) && al(&c->WP2c, panel * oz) && al(&c->WTipc, 2 * p * WL * oz) &&
+                 al(&c->WZc, 2 * p * WL * oz);
     }
     if (!ok) {
         cudaGetLastError();
@@ -1354,24 +1469,101 @@ void wide_free(Ctx *c) {
         ptrs.push_back(w[3]);
         w[0] = w[1] = w[2] = w[3] = nullptr;
     }
-    for (void *q : {c->WX1, c->WX2, c->WX1c, c->WX2c, c->WXr, c->WOm, c->WYk, c->WQk, c->WQc, c->WZk, c->WZc, c->WG,
+    ptrs.push_back(c->WCpl[0]);
+    if (c->WCpl[2] != c->WCpl[0]) ptrs.push_back(c->WCpl[2]);
+    ptrs.push_back(c->WCpl[3]);
+    c->WCpl[0] = c->WCpl[1] = c->WCpl[2] = c->WCpl[3] = nullptr;
+    for (void *q : {c->WP1, c->WP2, c->WP1c, c->WP2c, c->WTip, c->WTipc, c->WOm, c->WQk, c->WZk, c->WZc, c->WG,
                     (void *)c->WGd, c->WRi, c->WE, c->WV1, c->WV2, (void *)c->diag_list, (void *)c->gemm_err})
         ptrs.push_back(q);
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (c->wgraph) cudaGraphExecDestroy(c->wgraph);
+    if (c->wcap) cudaStreamDestroy(c->wcap);
+    c->wgraph = nullptr;
+    c->wcap = nullptr;
 }
 
-bool run_wide_factor(Ctx *c) {
+// Everything a factorisation enqueues: the block factorisation, the spikes
+// and their truncation, the reduced system, and the flags of the band rows
+// holding a nonzero (the FP64 residual visits only those).
+static bool wide_factor_device(Ctx *c) {
     const bool ok = c->fp64 ? wide_factor_t<double>(c) : wide_factor_t<float>(c);
     if (!ok) return false;
     if (c->p > 1 && c->r > 0 && !(run_reduced_build_ld(c, c->W) && run_reduced_factor(c))) return false;
-    // band rows with a nonzero entry: the FP64 residual visits only those
     const int nd = 2 * c->k + 1;
     if (cudaMemsetAsync(c->diag_list, 0, nd * sizeof(int), c->stream) != cudaSuccess) return false;
-    if (!launch(c, KID_DIAGS, [&] {
-            k_nonzero_diags<<<dim3(64, nd), 256, 0, c->stream>>>(c->band, c->ld, c->n, c->k, c->diag_list);
-        }))
+    return launch(c, KID_DIAGS, [&] {
+        k_nonzero_diags<<<dim3(64, nd), 256, 0, c->stream>>>(c->band, c->ld, c->n, c->k, c->diag_list);
+    });
+}
+
+// The factorisation's few thousand launches (the block products of the
+// recursive LU are small) as one graph launch: captured on the handle's
+// private stream the first time (and again when the band moves), replayed on
+// the handle's stream afterwards.
+static bool wide_factor_graph(Ctx *c) {
+    if (!c->wgraph || c->wgraph_band != c->band || c->wgraph_ld != c->ld) {
+        if (c->wgraph) cudaGraphExecDestroy(c->wgraph);
+        c->wgraph = nullptr;
+        if (!c->wcap && cudaStreamCreateWithFlags(&c->wcap, cudaStreamNonBlocking) != cudaSuccess) {
+            c->err = "capture stream creation failed";
+            return false;
+        }
+        const int64_t l0 = c->launches;
+        cudaStream_t own = c->stream;
+        c->stream = c->wcap;
+        if (cudaStreamBeginCapture(c->wcap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            c->stream = own;
+            c->err = "stream capture of the factorisation failed to start";
+            return false;
+        }
+        const bool ok = wide_factor_device(c);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->wcap, &g);
+        c->stream = own;
+        if (!ok || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (c->err.empty()) c->err = std::string("capture of the factorisation failed: ") + cudaGetErrorString(e);
+            return false;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&c->wgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->wgraph = nullptr;
+            c->err = std::string("graph instantiation failed: ") + cudaGetErrorString(ei);
+            return false;
+        }
+        c->wgraph_band = c->band;
+        c->wgraph_ld = c->ld;
+        c->wgraph_launches = c->launches - l0;
+        c->launches = l0;
+    }
+    if (cudaGraphLaunch(c->wgraph, c->stream) != cudaSuccess) {
+        c->err = "graph launch of the factorisation failed";
         return false;
+    }
+    c->launches += c->wgraph_launches;
+    return true;
+}
+
+bool run_wide_factor(Ctx *c) {
+    // profiling brackets every kernel with events on the handle's stream, so
+    // it runs the launches one by one; so does a handle whose capture failed
+    bool ok;
+    if (c->profile || c->wgraph_failed) {
+        ok = wide_factor_device(c);
+    } else {
+        ok = wide_factor_graph(c);
+        if (!ok && !c->wgraph) {  // nothing was launched: run the same work eagerly
+            c->wgraph_failed = true;
+            c->err.clear();
+            ok = wide_factor_device(c);
+        }
+    }
+    if (!ok) return false;
+    const int nd = 2 * c->k + 1;
     std::vector<int> flag(nd), list;
     int gerr = 0;
     if (cudaMemcpyAsync(flag.data(), c->diag_list, nd * sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
