@@ -78,7 +78,8 @@ enum { LRSPIKE_COMPRESS_SPIKE = 0, LRSPIKE_COMPRESS_COUPLING = 1 };
  * x = g - D^{-1}[C_i x_{i-1,b}; 0; B_i x_{i+1,t}].  Each application of the
  * solver (the outer loop's correction) is one such solve, so one outer step
  * gives the solution to about otf_tol.  Factorised like TRUNCATED.  Built
- * for k <= 64 without pivoting, outer IR or NONE, not graph_safe;
+ * without pivoting (k <= 1024; wide bands run every solve on the wide-band
+ * factors), outer IR or NONE, not graph_safe;
  * solve_transpose uses the TRUNCATED preconditioner.  Extra device memory:
  * FP64 n x max_nrhs, working precision n x max_nrhs, 10 x 2k(p-1) x max_nrhs
  * FP64. */

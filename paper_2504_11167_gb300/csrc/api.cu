@@ -187,9 +187,9 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     if (o.reduced == LRSPIKE_REDUCED_OTF) {
         if (o.p < 2 || o.r < 1)
             return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "the OTF reduced system needs p >= 2 and r >= 1");
-        if (wide || o.pivoting || o.graph_safe || o.outer == LRSPIKE_OUTER_BICGSTAB)
+        if (o.pivoting || o.graph_safe || o.outer == LRSPIKE_OUTER_BICGSTAB)
             return fail(nullptr, LRSPIKE_ERR_UNSUPPORTED,
-                        "OTF is built for k <= 64 without pivoting, outer IR or NONE, not graph_safe");
+                        "OTF is built without pivoting, for outer IR or NONE, not graph_safe");
     }
     if (!(o.otf_tol > 0.0) || o.otf_max_iter < 1)
         return fail(nullptr, LRSPIKE_ERR_INVALID_ARG, "otf_tol must be > 0 and otf_max_iter >= 1");

@@ -229,6 +229,7 @@ bool wide_setup(Ctx *c);
 void wide_free(Ctx *c);
 bool run_wide_factor(Ctx *c);
 bool run_wide_dstage(Ctx *c, const double *rin, int nrhs);
+bool run_wide_dstage_inv(Ctx *c, const double *rin, int nrhs, const double *inv);
 bool run_wide_dstage_t(Ctx *c, const double *hin, double *x, int64_t ldx, int nrhs, bool accumulate);
 bool run_lu_inv64(Ctx *c, void *A, int lda, int64_t sA, void *Li, void *Ui, int ldo, int64_t sO, int64_t row0);
 bool run_jacobi_batch(Ctx *c, int n, const double *G, int nmat, int rout, double rank_tol, void *out,

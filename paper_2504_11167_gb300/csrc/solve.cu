@@ -874,6 +874,7 @@ static bool project_t_impl(Ctx *c, const double *hin, int nrhs) {
 }
 
 bool run_dstage_inv(Ctx *c, const double *rin, int nrhs, const double *inv) {
+    if (c->wide) return run_wide_dstage_inv(c, rin, nrhs, inv);
     if (c->fp64) {
         switch (c->KB) {
             case 8: return dstage_impl<double, 8>(c, rin, nrhs, inv);

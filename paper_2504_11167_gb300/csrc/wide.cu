@@ -1584,13 +1584,14 @@ bool run_wide_factor(Ctx *c) {
            cudaStreamSynchronize(c->stream) == cudaSuccess;
 }
 
+// inv: the column scale factors of the input (rin / |rin| enters the solve)
 template <typename T>
-static bool wide_dstage_t(Ctx *c, const double *rin, int nrhs, bool trans, double *x, int64_t ldx, bool acc) {
+static bool wide_dstage_t(Ctx *c, const double *rin, int nrhs, bool trans, double *x, int64_t ldx, bool acc,
+                          const double *inv) {
     const int W = c->W, p = c->p;
     const int64_t PS = c->PS;
     Parts P{c->off_d, c->boff_d, p};
     const dim3 grid((unsigned)((PS + 255) / 256), p);
-    const double *inv = c->nrm + 2 * c->opt.max_nrhs;
     if (!launch(c, KID_WIDE_VEC, [&] {
             if (trans)
                 k_wide_pack_t<T><<<grid, 256, 0, c->stream>>>(rin, inv, c->zr, (const T *)c->PQ, W, P, c->k, c->r,
@@ -1616,14 +1617,19 @@ static bool wide_dstage_t(Ctx *c, const double *rin, int nrhs, bool trans, doubl
     });
 }
 
+bool run_wide_dstage_inv(Ctx *c, const double *rin, int nrhs, const double *inv) {
+    return c->fp64 ? wide_dstage_t<double>(c, rin, nrhs, false, nullptr, 0, false, inv)
+                   : wide_dstage_t<float>(c, rin, nrhs, false, nullptr, 0, false, inv);
+}
+
 bool run_wide_dstage(Ctx *c, const double *rin, int nrhs) {
-    return c->fp64 ? wide_dstage_t<double>(c, rin, nrhs, false, nullptr, 0, false)
-                   : wide_dstage_t<float>(c, rin, nrhs, false, nullptr, 0, false);
+    return run_wide_dstage_inv(c, rin, nrhs, c->nrm + 2 * c->opt.max_nrhs);
 }
 
 bool run_wide_dstage_t(Ctx *c, const double *hin, double *x, int64_t ldx, int nrhs, bool accumulate) {
-    return c->fp64 ? wide_dstage_t<double>(c, hin, nrhs, true, x, ldx, accumulate)
-                   : wide_dstage_t<float>(c, hin, nrhs, true, x, ldx, accumulate);
+    const double *inv = c->nrm + 2 * c->opt.max_nrhs;
+    return c->fp64 ? wide_dstage_t<double>(c, hin, nrhs, true, x, ldx, accumulate, inv)
+                   : wide_dstage_t<float>(c, hin, nrhs, true, x, ldx, accumulate, inv);
 }
 
 }  // namespace lrs

@@ -58,7 +58,6 @@ def test_defaults(lib):
     dict(reduced=2, pivoting=1),                           # OTF: no pivoting
     dict(reduced=2, outer=1),                              # OTF: outer IR or NONE
     dict(reduced=2, graph_safe=1),                         # OTF: not graph_safe
-    dict(n=20000, k=100, r=8, reduced=2),                  # OTF: k <= 64
 ])
 def test_create_reports_unbuilt_combinations(lib, changes):
     o = _opts(lib, n=changes.pop("n", 1000), k=changes.pop("k", 8), p=4, r=changes.pop("r", 2))

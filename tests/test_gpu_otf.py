@@ -53,6 +53,7 @@ CASES = [
     (5000, 16, 5, 4, 1.1, "coupling", 2),
     (9000, 64, 4, 16, 1.1, "coupling", 1),
     (420, 40, 5, 6, 1.3, "spike", 3),      # n_i = 84 < 2k: the two tips of a partition overlap
+    (6000, 96, 4, 8, 1.2, "spike", 2),     # wide band (W = 128): solves on the wide-band factors
 ]
 
 
@@ -102,3 +103,16 @@ def test_otf_needs_fewer_outer_steps_than_the_truncated_preconditioner(torch_cud
         _, i_t = s.solve(torch.from_numpy(np.ascontiguousarray(f.T)).cuda())
     assert i_otf["converged"] and i_t["converged"]
     assert i_otf["iterations"] < i_t["iterations"]
+
+
+def test_otf_wide_convection_diffusion(torch_cuda):
+    """LR-SPIKE-OTF on a wide, sparse-in-band system (the paper's setting for
+    it): 2-D convection-diffusion on a 96 x 96 grid (k = 96), TF32 factors,
+    the reduced system iterated to 1e-8 inside FP64 refinement to 1e-10."""
+    ab = inputs.convection_diffusion_band(96, 0.5)
+    k, n = 96, ab.shape[1]
+    f = inputs.rhs(n, 1, 23)
+    x, info = gpu_solve(torch_cuda, ab, f, k, 8, 8, precision="tf32", tol=1e-10, max_iter=20)
+    assert info["converged"]
+    res = np.asarray(f) - O.band_matvec(ab, k, x)
+    assert np.linalg.norm(res) / np.linalg.norm(f) <= 1.01e-10
