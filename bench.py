@@ -687,6 +687,15 @@ def main():
             "points": grid}
         del f16
         torch.cuda.empty_cache()
+        # the full low-rank reduced system (LR-SPIKE-I, solved directly by
+        # block cyclic reduction over the 255 interfaces) at r = 32
+        msf, _, proff, infof, _, _ = run("fp32", 2, 1, True, reduced="full", r=32)
+        variants["full_reduced_system_r32"] = {
+            "value": N * NRHS / (msf * 1e-3), "unit": UNIT, "ms_per_step": msf,
+            "iterations": infof["iterations"], "rel_residual": infof["max_rel_residual"],
+            "reduced": "FULL (LR-SPIKE-I), block cyclic reduction, r = 32",
+            "kernels": {k_: {"launches": c_, "ms_total": round(t_, 4)} for k_, (c_, t_) in proff.items()
+                        if c_ and k_.startswith("reduced")}}
         variants["plain_fp64_n65536_k16"] = config1_variant(dev)
         variants["convection_diffusion_k1024"] = cd_variants(dev, peaks)
         variants["differentiable_solve_n1048576_k32"] = autograd_variant(dev)

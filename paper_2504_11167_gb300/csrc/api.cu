@@ -100,13 +100,16 @@ static bool dalloc(P **ptr, size_t bytes) {
 static void free_all(Ctx *c) {
     void *ptrs[] = {c->off_d, c->boff_d, c->LT,   c->UT,  c->DI,   c->X,     c->Ucat,
                     c->PQ,    c->Gram,   c->Gpart, c->sigma, c->E, c->F,    c->Gs,    c->Rinv,
-                    c->Gam,   c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
+                    c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
                     c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots,
                     c->bpartial, c->PF, c->PIVP, c->ocv, c->og, c->orv, c->osc, c->oone, c->xalt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (double *p : c->bv)
         if (p) cudaFree(p);
+    for (auto &b : c->bcr)
+        for (double *p : {b.E, b.F, b.G, b.Einv, b.al, b.be})
+            if (p) cudaFree(p);
     wide_free(c);
     if (c->host) cudaFreeHost(c->host);
     for (auto &pd : c->pending) {
@@ -261,10 +264,14 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
              dalloc(&c->Ucat, (size_t)c->n * n2 * T) && dalloc(&c->PQ, (size_t)c->p * 2 * c->r * KB * T) &&
              dalloc(&c->sigma, (size_t)c->p * 2 * c->r * 8) && dalloc(&c->E, ni * n2 * n2 * 8) &&
              dalloc(&c->F, ni * n2 * n2 * 8) && dalloc(&c->Gs, ni * n2 * n2 * 8) &&
-             dalloc(&c->Rinv, ni * n2 * n2 * 8) && dalloc(&c->Gam, ni * n2 * n2 * 8) &&
+             dalloc(&c->Rinv, ni * n2 * n2 * 8) &&
              dalloc(&c->psi, ni * n2 * mx * 8) && dalloc(&c->zr, ni * n2 * mx * 8) &&
              dalloc(&c->wr, ni * n2 * mx * 8);
     }
+    if (ok && spikes && o.reduced == LRSPIKE_REDUCED_FULL)
+        for (int t = 0; t < 2 && ok; ++t)
+            for (double **q : {&c->bcr[t].E, &c->bcr[t].F, &c->bcr[t].G, &c->bcr[t].Einv, &c->bcr[t].al, &c->bcr[t].be})
+                ok = ok && dalloc(q, ni * n2 * n2 * 8);
     if (ok && o.outer == LRSPIKE_OUTER_BICGSTAB) ok = bicgstab_alloc(c);
     if (ok && c->otf) ok = otf_alloc(c);
     // fused retrieval + residual in the IR loop: rows of one CTA (256) and its
@@ -287,7 +294,6 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     cudaMemcpy(c->off_d, c->off_h.data(), (c->p + 1) * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(c->boff_d, c->boff_h.data(), (c->p + 1) * 8, cudaMemcpyHostToDevice);
     cudaMemset(c->counter, 0, 64);
-    if (c->Gam) cudaMemset(c->Gam, 0, ni * n2 * n2 * 8);
     const cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_all(c);

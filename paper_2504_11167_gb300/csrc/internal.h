@@ -93,8 +93,14 @@ struct Ctx {
     double *sigma = nullptr;  // [p][2][r]
     // reduced system, interfaces i = 0..p-2, blocks of 2r x 2r (row-major)
     double *E = nullptr, *F = nullptr, *Gs = nullptr;   // diagonal, super, sub blocks
-    double *Rinv = nullptr;   // TRUNCATED: E_i^{-1}; FULL: Delta_i^{-1}
-    double *Gam = nullptr;    // FULL: Gamma_i = G_i Delta_{i-1}^{-1}
+    double *Rinv = nullptr;   // TRUNCATED: E_i^{-1}
+    // FULL: block cyclic reduction of R (set 0) and of R^T (set 1): working
+    // copies of the blocks (reduced in place level by level), the inverses of
+    // the blocks each level eliminates, and the level multipliers
+    // alpha = G E^{-1}, beta = F E^{-1} of the equations it keeps
+    struct BcrSet {
+        double *E = nullptr, *F = nullptr, *G = nullptr, *Einv = nullptr, *al = nullptr, *be = nullptr;
+    } bcr[2];
 
     // solve scratch (max_nrhs columns)
     double *rv = nullptr;     // FP64 residual / work vector, n x max_nrhs

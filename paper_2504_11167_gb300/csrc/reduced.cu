@@ -11,8 +11,9 @@
 // TRUNCATED (LR-SPIKE-T, S~~_r of eq. 'red_sys_prec_mid_2') keeps E_i only:
 // the paper drops the top tip of T~ and the bottom tip of W~, which are
 // exactly F and G here.  FULL keeps all blocks (the reduced system of
-// LR-SPIKE-I, here solved directly by block LU: R = L_b U_b with
-// Delta_0 = E_0, Gamma_i = G_i Delta_{i-1}^{-1}, Delta_i = E_i - Gamma_i F_{i-1}).
+// LR-SPIKE-I, here solved directly by block cyclic reduction, below).
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -223,47 +224,6 @@ __global__ void k_red_factor_trunc_ip(const double *__restrict__ E, int n2, doub
     for (int t = threadIdx.x; t < n2 * n2; t += blockDim.x) out[t] = a[t];
 }
 
-// Block LU of the block-tridiagonal R in one CTA (sequential over interfaces).
-__global__ void k_red_factor_full(const double *__restrict__ E, const double *__restrict__ F,
-                                  const double *__restrict__ Gs, int n2, int ni,
-                                  double *__restrict__ Rinv, double *__restrict__ Gam,
-                                  int64_t *status) {
-    extern __shared__ double sm[];
-    double *aug = sm, *fac = aug + 2 * n2 * n2, *tmp = fac + n2;
-    __shared__ int pivrow;
-    const int nn = n2 * n2;
-    for (int i = 0; i < ni; ++i) {
-        // Delta_i = E_i - Gamma_i F_{i-1}, Gamma_i = G_i Delta_{i-1}^{-1}
-        if (i > 0) {
-            const double *Dprev = Rinv + (int64_t)(i - 1) * nn;
-            const double *Gi = Gs + (int64_t)i * nn;
-            double *gam = Gam + (int64_t)i * nn;
-            for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-                const int a = t / n2, b = t % n2;
-                double acc = 0.0;
-                for (int q = 0; q < n2; ++q) acc += Gi[a * n2 + q] * Dprev[q * n2 + b];
-                gam[t] = acc;
-            }
-            __syncthreads();
-            const double *Fp = F + (int64_t)(i - 1) * nn;
-            for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-                const int a = t / n2, b = t % n2;
-                double acc = E[(int64_t)i * nn + t];
-                for (int q = 0; q < n2; ++q) acc -= gam[a * n2 + q] * Fp[q * n2 + b];
-                tmp[t] = acc;
-            }
-            __syncthreads();
-            load_aug(aug, tmp, n2);
-        } else {
-            load_aug(aug, E, n2);
-        }
-        const bool ok = gj_inverse(aug, n2, fac, &pivrow);
-        if (!ok && threadIdx.x == 0) atomicMin((unsigned long long *)status, 0x7ffffffffffffffeULL);
-        store_inv(aug, Rinv + (int64_t)i * nn, n2);
-        __syncthreads();
-    }
-}
-
 // z = R^{-1} psi (or R^{-T} psi), TRUNCATED: per interface.
 __global__ void k_red_solve_trunc(const double *__restrict__ Rinv, const double *__restrict__ psi,
                                   double *__restrict__ z, int n2, int nrhs, int trans) {
@@ -279,81 +239,220 @@ __global__ void k_red_solve_trunc(const double *__restrict__ Rinv, const double 
     }
 }
 
-// FULL: one CTA, forward and backward block substitution with R = L_b U_b.
-__global__ void k_red_solve_full(const double *__restrict__ Rinv, const double *__restrict__ F,
-                                 const double *__restrict__ Gam, const double *__restrict__ psi,
-                                 double *__restrict__ w, double *__restrict__ z, int n2, int ni,
-                                 int nrhs, int trans) {
-    const int nn = n2 * n2, nv = n2 * nrhs;
-    if (!trans) {
-        // L_b w = psi:  w_i = psi_i - Gamma_i w_{i-1}
-        for (int i = 0; i < ni; ++i) {
-            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-                const int a = t / nrhs, c = t % nrhs;
-                double acc = psi[(int64_t)i * nv + t];
-                if (i > 0)
-                    for (int q = 0; q < n2; ++q)
-                        acc -= Gam[(int64_t)i * nn + a * n2 + q] * w[(int64_t)(i - 1) * nv + q * nrhs + c];
-                w[(int64_t)i * nv + t] = acc;
-            }
-            __syncthreads();
-        }
-        // U_b z = w:  z_i = Delta_i^{-1} (w_i - F_i z_{i+1})
-        for (int i = ni - 1; i >= 0; --i) {
-            double *tmp = w + (int64_t)i * nv;  // reuse w_i in place as the bracket
-            if (i < ni - 1) {
-                for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-                    const int a = t / nrhs, c = t % nrhs;
-                    double acc = tmp[t];
-                    for (int q = 0; q < n2; ++q)
-                        acc -= F[(int64_t)i * nn + a * n2 + q] * z[(int64_t)(i + 1) * nv + q * nrhs + c];
-                    tmp[t] = acc;
-                }
-                __syncthreads();
-            }
-            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-                const int a = t / nrhs, c = t % nrhs;
-                double acc = 0.0;
-                for (int q = 0; q < n2; ++q) acc += Rinv[(int64_t)i * nn + a * n2 + q] * tmp[q * nrhs + c];
-                z[(int64_t)i * nv + t] = acc;
-            }
-            __syncthreads();
-        }
-    } else {
-        // U_b^T y = psi:  y_i = Delta_i^{-T} (psi_i - F_{i-1}^T y_{i-1})
-        for (int i = 0; i < ni; ++i) {
-            double *tmp = w + (int64_t)i * nv;
-            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-                const int a = t / nrhs, c = t % nrhs;
-                double acc = psi[(int64_t)i * nv + t];
-                if (i > 0)
-                    for (int q = 0; q < n2; ++q)
-                        acc -= F[(int64_t)(i - 1) * nn + q * n2 + a] * z[(int64_t)(i - 1) * nv + q * nrhs + c];
-                tmp[t] = acc;
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-                const int a = t / nrhs, c = t % nrhs;
-                double acc = 0.0;
-                for (int q = 0; q < n2; ++q) acc += Rinv[(int64_t)i * nn + q * n2 + a] * tmp[q * nrhs + c];
-                z[(int64_t)i * nv + t] = acc;
-            }
-            __syncthreads();
-        }
-        // L_b^T z = y:  z_i = y_i - Gamma_{i+1}^T z_{i+1}   (y held in z)
-        for (int i = ni - 2; i >= 0; --i) {
-            for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-                const int a = t / nrhs, c = t % nrhs;
-                double acc = z[(int64_t)i * nv + t];
-                for (int q = 0; q < n2; ++q)
-                    acc -= Gam[(int64_t)(i + 1) * nn + q * n2 + a] * z[(int64_t)(i + 1) * nv + q * nrhs + c];
-                w[(int64_t)i * nv + t] = acc;
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < nv; t += blockDim.x) z[(int64_t)i * nv + t] = w[(int64_t)i * nv + t];
-            __syncthreads();
+// ---------------------------------------------------------------------------
+// FULL reduced system by block cyclic reduction (log2(p) levels instead of a
+// chain over the p-1 interfaces).  At level l (h = 2^l) the equations
+// i = 2h(j+1) - 1 are kept and their neighbours i -+ h eliminated:
+//   alpha_i = G_i E_{i-h}^{-1},  beta_i = F_i E_{i+h}^{-1}
+//   E_i <- E_i - alpha_i F_{i-h} - beta_i G_{i+h}
+//   G_i <- -alpha_i G_{i-h},  F_i <- -beta_i F_{i+h}   (now coupling i -+ 2h)
+// until one equation (i = 2^L - 1) is left.  The solve reduces the right-hand
+// side the same way (w_i -= alpha_i w_{i-h} + beta_i w_{i+h}), solves the last
+// equation, and back-substitutes level by level
+//   z_i = E_i^{-1} (w_i - G_i z_{i-h} - F_i z_{i+h})   for the eliminated i.
+// R^T is reduced the same way from its own blocks (diagonal E_i^T, super
+// G_{i+1}^T, sub F_{i-1}^T).  Blocks row-major n2 x n2, FP64.
+
+// working copies of the blocks of R (trans = 0) or R^T (trans = 1)
+__global__ void k_bcr_copy(const double *__restrict__ E, const double *__restrict__ F,
+                           const double *__restrict__ Gs, int m, int n2, int trans, double *__restrict__ oE,
+                           double *__restrict__ oF, double *__restrict__ oG) {
+    const int i = blockIdx.x, nn = n2 * n2;
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int a = t / n2, b = t % n2, tt = b * n2 + a;
+        if (!trans) {
+            oE[(int64_t)i * nn + t] = E[(int64_t)i * nn + t];
+            oF[(int64_t)i * nn + t] = F[(int64_t)i * nn + t];
+            oG[(int64_t)i * nn + t] = Gs[(int64_t)i * nn + t];
+        } else {
+            oE[(int64_t)i * nn + t] = E[(int64_t)i * nn + tt];
+            oF[(int64_t)i * nn + t] = (i + 1 < m) ? Gs[(int64_t)(i + 1) * nn + tt] : 0.0;
+            oG[(int64_t)i * nn + t] = (i >= 1) ? F[(int64_t)(i - 1) * nn + tt] : 0.0;
         }
     }
+}
+
+// Einv_i = E_i^{-1} for i = first + j stride, j < count (Gauss-Jordan in
+// shared memory with partial pivoting)
+__global__ void k_bcr_invert(const double *__restrict__ E, double *__restrict__ Einv, int n2, int first, int stride,
+                             int64_t *status) {
+    extern __shared__ double sm[];
+    double *aug = sm, *fac = aug + 2 * n2 * n2;
+    __shared__ int pivrow;
+    const int i = first + blockIdx.x * stride, nn = n2 * n2;
+    load_aug(aug, E + (int64_t)i * nn, n2);
+    const bool ok = gj_inverse(aug, n2, fac, &pivrow);
+    if (!ok && threadIdx.x == 0) atomicMin((unsigned long long *)status, 0x7ffffffffffffffeULL);
+    store_inv(aug, Einv + (int64_t)i * nn, n2);
+}
+
+// one level of the reduction for the kept equation i = 2h(j+1) - 1 (CTA j)
+__global__ void k_bcr_reduce(double *__restrict__ E, double *__restrict__ F, double *__restrict__ G,
+                             const double *__restrict__ Einv, double *__restrict__ al, double *__restrict__ be,
+                             int m, int n2, int h) {
+    extern __shared__ double sm[];
+    const int j = blockIdx.x, i = 2 * h * (j + 1) - 1, lo = i - h, hi = i + h, nn = n2 * n2;
+    const bool has_hi = hi < m;
+    double *A = sm, *B = sm + nn;  // alpha, beta
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int a = t / n2, b = t % n2;
+        double sa = 0.0, sb = 0.0;
+        for (int q = 0; q < n2; ++q) {
+            sa += G[(int64_t)i * nn + a * n2 + q] * Einv[(int64_t)lo * nn + q * n2 + b];
+            if (has_hi) sb += F[(int64_t)i * nn + a * n2 + q] * Einv[(int64_t)hi * nn + q * n2 + b];
+        }
+        A[t] = sa;
+        B[t] = sb;
+        al[(int64_t)j * nn + t] = sa;
+        be[(int64_t)j * nn + t] = sb;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int a = t / n2, b = t % n2;
+        double e = E[(int64_t)i * nn + t], g = 0.0, f = 0.0;
+        for (int q = 0; q < n2; ++q) {
+            e -= A[a * n2 + q] * F[(int64_t)lo * nn + q * n2 + b];
+            g -= A[a * n2 + q] * G[(int64_t)lo * nn + q * n2 + b];
+            if (has_hi) {
+                e -= B[a * n2 + q] * G[(int64_t)hi * nn + q * n2 + b];
+                f -= B[a * n2 + q] * F[(int64_t)hi * nn + q * n2 + b];
+            }
+        }
+        E[(int64_t)i * nn + t] = e;
+        G[(int64_t)i * nn + t] = g;
+        F[(int64_t)i * nn + t] = f;
+    }
+}
+
+// w_i -= alpha_i w_{i-h} + beta_i w_{i+h} for the kept i = 2h(j+1) - 1 (CTA j);
+// w in the psi layout [m][n2][nrhs]
+__global__ void k_bcr_fwd(const double *__restrict__ al, const double *__restrict__ be, double *__restrict__ w,
+                          int m, int n2, int h, int nrhs) {
+    const int j = blockIdx.x, i = 2 * h * (j + 1) - 1, lo = i - h, hi = i + h, nn = n2 * n2, nv = n2 * nrhs;
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        const int a = t / nrhs, c = t % nrhs;
+        double acc = w[(int64_t)i * nv + t];
+        for (int q = 0; q < n2; ++q) {
+            acc -= al[(int64_t)j * nn + a * n2 + q] * w[(int64_t)lo * nv + q * nrhs + c];
+            if (hi < m) acc -= be[(int64_t)j * nn + a * n2 + q] * w[(int64_t)hi * nv + q * nrhs + c];
+        }
+        w[(int64_t)i * nv + t] = acc;
+    }
+}
+
+// z_i = E_i^{-1} (w_i - G_i z_{i-h} - F_i z_{i+h}) for the eliminated
+// i = h (2j+1) - 1 (CTA j); the last equation (h = 0 marks it) has no neighbours
+__global__ void k_bcr_bwd(const double *__restrict__ Einv, const double *__restrict__ F,
+                          const double *__restrict__ G, const double *__restrict__ w, double *__restrict__ z, int m,
+                          int n2, int h, int top, int nrhs) {
+    extern __shared__ double tv[];  // [n2][nrhs]
+    const int j = blockIdx.x, i = h ? h * (2 * j + 1) - 1 : top, nn = n2 * n2, nv = n2 * nrhs;
+    const int lo = i - h, hi = i + h;
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        const int a = t / nrhs, c = t % nrhs;
+        double acc = w[(int64_t)i * nv + t];
+        if (h)
+            for (int q = 0; q < n2; ++q) {
+                if (lo >= 0) acc -= G[(int64_t)i * nn + a * n2 + q] * z[(int64_t)lo * nv + q * nrhs + c];
+                if (hi < m) acc -= F[(int64_t)i * nn + a * n2 + q] * z[(int64_t)hi * nv + q * nrhs + c];
+            }
+        tv[t] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        const int a = t / nrhs, c = t % nrhs;
+        double acc = 0.0;
+        for (int q = 0; q < n2; ++q) acc += Einv[(int64_t)i * nn + a * n2 + q] * tv[q * nrhs + c];
+        z[(int64_t)i * nv + t] = acc;
+    }
+}
+
+// levels of the reduction of m equations: kept and eliminated counts
+struct BcrLevels {
+    std::vector<int> kept, elim;
+    int top = 0;
+};
+static BcrLevels bcr_levels(int m) {
+    BcrLevels L;
+    int h = 1;
+    while (m / h > 1) {
+        L.kept.push_back(m / (2 * h));
+        int e = 0;
+        for (int64_t i = h - 1; i < m; i += 2 * h) ++e;
+        L.elim.push_back(e);
+        h *= 2;
+    }
+    L.top = h - 1;
+    return L;
+}
+
+static bool bcr_factor(Ctx *c) {
+    const int n2 = 2 * c->r, m = c->p - 1;
+    const size_t nn = (size_t)n2 * n2;
+    const BcrLevels L = bcr_levels(m);
+    const size_t inv_smem = (2 * nn + n2) * sizeof(double), red_smem = 2 * nn * sizeof(double);
+    cudaFuncSetAttribute(k_bcr_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
+    cudaFuncSetAttribute(k_bcr_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem);
+    for (int t = 0; t < 2; ++t) {
+        auto &b = c->bcr[t];
+        if (!launch(c, KID_RED_FACTOR, [&] {
+                k_bcr_copy<<<m, 256, 0, c->stream>>>(c->E, c->F, c->Gs, m, n2, t, b.E, b.F, b.G);
+            }))
+            return false;
+        size_t off = 0;
+        for (size_t l = 0; l < L.kept.size(); ++l) {
+            const int h = 1 << l;
+            if (!launch(c, KID_RED_FACTOR, [&] {
+                    k_bcr_invert<<<L.elim[l], 256, inv_smem, c->stream>>>(b.E, b.Einv, n2, h - 1, 2 * h, c->status);
+                }))
+                return false;
+            if (L.kept[l] > 0 && !launch(c, KID_RED_FACTOR, [&] {
+                    k_bcr_reduce<<<L.kept[l], 256, red_smem, c->stream>>>(b.E, b.F, b.G, b.Einv, b.al + off * nn,
+                                                                           b.be + off * nn, m, n2, h);
+                }))
+                return false;
+            off += L.kept[l];
+        }
+        if (!launch(c, KID_RED_FACTOR, [&] {
+                k_bcr_invert<<<1, 256, inv_smem, c->stream>>>(b.E, b.Einv, n2, L.top, 1, c->status);
+            }))
+            return false;
+    }
+    return true;
+}
+
+static bool bcr_solve(Ctx *c, int nrhs, bool trans) {
+    const int n2 = 2 * c->r, m = c->p - 1;
+    const size_t nn = (size_t)n2 * n2, nv = (size_t)n2 * nrhs;
+    const BcrLevels L = bcr_levels(m);
+    auto &b = c->bcr[trans ? 1 : 0];
+    if (cudaMemcpyAsync(c->wr, c->psi, (size_t)m * nv * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+        c->err = "reduced right-hand side copy failed";
+        return false;
+    }
+    size_t off = 0;
+    std::vector<size_t> offs;
+    for (size_t l = 0; l < L.kept.size(); ++l) {
+        offs.push_back(off);
+        if (L.kept[l] > 0 && !launch(c, KID_RED_SOLVE, [&] {
+                k_bcr_fwd<<<L.kept[l], 128, 0, c->stream>>>(b.al + off * nn, b.be + off * nn, c->wr, m, n2, 1 << l,
+                                                          nrhs);
+            }))
+            return false;
+        off += L.kept[l];
+    }
+    const size_t smem = nv * sizeof(double);
+    if (!launch(c, KID_RED_SOLVE, [&] {
+            k_bcr_bwd<<<1, 128, smem, c->stream>>>(b.Einv, b.F, b.G, c->wr, c->zr, m, n2, 0, L.top, nrhs);
+        }))
+        return false;
+    for (int l = (int)L.kept.size() - 1; l >= 0; --l)
+        if (!launch(c, KID_RED_SOLVE, [&] {
+                k_bcr_bwd<<<L.elim[l], 128, smem, c->stream>>>(b.Einv, b.F, b.G, c->wr, c->zr, m, n2, 1 << l, 0,
+                                                               nrhs);
+            }))
+            return false;
+    return true;
 }
 
 // ldpq: row stride of the projections P_i, Q_i (the block size)
@@ -398,12 +497,8 @@ bool run_reduced_factor(Ctx *c) {
             k_red_factor_trunc<<<ni, 256, smem, c->stream>>>(c->E, n2, c->Rinv, c->status);
         });
     }
-    const size_t smem = (2 * n2 * n2 + n2 + n2 * n2) * sizeof(double);
-    cudaFuncSetAttribute(k_red_factor_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return launch(c, KID_RED_FACTOR, [&] {
-        k_red_factor_full<<<1, 256, smem, c->stream>>>(c->E, c->F, c->Gs, n2, ni, c->Rinv, c->Gam,
-                                                       c->status);
-    });
+    (void)ni;
+    return bcr_factor(c);
 }
 
 bool run_reduced_solve(Ctx *c, int nrhs, bool trans) {
@@ -413,10 +508,7 @@ bool run_reduced_solve(Ctx *c, int nrhs, bool trans) {
         return launch(c, KID_RED_SOLVE, [&] {
             k_red_solve_trunc<<<ni, 128, 0, c->stream>>>(c->Rinv, c->psi, c->zr, n2, nrhs, trans);
         });
-    return launch(c, KID_RED_SOLVE, [&] {
-        k_red_solve_full<<<1, 256, 0, c->stream>>>(c->Rinv, c->F, c->Gam, c->psi, c->wr, c->zr, n2, ni,
-                                                   nrhs, trans);
-    });
+    return bcr_solve(c, nrhs, trans);
 }
 
 }  // namespace lrs

@@ -72,6 +72,8 @@ CASES = [
     (50000, 8, 16, 4, 1.5, "spike", "truncated", 16),   # many blocks, widest nrhs
     (5000, 24, 4, 6, 1.3, "coupling", "full", 1),       # KB = 32, one column: warp D-stage
     (9000, 40, 3, 10, 1.2, "spike", "truncated", 1),    # KB = 64, one column: warp D-stage
+    (12800, 8, 64, 4, 1.2, "spike", "full", 2),         # FULL by cyclic reduction: 63 interfaces, 6 levels
+    (6600, 12, 33, 5, 1.3, "coupling", "full", 1),      # 32 interfaces: the last level keeps one block
 ]
 
 
