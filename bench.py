@@ -449,9 +449,12 @@ def batch_variant(dev, systems_count=512, steps=3, iterations=10):
         ms = e0.elapsed_time(e1) / steps
         worst = max(x["max_rel_residual"] for x in infos)
         unconverged = sum(1 for x in infos if not x["converged"])
+        hist = {}
+        for x in infos:   # refinement steps each system ran before its residual met tol
+            hist[x["iterations"]] = hist.get(x["iterations"], 0) + 1
         used = list(b.shapes)
         b.close()
-        return ms, (worst, unconverged), used
+        return ms, (worst, unconverged, dict(sorted(hist.items()))), used
 
     ms_def, worst_def, shapes_def = timed(None)
     classes = {}
@@ -465,15 +468,19 @@ def batch_variant(dev, systems_count=512, steps=3, iterations=10):
     torch.cuda.empty_cache()
     return {"value": total / (ms_tun * 1e-3), "unit": UNIT, "ms_per_step": ms_tun,
             "default_shapes": {"value": total / (ms_def * 1e-3), "ms_per_step": ms_def,
-                               "max_rel_residual": worst_def[0], "unconverged_systems": worst_def[1]},
+                               "max_rel_residual": worst_def[0], "unconverged_systems": worst_def[1],
+                               "steps_histogram": worst_def[2]},
             "autotuned_shapes": {"value": total / (ms_tun * 1e-3), "ms_per_step": ms_tun,
                                  "max_rel_residual": worst_tun[0], "unconverged_systems": worst_tun[1],
+                                 "steps_histogram": worst_tun[2],
                                  "classes": len(best),
                                  "systems_with_changed_shape": changed},
             "config": {"workload": f"{systems_count} banded systems, n log-uniform [4096, 262144], "
                                    "k in {8,16,32,64}, r = k/4, dominance 1.5",
-                       "unknowns": total, "precision": "fp32", "refinement_steps": iterations,
-                       "graph": "one CUDA graph per batch (factor + solve of every system)"}}
+                       "unknowns": total, "precision": "fp32", "max_refinement_steps": iterations,
+                       "tol": 1e-10,
+                       "graph": "one CUDA graph per batch (factor + solve of every system); a system "
+                                "whose residual meets tol skips its remaining steps on the device"}}
 
 
 def fp64_peak_measured():

@@ -129,9 +129,12 @@ typedef struct {
     uint64_t seed;        /* default 0x4C52535049                                    */
     /* graph_safe = 1: factor and solve only enqueue work on the handle's stream
      * (no host synchronisation, no host reads, no allocation), so a caller can
-     * capture them in a CUDA graph and replay it.  The solve then runs exactly
+     * capture them in a CUDA graph and replay it.  The solve then enqueues
      * max_iter refinement steps (IR; NONE is one application) and leaves the
-     * final residual on the device; lrspike_finish reports the outcome.
+     * final residual on the device; lrspike_finish reports the outcome.  With
+     * IR, the residual that meets tol for every column sets a device flag and
+     * the kernels of the remaining enqueued steps return at entry (x and the
+     * residual norms stay those of the converged step).
      * Requires device buffers, outer IR or NONE, profile 0, k <= 64. */
     int32_t graph_safe;
     /* block: the block size KB (8, 16, 32 or 64, >= the smallest block that
@@ -206,8 +209,10 @@ lrspike_status lrspike_solve_transpose(lrspike_handle hd, const double *h, doubl
 
 /* For a graph_safe handle: waits for the handle's stream and reports the last
  * factorisation (SINGULAR as lrspike_factor would) and the last solve (info as
- * lrspike_solve fills it: iterations = max_iter, the per-column relative
- * residual of the final iterate; NOT_CONVERGED if a column is above tol).
+ * lrspike_solve fills it: iterations = the refinement steps that ran before
+ * the residual met tol (max_iter if it never did; 1 for NONE), the per-column
+ * relative residual of the final iterate; NOT_CONVERGED if a column is above
+ * tol).
  * STATE if nothing was solved since the last factor. */
 lrspike_status lrspike_finish(lrspike_handle h, lrspike_info *info);
 

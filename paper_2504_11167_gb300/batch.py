@@ -2,8 +2,10 @@
 CUDA-graph launch.
 
 Every system gets its own graph-safe LR-SPIKE handle (factor and solve only
-enqueue work: a fixed number of FP64 refinement steps, no host reads) on one
-of a pool of side streams.  `capture()` records the factorisations and solves
+enqueue work: up to `iterations` FP64 refinement steps, no host reads) on one
+of a pool of side streams.  The residual that meets tol raises a device flag
+of its system, and the kernels of that system's remaining steps return at
+entry, so a batch pays each system's own step count, not the worst case's.  `capture()` records the factorisations and solves
 of all systems into one CUDA graph, forked from the capture stream into the
 side streams and joined back, so independent systems run concurrently on the
 GPU; `replay()` launches the whole batch with a single graph launch; `finish()`

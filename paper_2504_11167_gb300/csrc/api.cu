@@ -101,7 +101,7 @@ static void free_all(Ctx *c) {
     void *ptrs[] = {c->off_d, c->boff_d, c->LT,   c->UT,  c->DI,   c->X,     c->Ucat,
                     c->PQ,    c->Gram,   c->Gpart, c->sigma, c->E, c->F,    c->Gs,    c->Rinv,
                     c->rv,     c->Yv,   c->Gv,  c->psi,  c->zr,   c->wr,    c->nrm,
-                    c->partial, c->counter, c->status, c->band_own, c->io_f, c->io_x, c->dots,
+                    c->partial, c->counter, c->status, c->stopf, c->band_own, c->io_f, c->io_x, c->dots,
                     c->bpartial, c->PF, c->PIVP, c->ocv, c->og, c->orv, c->osc, c->oone, c->xalt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -256,7 +256,8 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
                            dalloc(&c->DI, NB * KB * T)) &&
               dalloc(&c->rv, (size_t)c->n * mx * 8) && dalloc(&c->Yv, (size_t)c->n * mx * T) &&
               dalloc(&c->Gv, (size_t)c->n * mx * T) && dalloc(&c->nrm, 4 * mx * 8) &&
-              dalloc(&c->partial, (size_t)rb * mx * 8) && dalloc(&c->counter, 64) && dalloc(&c->status, 64);
+              dalloc(&c->partial, (size_t)rb * mx * 8) && dalloc(&c->counter, 64) && dalloc(&c->status, 64) &&
+              dalloc(&c->stopf, 16);
     if (ok && spikes) {
         ok = (wide ? true
                    : dalloc(&c->X, NB * KB * c->m * T) && dalloc(&c->Gram, (size_t)c->p * 2 * KB * KB * 8) &&
@@ -294,6 +295,7 @@ extern "C" lrspike_status lrspike_create(const lrspike_options *opt, void *strea
     cudaMemcpy(c->off_d, c->off_h.data(), (c->p + 1) * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(c->boff_d, c->boff_h.data(), (c->p + 1) * 8, cudaMemcpyHostToDevice);
     cudaMemset(c->counter, 0, 64);
+    cudaMemset(c->stopf, 0, 16);
     const cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_all(c);
@@ -375,6 +377,7 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
         }
     }
     if (!ok) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+    c->bcr_t_ready = gs;  // also after a replayed factorisation graph
     if (gs) {  // the status is read by lrspike_finish
         c->factored = true;
         c->last_nrhs = 0;
@@ -408,14 +411,30 @@ static lrspike_status solve_common(Ctx *c, const double *f, double *x, int nrhs,
     if (c->opt.graph_safe) {
         // device buffers; exactly max_iter refinement steps (NONE: one application);
         // the final residual stays on the device for lrspike_finish
+        // up to max_iter steps enqueued; with outer IR the residual that meets
+        // tol raises a device flag and the kernels of the remaining steps
+        // return at entry (the norms of that residual stay for lrspike_finish)
         const bool none = c->opt.outer == LRSPIKE_OUTER_NONE;
         const int steps = none ? 1 : c->opt.max_iter;
+        struct Reset {  // the rule is enqueue-time state of this call only
+            Ctx *c;
+            ~Reset() { c->stop = StopRule(); c->skip = nullptr; }
+        } reset{c};
         if (cudaMemset2DAsync(x, ld * 8, 0, c->n * 8, nrhs, c->stream) != cudaSuccess) return cuda_fail(c, "x reset");
+        if (cudaMemsetAsync(c->stopf, 0, 2 * sizeof(int), c->stream) != cudaSuccess) return cuda_fail(c, "flag reset");
         if (!run_norms(c, f, ld, nrhs, c->nrm)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        if (!none) {
+            c->stop.flag = c->stopf;
+            c->stop.fnrm = c->nrm;
+            c->stop.tol = c->opt.tol;
+            c->stop.count = 1;
+            c->skip = c->stopf;
+        }
         for (int it = 0; it < steps; ++it)
             if (!run_residual(c, f, x, ld, nrhs, trans, it == 0) ||
                 !apply_precond(c, c->rv, x, ld, nrhs, trans, true))
                 return fail(c, LRSPIKE_ERR_CUDA, c->err);
+        c->stop.count = 0;
         if (!run_residual(c, f, x, ld, nrhs, trans, false)) return fail(c, LRSPIKE_ERR_CUDA, c->err);
         c->last_nrhs = nrhs;
         if (info) {
@@ -586,8 +605,10 @@ extern "C" lrspike_status lrspike_finish(lrspike_handle h, lrspike_info *info) {
     const int nrhs = c->last_nrhs, mx = c->opt.max_nrhs;
     if (nrhs == 0) return fail(c, LRSPIKE_ERR_STATE, "no solve since the last factor");
     std::vector<double> nf(nrhs), nr(nrhs);
+    int flag[2] = {0, 0};
     if (cudaMemcpy(nf.data(), c->nrm, nrhs * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(nr.data(), c->nrm + mx, nrhs * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(nr.data(), c->nrm + mx, nrhs * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(flag, c->stopf, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess)
         return cuda_fail(c, "residual read");
     double worst = 0.0;
     bool ok = true;
@@ -597,7 +618,9 @@ extern "C" lrspike_status lrspike_finish(lrspike_handle h, lrspike_info *info) {
         ok = ok && rel <= c->opt.tol;
         worst = std::max(worst, (rel == rel) ? rel : INFINITY);
     }
-    const int steps = c->opt.outer == LRSPIKE_OUTER_NONE ? 1 : c->opt.max_iter;
+    // outer IR: the preconditioner applications that ran before the residual
+    // met tol (the rest of the enqueued steps returned at entry)
+    const int steps = c->opt.outer == LRSPIKE_OUTER_NONE ? 1 : flag[1];
     if (info) {
         info->iterations = steps;
         info->converged = ok ? 1 : 0;

@@ -53,6 +53,18 @@ struct Pending {
 
 // One handle.  Device arrays typed void* hold the working precision T
 // (double in FP64 mode, float in the mixed modes).
+// Early exit of a graph-safe refinement (a fixed number of enqueued steps):
+// the residual whose column norms all meet |r_j| <= tol |f_j| raises flag[0];
+// while it is up every later kernel of the loop returns at entry.  flag[1]
+// counts the residuals of the loop that found the tolerance unmet (= the
+// preconditioner applications that ran).  flag == nullptr: no rule.
+struct StopRule {
+    int *flag = nullptr;
+    const double *fnrm = nullptr;
+    double tol = 0.0;
+    int count = 0;  // 1: a miss adds one step to flag[1]
+};
+
 struct Ctx {
     lrspike_options opt{};
     cudaStream_t stream = nullptr;
@@ -101,6 +113,7 @@ struct Ctx {
     struct BcrSet {
         double *E = nullptr, *F = nullptr, *G = nullptr, *Einv = nullptr, *al = nullptr, *be = nullptr;
     } bcr[2];
+    bool bcr_t_ready = false;  // bcr[1] (R^T) reduced since the last factorisation
 
     // solve scratch (max_nrhs columns)
     double *rv = nullptr;     // FP64 residual / work vector, n x max_nrhs
@@ -114,6 +127,9 @@ struct Ctx {
     int64_t npartial = 0;
     unsigned int *counter = nullptr;
     int64_t *status = nullptr; // first singular global row (INT64_MAX = none)
+    int *stopf = nullptr;       // graph-safe early exit: [0] converged, [1] steps applied
+    StopRule stop;              // rule the residual applies during a graph-safe solve
+    const int *skip = nullptr;  // refinement kernels return at entry while *skip != 0
     double *host = nullptr;    // pinned host scratch
     // BiCGStab vectors (FP64, n x max_nrhs each: r, shadow r, p, v, s, t,
     // M^{-1}p, M^{-1}s), per-column scalars and reduction partials

@@ -653,8 +653,9 @@ template <typename T, int KB>
 __global__ void __launch_bounds__(4 * KB)
     k_dstage_piv(const T *__restrict__ PF, const unsigned char *__restrict__ PIV, const T *__restrict__ PQ, Parts P,
                  int k, int r, int64_t n, const double *__restrict__ rin, const double *__restrict__ inv, int nrhs,
-                 T *__restrict__ Yv, T *__restrict__ Gv, double *__restrict__ psi) {
+                 T *__restrict__ Yv, T *__restrict__ Gv, double *__restrict__ psi, const int *skip) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (skip && *skip) return;  // graph-safe refinement already met tol
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int64_t b0 = P.boff[part];
@@ -726,8 +727,9 @@ __global__ void __launch_bounds__(4 * KB)
     k_dstage_t_piv(const T *__restrict__ PF, const unsigned char *__restrict__ PIV, const T *__restrict__ PQ,
                    Parts P, int k, int r, int64_t n, const double *__restrict__ hin, const double *__restrict__ inv,
                    const double *__restrict__ zr, int nrhs, T *__restrict__ Yv, const double *__restrict__ nrm,
-                   double *__restrict__ x, int64_t ldx, int accumulate) {
+                   double *__restrict__ x, int64_t ldx, int accumulate, const int *skip) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (skip && *skip) return;
     T *corr = reinterpret_cast<T *>(smem_raw + PivSmem<T, KB, VW16>::bytes);
     const int part = blockIdx.x;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
@@ -797,7 +799,7 @@ bool dstage_piv_impl(Ctx *c, const double *rin, int nrhs) {
     return launch(c, KID_DSTAGE, [&] {
         kern<<<c->p, 4 * KB, smem, c->stream>>>((const T *)c->PF, c->PIVP, (const T *)c->PQ, P, c->k, c->r, c->n,
                                                rin, c->nrm + 2 * c->opt.max_nrhs, nrhs, (T *)c->Yv, (T *)c->Gv,
-                                               c->psi);
+                                               c->psi, c->skip);
     });
 }
 
@@ -810,7 +812,7 @@ bool dstage_t_piv_impl(Ctx *c, const double *hin, double *x, int64_t ldx, int nr
     return launch(c, KID_DSTAGE_T, [&] {
         kern<<<c->p, 4 * KB, smem, c->stream>>>((const T *)c->PF, c->PIVP, (const T *)c->PQ, P, c->k, c->r, c->n,
                                                hin, c->nrm + 2 * c->opt.max_nrhs, c->zr, nrhs, (T *)c->Yv,
-                                               c->nrm + c->opt.max_nrhs, x, ldx, acc);
+                                               c->nrm + c->opt.max_nrhs, x, ldx, acc, c->skip);
     });
 }
 

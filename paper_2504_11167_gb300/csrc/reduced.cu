@@ -286,16 +286,20 @@ __global__ void k_bcr_invert(const double *__restrict__ E, double *__restrict__ 
     store_inv(aug, Einv + (int64_t)i * nn, n2);
 }
 
-// one level of the reduction for the kept equation i = 2h(j+1) - 1 (CTA j)
+// one level of the reduction for the kept equation i = 2h(j+1) - 1: CTA
+// (j, y) forms rows [y RB, y RB + RB) of alpha_i, beta_i and of the new E_i,
+// G_i, F_i (each row of the update needs only that row of alpha and beta)
+constexpr int BCR_RB = 8;
 __global__ void k_bcr_reduce(double *__restrict__ E, double *__restrict__ F, double *__restrict__ G,
                              const double *__restrict__ Einv, double *__restrict__ al, double *__restrict__ be,
                              int m, int n2, int h) {
     extern __shared__ double sm[];
     const int j = blockIdx.x, i = 2 * h * (j + 1) - 1, lo = i - h, hi = i + h, nn = n2 * n2;
+    const int r0 = blockIdx.y * BCR_RB, nr = min(BCR_RB, n2 - r0);
     const bool has_hi = hi < m;
-    double *A = sm, *B = sm + nn;  // alpha, beta
-    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-        const int a = t / n2, b = t % n2;
+    double *A = sm, *B = sm + BCR_RB * n2;  // rows r0.. of alpha, beta
+    for (int t = threadIdx.x; t < nr * n2; t += blockDim.x) {
+        const int a = r0 + t / n2, b = t % n2;
         double sa = 0.0, sb = 0.0;
         for (int q = 0; q < n2; ++q) {
             sa += G[(int64_t)i * nn + a * n2 + q] * Einv[(int64_t)lo * nn + q * n2 + b];
@@ -303,24 +307,24 @@ __global__ void k_bcr_reduce(double *__restrict__ E, double *__restrict__ F, dou
         }
         A[t] = sa;
         B[t] = sb;
-        al[(int64_t)j * nn + t] = sa;
-        be[(int64_t)j * nn + t] = sb;
+        al[(int64_t)j * nn + a * n2 + b] = sa;
+        be[(int64_t)j * nn + a * n2 + b] = sb;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-        const int a = t / n2, b = t % n2;
-        double e = E[(int64_t)i * nn + t], g = 0.0, f = 0.0;
+    for (int t = threadIdx.x; t < nr * n2; t += blockDim.x) {
+        const int ra = t / n2, a = r0 + ra, b = t % n2;
+        double e = E[(int64_t)i * nn + a * n2 + b], g = 0.0, f = 0.0;
         for (int q = 0; q < n2; ++q) {
-            e -= A[a * n2 + q] * F[(int64_t)lo * nn + q * n2 + b];
-            g -= A[a * n2 + q] * G[(int64_t)lo * nn + q * n2 + b];
+            e -= A[ra * n2 + q] * F[(int64_t)lo * nn + q * n2 + b];
+            g -= A[ra * n2 + q] * G[(int64_t)lo * nn + q * n2 + b];
             if (has_hi) {
-                e -= B[a * n2 + q] * G[(int64_t)hi * nn + q * n2 + b];
-                f -= B[a * n2 + q] * F[(int64_t)hi * nn + q * n2 + b];
+                e -= B[ra * n2 + q] * G[(int64_t)hi * nn + q * n2 + b];
+                f -= B[ra * n2 + q] * F[(int64_t)hi * nn + q * n2 + b];
             }
         }
-        E[(int64_t)i * nn + t] = e;
-        G[(int64_t)i * nn + t] = g;
-        F[(int64_t)i * nn + t] = f;
+        E[(int64_t)i * nn + a * n2 + b] = e;
+        G[(int64_t)i * nn + a * n2 + b] = g;
+        F[(int64_t)i * nn + a * n2 + b] = f;
     }
 }
 
@@ -386,14 +390,14 @@ static BcrLevels bcr_levels(int m) {
     return L;
 }
 
-static bool bcr_factor(Ctx *c) {
+// set 0 reduces R, set 1 R^T
+static bool bcr_factor(Ctx *c, int t) {
     const int n2 = 2 * c->r, m = c->p - 1;
     const size_t nn = (size_t)n2 * n2;
     const BcrLevels L = bcr_levels(m);
-    const size_t inv_smem = (2 * nn + n2) * sizeof(double), red_smem = 2 * nn * sizeof(double);
+    const size_t inv_smem = (2 * nn + n2) * sizeof(double), red_smem = 2 * BCR_RB * n2 * sizeof(double);
     cudaFuncSetAttribute(k_bcr_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
-    cudaFuncSetAttribute(k_bcr_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem);
-    for (int t = 0; t < 2; ++t) {
+    {
         auto &b = c->bcr[t];
         if (!launch(c, KID_RED_FACTOR, [&] {
                 k_bcr_copy<<<m, 256, 0, c->stream>>>(c->E, c->F, c->Gs, m, n2, t, b.E, b.F, b.G);
@@ -407,8 +411,8 @@ static bool bcr_factor(Ctx *c) {
                 }))
                 return false;
             if (L.kept[l] > 0 && !launch(c, KID_RED_FACTOR, [&] {
-                    k_bcr_reduce<<<L.kept[l], 256, red_smem, c->stream>>>(b.E, b.F, b.G, b.Einv, b.al + off * nn,
-                                                                           b.be + off * nn, m, n2, h);
+                    k_bcr_reduce<<<dim3(L.kept[l], (n2 + BCR_RB - 1) / BCR_RB), 256, red_smem, c->stream>>>(
+                        b.E, b.F, b.G, b.Einv, b.al + off * nn, b.be + off * nn, m, n2, h);
                 }))
                 return false;
             off += L.kept[l];
@@ -425,6 +429,11 @@ static bool bcr_solve(Ctx *c, int nrhs, bool trans) {
     const int n2 = 2 * c->r, m = c->p - 1;
     const size_t nn = (size_t)n2 * n2, nv = (size_t)n2 * nrhs;
     const BcrLevels L = bcr_levels(m);
+    // R^T is reduced the first time a transposed solve needs it
+    if (trans && !c->bcr_t_ready) {
+        if (!bcr_factor(c, 1)) return false;
+        c->bcr_t_ready = true;
+    }
     auto &b = c->bcr[trans ? 1 : 0];
     if (cudaMemcpyAsync(c->wr, c->psi, (size_t)m * nv * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
         c->err = "reduced right-hand side copy failed";
@@ -498,7 +507,10 @@ bool run_reduced_factor(Ctx *c) {
         });
     }
     (void)ni;
-    return bcr_factor(c);
+    // a graph-safe handle reduces both now (a captured transposed solve must
+    // not depend on host state); others reduce R^T on first use
+    c->bcr_t_ready = c->opt.graph_safe != 0;
+    return bcr_factor(c, 0) && (!c->opt.graph_safe || bcr_factor(c, 1));
 }
 
 bool run_reduced_solve(Ctx *c, int nrhs, bool trans) {

@@ -24,7 +24,7 @@ constexpr int RBS = 256;  // rows per CTA in the row-parallel kernels
 // CTA (atomic ticket) sums all partials in CTA order and writes the norms.
 template <int NR>
 __device__ void reduce_columns(double (&ss)[NR], int nrhs, double *partial, unsigned *counter,
-                               double *nrm_out, double *inv_out) {
+                               double *nrm_out, double *inv_out, StopRule st = StopRule()) {
     __shared__ double red[NR][RBS / 32];
     __shared__ bool is_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -62,6 +62,12 @@ __device__ void reduce_columns(double (&ss)[NR], int nrhs, double *partial, unsi
             }
             __syncthreads();
         }
+        if (st.flag && threadIdx.x == 0) {  // early-exit rule (NaN norms never meet it)
+            bool met = true;
+            for (int c = 0; c < nrhs; ++c) met = met && nrm_out[c] <= st.tol * st.fnrm[c];
+            if (met) st.flag[0] = 1;
+            else st.flag[1] += st.count;
+        }
     }
     if (is_last && threadIdx.x == 0) *counter = 0u;  // ready for the next launch
 }
@@ -71,7 +77,8 @@ __global__ void __launch_bounds__(RBS)
     k_residual(const double *__restrict__ band, int64_t ldb, int k, int64_t n,
                const double *__restrict__ f, const double *__restrict__ x, int64_t ld, int nrhs,
                int trans, int xzero, double *__restrict__ r, double *partial, unsigned *counter,
-               double *nrm_out, double *inv_out, const int *__restrict__ dlist, int ndl) {
+               double *nrm_out, double *inv_out, const int *__restrict__ dlist, int ndl, StopRule st) {
+    if (st.flag && *(volatile int *)st.flag) return;  // an earlier residual met tol: x is final
     const int64_t i = blockIdx.x * (int64_t)RBS + threadIdx.x;
     double acc[NR], ss[NR];
 #pragma unroll
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(RBS)
                 ss[c] = acc[c] * acc[c];
             }
     }
-    reduce_columns<NR>(ss, nrhs, partial, counter, nrm_out, inv_out);
+    reduce_columns<NR>(ss, nrhs, partial, counter, nrm_out, inv_out, st);
 }
 
 // One row of the retrieval, shared by k_retrieve1 and k_residual_ret so the two
@@ -506,8 +513,9 @@ __global__ void __launch_bounds__(Geo<KB>::NT, 2)
     k_dstage(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
              const T *__restrict__ PQ, Parts P, int k, int r, int64_t n, const double *__restrict__ rin,
              const double *__restrict__ inv, int nrhs, T *__restrict__ Yv, T *__restrict__ Gv,
-             double *__restrict__ psi) {
+             double *__restrict__ psi, const int *skip) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (skip && *skip) return;
     if (nrhs < 4)
         dstage_body<T, KB, Split::DOTS, NBUF>(LT, UT, DI, PQ, P, k, r, n, rin, inv, nrhs, Yv, Gv, psi, smem_raw);
     else
@@ -522,8 +530,9 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(RBS)
     k_retrieve(const T *__restrict__ Gv, const T *__restrict__ Ucat, const double *__restrict__ zr,
                Parts P, int r, int64_t n, int nrhs, const double *__restrict__ nrm, double *__restrict__ x,
-               int64_t ld, int accumulate) {
+               int64_t ld, int accumulate, const int *skip) {
     extern __shared__ double zs[];  // [2r][nrhs]: zeta_part, omega_part
+    if (skip && *skip) return;
     const int part = blockIdx.y;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int n2 = 2 * r;
@@ -574,7 +583,9 @@ __global__ void __launch_bounds__(RBS)
 template <typename T, int NQ>
 __global__ void __launch_bounds__(RBS)
     k_retrieve1(const T *__restrict__ Gv, const T *__restrict__ Ucat, const double *__restrict__ zr, Parts P,
-                int r, int64_t n, const double *__restrict__ nrm, double *__restrict__ x, int accumulate) {
+                int r, int64_t n, const double *__restrict__ nrm, double *__restrict__ x, int accumulate,
+                const int *skip) {
+    if (skip && *skip) return;
     const int part = blockIdx.y;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int n2 = 2 * r;
@@ -722,8 +733,10 @@ __global__ void __launch_bounds__(Geo<KB>::NT)
     k_dstage_t(const T *__restrict__ LT, const T *__restrict__ UT, const T *__restrict__ DI,
                const T *__restrict__ PQ, Parts P, int k, int r, int64_t n, const double *__restrict__ hin,
                const double *__restrict__ inv, const double *__restrict__ zr, int nrhs, T *__restrict__ Yv,
-               const double *__restrict__ nrm, double *__restrict__ x, int64_t ldx, int accumulate) {
+               const double *__restrict__ nrm, double *__restrict__ x, int64_t ldx, int accumulate,
+               const int *skip) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (skip && *skip) return;
     if (nrhs < 4)
         dstage_t_body<T, KB, Split::DOTS>(LT, UT, DI, PQ, P, k, r, n, hin, inv, zr, nrhs, Yv, nrm, x, ldx,
                                           accumulate, smem_raw);
@@ -741,7 +754,7 @@ static bool residual_nr(Ctx *c, const double *f, const double *x, int64_t ld, in
     return launch(c, KID_RESIDUAL, [&] {
         k_residual<NR><<<row_blocks(c->n), RBS, 0, c->stream>>>(
             c->band, c->ld, c->k, c->n, f, x, ld, nrhs, trans, xz, c->rv, c->partial, c->counter,
-            c->nrm + c->opt.max_nrhs, c->nrm + 2 * c->opt.max_nrhs, c->diag_list, c->ndiag);
+            c->nrm + c->opt.max_nrhs, c->nrm + 2 * c->opt.max_nrhs, c->diag_list, c->ndiag, c->stop);
     });
 }
 
@@ -752,11 +765,11 @@ bool launch_residual_raw(const double *band, int64_t ldb, int k, int64_t n, cons
                          unsigned *counter, double *nrm, cudaStream_t st) {
     const unsigned g = row_blocks(n);
     switch (nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16) {
-        case 1: k_residual<1><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
-        case 2: k_residual<2><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
-        case 4: k_residual<4><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
-        case 8: k_residual<8><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
-        default: k_residual<16><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0); break;
+        case 1: k_residual<1><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0, StopRule()); break;
+        case 2: k_residual<2><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0, StopRule()); break;
+        case 4: k_residual<4><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0, StopRule()); break;
+        case 8: k_residual<8><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0, StopRule()); break;
+        default: k_residual<16><<<g, RBS, 0, st>>>(band, ldb, k, n, f, x, ld, nrhs, 0, 0, r, partial, counter, nrm, nullptr, nullptr, 0, StopRule()); break;
     }
     return cudaGetLastError() == cudaSuccess;
 }
@@ -800,7 +813,7 @@ static bool dstage_launch(Ctx *c, const double *rin, int nrhs, const double *inv
     return launch(c, KID_DSTAGE, [&] {
         kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT, (const T *)c->DI,
                                                      (const T *)c->PQ, P, c->k, c->r, c->n, rin, inv, nrhs,
-                                                     (T *)c->Yv, (T *)c->Gv, c->psi);
+                                                     (T *)c->Yv, (T *)c->Gv, c->psi, c->skip);
     });
 }
 
@@ -822,7 +835,7 @@ static bool dstage_t_impl(Ctx *c, const double *hin, double *x, int64_t ldx, int
         kern<<<c->p, Geo<KB>::NT, smem, c->stream>>>((const T *)c->LT, (const T *)c->UT, (const T *)c->DI,
                                                      (const T *)c->PQ, P, c->k, c->r, c->n, hin,
                                                      c->nrm + 2 * c->opt.max_nrhs, c->zr, nrhs, (T *)c->Yv,
-                                                     c->nrm + c->opt.max_nrhs, x, ldx, acc);
+                                                     c->nrm + c->opt.max_nrhs, x, ldx, acc, c->skip);
     });
 }
 
@@ -833,7 +846,7 @@ static bool retrieve1_nq(Ctx *c, double *x, int acc) {
     dim3 grid((unsigned)((c->maxni + RBS * RPT - 1) / (RBS * RPT)), c->p);
     return launch(c, KID_RETRIEVE, [&] {
         k_retrieve1<T, NQ><<<grid, RBS, 0, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r, c->n,
-                                                        c->nrm + c->opt.max_nrhs, x, acc);
+                                                        c->nrm + c->opt.max_nrhs, x, acc, c->skip);
     });
 }
 
@@ -853,13 +866,13 @@ static bool retrieve_impl(Ctx *c, double *x, int64_t ld, int nrhs, int acc) {
     return launch(c, KID_RETRIEVE, [&] {
         if (nrhs <= 4)
             k_retrieve<T, 4><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r,
-                                                            c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc);
+                                                            c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc, c->skip);
         else if (nrhs <= 8)
             k_retrieve<T, 8><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r,
-                                                            c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc);
+                                                            c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc, c->skip);
         else
             k_retrieve<T, 16><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P,
-                                                             c->r, c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc);
+                                                             c->r, c->n, nrhs, c->nrm + c->opt.max_nrhs, x, ld, acc, c->skip);
     });
 }
 

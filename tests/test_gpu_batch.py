@@ -1,6 +1,7 @@
 """Batched uneven systems in one CUDA-graph launch (graph-safe handles on a
 pool of streams): every system converges to 1e-10 (FP32 factors, FP64
 refinement), replaying the graph reproduces the eager launches bit for bit,
+a system whose residual meets tol skips its remaining steps on the device,
 and the autotuner returns a shape that solves its class."""
 import numpy as np
 import pytest
@@ -71,4 +72,63 @@ def test_autotune_picks_a_working_candidate(torch_cuda):
     b = batch.BatchSolver([(band, ft, k)], shapes=[shape], iterations=8, streams=1)
     b.run_eager()
     assert b.finish()[0]["converged"]
+    b.close()
+
+
+def test_graph_safe_refinement_exits_on_the_device(torch_cuda):
+    """A graph-safe IR solve enqueues max_iter steps; the residual that meets
+    tol raises the handle's device flag and the remaining steps return at
+    entry.  The reported step count equals the host-driven IR's, x equals (bit
+    for bit) the x of a graph-safe solve enqueued with exactly that many
+    steps, and an unreachable tol (0) runs every step."""
+    torch = torch_cuda
+    from paper_2504_11167_gb300.solver import LRSpike
+    n, k, p, r = 30000, 16, 6, 4
+    ab = inputs.dominant_band(n, k, 1.5, 77)
+    f = inputs.rhs(n, 1, 77)
+    band = torch.from_numpy(ab).cuda()
+    ft = torch.from_numpy(np.ascontiguousarray(f.T)).cuda()
+
+    def graph_safe(max_iter, tol):
+        with LRSpike(n, k, p, r, precision="fp32", reduced="truncated", outer="ir", tol=tol,
+                     max_iter=max_iter, max_nrhs=1, graph_safe=True) as s:
+            s.factor(band)
+            x = torch.empty_like(ft)
+            s.solve(ft, x)
+            info = s.finish(nrhs=1, allow_unconverged=True)
+        return x, info
+
+    x30, i30 = graph_safe(30, 1e-10)
+    assert i30["converged"] and 1 <= i30["iterations"] < 30
+    with LRSpike(n, k, p, r, precision="fp32", reduced="truncated", outer="ir", tol=1e-10, max_iter=30) as s:
+        s.factor(band)
+        _, ih = s.solve(ft)
+    assert ih["iterations"] == i30["iterations"]
+    xe, ie = graph_safe(i30["iterations"], 1e-10)
+    assert ie["converged"] and ie["iterations"] == i30["iterations"]
+    assert torch.equal(x30, xe)
+    assert ie["max_rel_residual"] == i30["max_rel_residual"]
+    x0, i0 = graph_safe(5, 0.0)
+    assert not i0["converged"] and i0["iterations"] == 5
+
+
+def test_graph_replays_reset_the_exit_flag(torch_cuda):
+    """Each replay clears the flag before its first residual: a batch replayed
+    twice reports the same step counts and the same x."""
+    torch = torch_cuda
+    from paper_2504_11167_gb300.batch import BatchSolver
+    systems, _ = make_systems(torch, 6, 900)
+    b = BatchSolver(systems, iterations=12, streams=3)
+    b.capture()
+    b.replay()
+    first = b.finish()
+    x1 = [x.clone() for x in b.x]
+    for x in b.x:
+        x.fill_(float("nan"))
+    b.replay()
+    second = b.finish()
+    assert [i["iterations"] for i in first] == [i["iterations"] for i in second]
+    assert all(i["converged"] and i["iterations"] < 12 for i in second)
+    for a, c in zip(x1, b.x):
+        assert torch.equal(a, c)
     b.close()

@@ -3,8 +3,8 @@ k <= 64 factors, every partition holding >= 256 + 2k rows): the retrieval
 x += |r| (g - U z) of an application is formed by the next residual kernel,
 the iterate alternating between the caller's buffer and a second one.
 
-* Bit-identical to the separate kernels: a graph-safe handle runs exactly
-  max_iter unfused steps (residual, D-stage, reduced solve, retrieval), the
+* Bit-identical to the separate kernels: a graph-safe handle with an
+  unreachable tol runs exactly max_iter unfused steps (residual, D-stage, reduced solve, retrieval), the
   same arithmetic in the same order; after the same number of steps the two
   iterates agree bit for bit, for an even and an odd step count (the fused
   loop's result then sits in one or the other buffer).
@@ -45,7 +45,8 @@ def run_pair(torch, case, precision, steps):
         s.factor(band)
         xf, info = s.solve(f, allow_unconverged=True)
         xf = xf.clone()
-    with LRSpike(n, k, p, r, precision=precision, compress=comp, max_iter=steps, graph_safe=True) as s:
+    with LRSpike(n, k, p, r, precision=precision, compress=comp, tol=1e-300, max_iter=steps,
+                 graph_safe=True) as s:
         s.factor(band)
         xg, _ = s.solve(f)
         s.finish(nrhs=1, allow_unconverged=True)
