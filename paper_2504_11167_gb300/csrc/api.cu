@@ -120,6 +120,90 @@ static void free_all(Ctx *c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
+    for (auto e : c->grp_ev) cudaEventDestroy(e);
+    for (auto st : c->grp_streams) cudaStreamDestroy(st);
+    if (c->ev_up) cudaEventDestroy(c->ev_up);
+    if (c->ev_strips) cudaEventDestroy(c->ev_strips);
+    if (c->up) cudaStreamDestroy(c->up);
+}
+
+// A host band is uploaded in groups of partitions overlapped with the band LU
+// when the LU is the column kernel (unpivoted, FP32 / FP64 working precision,
+// k <= 64) and there are partitions to overlap.
+static bool upload_pipelined(const Ctx *c) {
+    return !c->wide && !c->opt.pivoting && c->opt.precision != LRSPIKE_MIXED_TF32 && c->p >= 2;
+}
+
+static int upload_groups(const Ctx *c) { return std::min(c->p, 16); }
+
+static bool upload_setup(Ctx *c) {
+    if (c->up) return true;
+    const int G = upload_groups(c);
+    bool ok = cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->ev_strips, cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 0; ok && g < G; ++g) {
+        cudaStream_t st = nullptr;
+        ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) c->grp_streams.push_back(st);
+    }
+    for (int e = 0; ok && e < 2 * G; ++e) {
+        cudaEvent_t ev = nullptr;
+        ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) c->grp_ev.push_back(ev);
+    }
+    return ok;
+}
+
+// Enqueues the upload of a host band into band_own on the upload stream (after
+// the handle's earlier work): with a coupling branch first the 2k columns
+// around every interface (B_i, C_i; event ev_strips), then the partition
+// groups' columns, each followed by its event grp_ev[2g].  Every column range
+// is a pitched copy of the 2k+1 band rows.  The group copies rewrite the
+// interface columns with the same bytes.
+static bool upload_band(Ctx *c, const double *band, int64_t ld) {
+    const int G = upload_groups(c), rows = 2 * c->k + 1;
+    auto copy_cols = [&](int64_t c0, int64_t c1) {
+        return c1 <= c0 || cudaMemcpy2DAsync(c->band_own + c0, ld * 8, band + c0, ld * 8, (size_t)(c1 - c0) * 8,
+                                             rows, cudaMemcpyHostToDevice, c->up) == cudaSuccess;
+    };
+    if (cudaEventRecord(c->ev_up, c->stream) != cudaSuccess || cudaStreamWaitEvent(c->up, c->ev_up, 0) != cudaSuccess)
+        return false;
+    if (c->side) {
+        for (int i = 1; i < c->p; ++i) {
+            const int64_t e = c->off_h[i];
+            if (!copy_cols(std::max<int64_t>(0, e - c->k), std::min<int64_t>(c->n, e + c->k))) return false;
+        }
+        if (cudaEventRecord(c->ev_strips, c->up) != cudaSuccess) return false;
+    }
+    for (int g = 0; g < G; ++g) {
+        const int g0 = (int)((int64_t)g * c->p / G), g1 = (int)((int64_t)(g + 1) * c->p / G);
+        if (!copy_cols(c->off_h[g0], c->off_h[g1]) || cudaEventRecord(c->grp_ev[2 * g], c->up) != cudaSuccess)
+            return false;
+    }
+    return true;
+}
+
+// The band LU of each partition group on its own stream, after its upload;
+// the handle's stream waits for all of them.
+static bool band_lu_grouped(Ctx *c) {
+    const int G = upload_groups(c);
+    cudaStream_t own = c->stream;
+    bool ok = true;
+    for (int g = 0; ok && g < G; ++g) {
+        cudaStream_t st = c->grp_streams[g];
+        c->lu_g0 = (int)((int64_t)g * c->p / G);
+        c->lu_g1 = (int)((int64_t)(g + 1) * c->p / G);
+        ok = cudaStreamWaitEvent(st, c->grp_ev[2 * g], 0) == cudaSuccess;
+        c->stream = st;
+        ok = ok && run_band_lu(c);
+        c->stream = own;
+        ok = ok && cudaEventRecord(c->grp_ev[2 * g + 1], st) == cudaSuccess &&
+             cudaStreamWaitEvent(own, c->grp_ev[2 * g + 1], 0) == cudaSuccess;
+    }
+    c->lu_g0 = 0;
+    c->lu_g1 = -1;
+    return ok;
 }
 
 extern "C" lrspike_status lrspike_options_default(lrspike_options *o, int64_t n, int32_t k, int32_t p,
@@ -323,6 +407,7 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
     cudaSetDevice(c->device);
     c->factored = false;
     const bool gs = c->opt.graph_safe != 0;  // enqueue only: no host reads, no synchronisation
+    bool piped = false;  // host band uploaded in groups beside the band LU
     if (gs || is_device_ptr(band)) {
         c->band = band;
     } else {
@@ -334,8 +419,12 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
             if (!dalloc(&c->band_own, bytes)) return fail(c, LRSPIKE_ERR_OOM, "band copy allocation failed");
             c->band_own_bytes = bytes;
         }
-        if (cudaMemcpyAsync(c->band_own, band, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        piped = upload_pipelined(c);
+        if (piped) {
+            if (!upload_setup(c)) return cuda_fail(c, "upload stream creation");
+        } else if (cudaMemcpyAsync(c->band_own, band, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
             return cuda_fail(c, "band host-to-device copy");
+        }
         c->band = c->band_own;
     }
     c->ld = ld;
@@ -348,6 +437,7 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
             return cuda_fail(c, "status reset");
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "stream sync");
     }
+    if (piped && !upload_band(c, band, ld)) return cuda_fail(c, "band host-to-device copy");
     bool ok;
     if (c->side) {
         // Coupling compression: the Gram matrices of B_i and C_i, their
@@ -355,8 +445,13 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
         // they run on the side stream while the band LU (one CTA per
         // partition, SMs not full) runs on the handle's stream; the spike
         // sweep waits for both.  The LU is enqueued first.
-        ok = cudaEventRecord(c->ev_fork, c->stream) == cudaSuccess && run_band_lu(c) &&
-             cudaStreamWaitEvent(c->side, c->ev_fork, 0) == cudaSuccess;
+        // (a host band: the side stream starts once the interface columns have
+        // landed, the LU per partition group as its columns land)
+        if (piped)
+            ok = band_lu_grouped(c) && cudaStreamWaitEvent(c->side, c->ev_strips, 0) == cudaSuccess;
+        else
+            ok = cudaEventRecord(c->ev_fork, c->stream) == cudaSuccess && run_band_lu(c) &&
+                 cudaStreamWaitEvent(c->side, c->ev_fork, 0) == cudaSuccess;
         if (ok) {
             cudaStream_t own = c->stream;
             c->stream = c->side;
@@ -367,7 +462,7 @@ extern "C" lrspike_status lrspike_factor(lrspike_handle h, const double *band, i
         }
         ok = ok && run_sweep(c) && run_make_u(c) && run_reduced_build(c) && run_reduced_factor(c);
     } else {
-        ok = c->wide ? run_wide_factor(c) : run_band_lu(c);
+        ok = c->wide ? run_wide_factor(c) : piped ? band_lu_grouped(c) : run_band_lu(c);
         if (ok && !c->wide && c->p > 1 && c->r > 0) {
             if (c->opt.compress == LRSPIKE_COMPRESS_COUPLING)
                 ok = run_coupling_gram(c) && run_jacobi(c) && run_spike_rhs(c) && run_sweep(c) && run_make_u(c);

@@ -716,7 +716,11 @@ __global__ void __launch_bounds__(InvGeo<T, KB>::NT) k_band_lu_inv(T *__restrict
 
 template <typename T, int KB>
 static bool col_impl(Ctx *c) {
-    Parts P{c->off_d, c->boff_d, c->p};
+    // partitions [g0, g1): a Parts view starting at g0 (the kernels index
+    // rows and blocks through the offsets, which stay global)
+    const int g0 = c->lu_g1 < 0 ? 0 : c->lu_g0, g1 = c->lu_g1 < 0 ? c->p : c->lu_g1;
+    const int64_t b0 = c->boff_h[g0], nb = c->boff_h[g1] - b0;
+    Parts P{c->off_d + g0, c->boff_d + g0, g1 - g0};
     const size_t sm1 = ColSmem<T, KB>::bytes, sm2 = InvGeo<T, KB>::bytes;
     if constexpr (sizeof(T) == 4)
         cudaFuncSetAttribute(k_band_lu_col<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
@@ -725,17 +729,18 @@ static bool col_impl(Ctx *c) {
         const size_t smc = Col1Smem<T, KB>::bytes;
         cudaFuncSetAttribute(k_band_lu_col1<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
         if (!launch(c, KID_LU, [&] {
-                k_band_lu_col1<T, KB><<<c->p, Col1Geo<T, KB>::NT, smc, c->stream>>>(
+                k_band_lu_col1<T, KB><<<g1 - g0, Col1Geo<T, KB>::NT, smc, c->stream>>>(
                     c->band, c->ld, c->k, P, (T *)c->LT, (T *)c->UT, (T *)c->DI, c->status);
             }))
             return false;
     } else if (!launch(c, KID_LU, [&] {
-                   k_band_lu_col<T, KB><<<c->p, ColGeo<T, KB>::NT, sm1, c->stream>>>(
+                   k_band_lu_col<T, KB><<<g1 - g0, ColGeo<T, KB>::NT, sm1, c->stream>>>(
                        c->band, c->ld, c->k, P, (T *)c->LT, (T *)c->UT, (T *)c->DI, c->status);
                }))
         return false;
     return launch(c, KID_LU_INV, [&] {
-        k_band_lu_inv<T, KB><<<(unsigned)c->NB, InvGeo<T, KB>::NT, sm2, c->stream>>>((T *)c->LT, (T *)c->UT);
+        k_band_lu_inv<T, KB><<<(unsigned)nb, InvGeo<T, KB>::NT, sm2, c->stream>>>(
+            (T *)c->LT + b0 * KB * KB, (T *)c->UT + b0 * KB * KB);
     });
 }
 

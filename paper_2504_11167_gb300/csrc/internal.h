@@ -79,6 +79,15 @@ struct Ctx {
     // into Ucat itself (run_make_u then has nothing to do)
     bool u_by_sweep = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // factorisation of a host band (k <= 64, band LU by the column kernel):
+    // the upload runs on its own stream in partition groups (the columns
+    // around every interface first, for the coupling branch), and each
+    // group's band LU starts on its own stream as soon as its columns land
+    cudaStream_t up = nullptr;
+    std::vector<cudaStream_t> grp_streams;
+    std::vector<cudaEvent_t> grp_ev;  // [2g]: group g uploaded, [2g+1]: its LU done
+    cudaEvent_t ev_up = nullptr, ev_strips = nullptr;
+    int lu_g0 = 0, lu_g1 = -1;        // partitions [lu_g0, lu_g1) of the next band LU (lu_g1 < 0: all)
     int device = 0;
     int KB = 8;          // block size (>= k, power of two in 8..64)
     bool fp64 = true;    // working precision is double
