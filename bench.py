@@ -38,6 +38,10 @@ the oracle on one thread and LAPACK's banded solve (scipy.solve_banded).
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        python bench.py --profile-case   (one factor + solve at n = 1,048,576,
                                          p = 64: the case used for ncu captures)
+       python bench.py --profile-wide NX (one factor + BiCGStab solve of the
+                                         convection-diffusion system on an NX x NX
+                                         grid, k = NX, TF32, 4 RHS, n_i = 16,384:
+                                         the case of the wide-band ncu captures)
 With N > 1 (torchrun), every rank solves its own copy of the workload (the
 path needs no exchange between independent systems; weak scaling).
 """
@@ -73,6 +77,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--profile-wide", type=int, default=0, metavar="NX",
+                    help="convection-diffusion case on an NX x NX grid for wide-band ncu captures")
     ap.add_argument("--profile-partitions", type=int, default=0,
                     help="partitions of the --profile-case run (default p/4: the bench's n_i; "
                          "256: the bench's CTA count at n_i = 4096)")
@@ -302,9 +308,11 @@ def cd_variant(band, f, precision: str, r: int, steps: int, warmup: int, dev, pe
                                                                  if precision == "tf32" else ""),
             "work": "algorithmic: band LU 2nk^2 + spikes 6nk^2 + randomized truncation, per factorisation"}
     if ds_cnt:
-        # nonzero triangles of the four W x W factor tiles per block step, FP32
+        # nonzero triangles of the four W x W factor tiles per block step (FP32
+        # tiles; BF16 tiles with BF16 factors) + the FP32 vectors
         W, NBW = 1024, 16
-        bytes_per = 4 * (W * (W + 1) // 2) * 4 * NBW * p + n * nrhs * 4 * 4
+        tile_b = 2 if precision == "bf16" else 4
+        bytes_per = tile_b * (W * (W + 1) // 2) * 4 * NBW * p + n * nrhs * 4 * 4
         ach = bytes_per / (ds_ms / ds_cnt * 1e-3) / 1e9
         pk = peaks.get("hbm_gbs", 6800.0)
         roof["dstage"] = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
@@ -529,10 +537,41 @@ def profile_case(parts: int = 0):
                                        "rel_residual": info["max_rel_residual"]}}))
 
 
+def profile_wide(nx: int):
+    """One factorisation + BiCGStab solve of the convection-diffusion system on
+    an nx x nx grid (k = nx, Pe 0.5, TF32 operands, r = 16, 4 RHS, partitions of
+    16,384 rows as in the 1024^2 configuration): the tensor-core products and
+    the cluster D-stage at a size ncu replays quickly (nx = 512: a 2.1 GB band,
+    larger than L2)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_11167_gb300 import inputs
+    from paper_2504_11167_gb300.solver import LRSpike
+    dev = torch.device("cuda", 0)
+    band = cd_band_device(nx, 0.5, dev)
+    n, k = nx * nx, nx
+    p = max(2, n // 16384)
+    g = torch.Generator(device=dev)
+    g.manual_seed(inputs.SEED_BASE + 3)
+    f = torch.rand(4, n, generator=g, dtype=torch.float64, device=dev) * 2.0 - 1.0
+    with LRSpike(n, k, p, 16, precision="tf32", reduced="truncated", outer="bicgstab", tol=1e-10,
+                 max_iter=400, max_nrhs=4) as s:
+        s.factor(band)
+        x, info = s.solve(f)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_wide": {"n": n, "k": k, "p": p, "r": 16, "iterations": info["iterations"],
+                                       "rel_residual": info["max_rel_residual"]}}))
+    if not info["converged"]:
+        raise SystemExit("profile_wide: not converged")
+
+
 def main():
     args = parse()
     if args.profile_case:
         return profile_case(args.profile_partitions)
+    if args.profile_wide:
+        return profile_wide(args.profile_wide)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -60,7 +60,8 @@ typedef enum {
  * product of the factorisation and the spike compression (tcgen05, FP32
  * accumulator).  MIXED_BF16 (k > 64 only): those block products take BF16
  * operands (rounded to nearest even from the FP32 values), FP32 accumulation;
- * factors are stored in FP32 and the D-stage runs in FP32. */
+ * the D-stage streams the BF16 copies of the factor tiles (half the bytes)
+ * and accumulates in FP32. */
 enum { LRSPIKE_FP64 = 0, LRSPIKE_MIXED_FP32 = 1, LRSPIKE_MIXED_TF32 = 2, LRSPIKE_MIXED_BF16 = 3 };
 /* Compression of the spikes (section 3.1): SPIKE = truncated SVD of the
  * explicit spikes T_i, W_i (the paper's choice, optimal by Eckart-Young);

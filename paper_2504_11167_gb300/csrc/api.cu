@@ -131,7 +131,8 @@ static void free_all(Ctx *c) {
 // when the LU is the column kernel (unpivoted, FP32 / FP64 working precision,
 // k <= 64) and there are partitions to overlap.
 static bool upload_pipelined(const Ctx *c) {
-    return !c->wide && !c->opt.pivoting && c->opt.precision != LRSPIKE_MIXED_TF32 && c->p >= 2;
+    // (a profiling handle times every launch on the handle's stream: one LU)
+    return !c->wide && !c->opt.pivoting && c->opt.precision != LRSPIKE_MIXED_TF32 && c->p >= 2 && !c->profile;
 }
 
 static int upload_groups(const Ctx *c) { return std::min(c->p, 16); }
@@ -184,8 +185,10 @@ static bool upload_band(Ctx *c, const double *band, int64_t ld) {
     return true;
 }
 
-// The band LU of each partition group on its own stream, after its upload;
-// the handle's stream waits for all of them.
+// The band LU of each partition group, then its triangular inverses, on the
+// group's own stream after the group's upload; the handle's stream waits for
+// all of them.  (A device band keeps one LU launch over all partitions:
+// sixteen concurrent group launches of the same CTAs measured slower.)
 static bool band_lu_grouped(Ctx *c) {
     const int G = upload_groups(c);
     cudaStream_t own = c->stream;

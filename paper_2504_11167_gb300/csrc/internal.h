@@ -175,6 +175,7 @@ struct Ctx {
     void *WQk = nullptr;                    // [2p][PS x lp]: orthonormal range basis (working)
     void *WZk = nullptr, *WZc = nullptr;    // [2p][W x lp]: T^T Q (working / operand BF16)
     void *WG = nullptr;                     // [2p][lp x lp] Gram (working)
+    void *WGp = nullptr;                    // [2p][gram chunks of PS][lp x lp] partial Grams over row chunks
     double *WGd = nullptr;                  // [2p][lp x lp] FP64 Gram
     void *WRi = nullptr;                    // [2p][lp x lp] R^{-1} of the CholeskyQR pass
     void *WE = nullptr;                     // [2p][r][lp] leading eigenvectors

@@ -327,14 +327,21 @@ __global__ void __launch_bounds__(TTHREADS, 2)
                 const int nv = min(32, P.N - nb);
                 if (P.f) {
                     float *fp = P.f + (int64_t)b * P.sf + m;
+                    if (P.beta != 0.0f) {
+                        // all 32 reads of C before the first write of the
+                        // same array, so they are in flight together
+                        float cin[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) cin[j] = (j < nv) ? fp[(int64_t)(nb + j) * P.ldf] : 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = fmaf(P.beta, cin[j], P.alpha * v[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] *= P.alpha;
+                    }
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (j < nv) {
-                            float val = P.alpha * v[j];
-                            if (P.beta != 0.0f) val = fmaf(P.beta, fp[(int64_t)(nb + j) * P.ldf], val);
-                            fp[(int64_t)(nb + j) * P.ldf] = val;
-                            v[j] = val;
-                        }
+                        if (j < nv) fp[(int64_t)(nb + j) * P.ldf] = v[j];
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] *= P.alpha;

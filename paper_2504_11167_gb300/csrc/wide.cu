@@ -138,6 +138,15 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
     }
+    // the reads of C (beta != 0) all before the first write of C
+    T cin[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + tx + 16 * i, n = n0 + ty + 16 * j;
+            cin[i][j] = (beta != T(0) && m < M && n < N) ? C[(int64_t)b * sc + m + (int64_t)n * ldc] : T(0);
+        }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -146,7 +155,7 @@ __global__ void __launch_bounds__(256)
             if (m < M && n < N) {
                 T v = alpha * acc[i][j];
                 const int64_t ci = (int64_t)b * sc + m + (int64_t)n * ldc;
-                if (beta != T(0)) v = fma(beta, C[ci], v);
+                if (beta != T(0)) v = fma(beta, cin[i][j], v);
                 if (C) C[ci] = v;
                 if (Cr) Cr[(int64_t)b * sr + n + (int64_t)m * ldr] = v;
             }
@@ -398,6 +407,72 @@ __global__ void k_wide_sketch(O *__restrict__ Om, int W, int k, int ell, int lp,
             v = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
         }
         Om[e] = cvtd<O>(v);
+    }
+}
+
+// Gram matrices Y_m^T Y_m of the 2p sketch iterates (Y_m column-major,
+// PS x lp, leading dimension PS) split over row chunks so that every SM has
+// work: CTA (tile, c, m) forms the 64 x 64 output tile of the partial Gram of
+// rows [c GRAM_ROWS, (c+1) GRAM_ROWS) (16-row slabs in shared memory, 4 x 4
+// per thread); k_gram_sum adds the chunks in a fixed order in FP64.
+constexpr int GRAM_ROWS = 1024;
+inline int gram_chunks(int64_t PS) { return (int)((PS + GRAM_ROWS - 1) / GRAM_ROWS); }
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_gram_part(const T *__restrict__ Y, int lp, int64_t PS, int64_t sY, T *__restrict__ part) {
+    __shared__ T As[16][65], Bs[16][65];
+    const int tiles = (lp + 63) / 64;
+    const int m0 = (blockIdx.x % tiles) * 64, n0 = (blockIdx.x / tiles) * 64, ch = blockIdx.y, mat = blockIdx.z;
+    const T *Ym = Y + (int64_t)mat * sY;
+    const int64_t r0 = (int64_t)ch * GRAM_ROWS, r1 = min(PS, r0 + GRAM_ROWS);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int64_t k0 = r0; k0 < r1; k0 += 16) {
+        for (int e = threadIdx.x; e < 1024; e += 256) {
+            const int kk = e & 15, mm = e >> 4;
+            const int64_t gk = k0 + kk;
+            As[kk][mm] = (gk < r1 && m0 + mm < lp) ? Ym[gk + (int64_t)(m0 + mm) * PS] : T(0);
+            Bs[kk][mm] = (gk < r1 && n0 + mm < lp) ? Ym[gk + (int64_t)(n0 + mm) * PS] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    T *out = part + ((int64_t)mat * gridDim.y + ch) * lp * lp;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int a = m0 + tx + 16 * i, b = n0 + ty + 16 * j;
+            if (a < lp && b < lp) out[a + (int64_t)b * lp] = acc[i][j];
+        }
+}
+
+template <typename T>
+__global__ void k_gram_sum(const T *__restrict__ part, int nch, int64_t sG, int64_t count, double *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t mat = e / sG, idx = e % sG;
+        const T *src = part + mat * nch * sG + idx;
+        double s = 0.0;
+        for (int c = 0; c < nch; ++c) s += (double)src[(int64_t)c * sG];
+        out[e] = s;
     }
 }
 
@@ -680,6 +755,15 @@ struct V4 {
 };
 // four consecutive shared-memory values (16-byte aligned), one vector load
 template <typename T>
+__device__ __forceinline__ V4<T> lds4(const T *p);
+// four BF16 tile values (8-byte aligned) widened to FP32: a BF16 value is the
+// high half of the FP32 value with the same bits, so the widening is exact
+__device__ __forceinline__ V4<float> lds4(const __nv_bfloat16 *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    return {__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+            __uint_as_float(u.y & 0xffff0000u)};
+}
+template <typename T>
 __device__ __forceinline__ V4<T> lds4(const T *p) {
     if constexpr (sizeof(T) == 4) {
         const float4 v = *reinterpret_cast<const float4 *>(p);
@@ -751,7 +835,8 @@ struct DsMaps {
     CUtensorMap m[4];
 };
 
-template <typename T, int NR>
+// T: vectors and accumulation; TT: factor tiles (T, or BF16 with BF16 factors)
+template <typename T, typename TT, int NR>
 __global__ void __launch_bounds__(DS_THREADS, 1)
     k_wide_dstage(const __grid_constant__ DsMaps maps, int W, int NB, int64_t PS, int c0, int S, int BC, T *V1,
                   T *V2, int *err) {
@@ -767,9 +852,9 @@ __global__ void __launch_bounds__(DS_THREADS, 1)
     volatile long long *posted = reinterpret_cast<volatile long long *>(empty + S);
     int *pre = reinterpret_cast<int *>(dsm + 2 * S * 8 + 8);  // box prefix per group: head G+1, tail G+1
     // TMA box destinations: 128-byte aligned slots after the header
-    T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(dsm) + 2 * S * 8 + 8 + 8 * (G + 1) + 1023) &
-                                    ~(uintptr_t)1023);
-    T *vin = ring + (int64_t)S * DS_GL * BC;  // NR columns of W
+    TT *ring = reinterpret_cast<TT *>((reinterpret_cast<uintptr_t>(dsm) + 2 * S * 8 + 8 + 8 * (G + 1) + 1023) &
+                                      ~(uintptr_t)1023);
+    T *vin = reinterpret_cast<T *>(ring + (int64_t)S * DS_GL * BC);  // NR columns of W
     T *slice0 = vin + (int64_t)W * NR, *slice1 = slice0 + (int64_t)owned * NR;
     T *v1 = V1 + ((int64_t)part * VP + c0) * PS, *v2 = V2 + ((int64_t)part * VP + c0) * PS;
     if (threadIdx.x == 0) {
@@ -818,7 +903,7 @@ __global__ void __launch_bounds__(DS_THREADS, 1)
                         }
                         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                                          ds_smem(&full[slot])),
-                                     "r"((uint32_t)(DS_GL * BC * sizeof(T)))
+                                     "r"((uint32_t)(DS_GL * BC * sizeof(TT)))
                                      : "memory");
                         asm volatile(
                             "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
@@ -889,7 +974,7 @@ __global__ void __launch_bounds__(DS_THREADS, 1)
                         ok = false;
                         continue;
                     }
-                    const T *buf = ring + (int64_t)slot * DS_GL * BC + (int64_t)(4 * q) * BC;
+                    const TT *buf = ring + (int64_t)slot * DS_GL * BC + (int64_t)(4 * q) * BC;
                     const int col0 = bx * BC, len = min(BC, W - col0);
                     for (int e = 4 * lane; e < len; e += 128) {
                         V4<T> v[NR];
@@ -956,24 +1041,24 @@ __global__ void __launch_bounds__(DS_THREADS, 1)
     }
 }
 
-template <typename T, int NR>
+template <typename T, typename TT, int NR>
 size_t dstage_smem(int W, int cs, int S, int BC) {
     const int G = W / cs / DS_GL;
     // header, alignment of the ring to 1024 bytes, ring, vector, two slices
-    return (2 * (size_t)S * 8 + 8 + 8 * (G + 1)) + 1024 + (size_t)S * DS_GL * BC * sizeof(T) +
+    return (2 * (size_t)S * 8 + 8 + 8 * (G + 1)) + 1024 + (size_t)S * DS_GL * BC * sizeof(TT) +
            (size_t)W * NR * sizeof(T) + 2 * (size_t)(W / cs) * NR * sizeof(T);
 }
 
 // Cluster size: the largest CS <= 8 (16-line groups) for which all p
 // clusters are resident at once; otherwise the one that keeps the most CTAs
 // resident.
-template <typename T, int NR>
+template <typename T, typename TT, int NR>
 int dstage_cluster(Ctx *c, int S, int BC) {
     int best = 0, fallback = 0;
     int64_t fallback_ctas = 0;
     for (int cs = 1; cs <= 8; cs *= 2) {
         if (c->W % (DS_GL * cs)) break;
-        const size_t smem = dstage_smem<T, NR>(c->W, cs, S, BC);
+        const size_t smem = dstage_smem<T, TT, NR>(c->W, cs, S, BC);
         if (smem > (227u << 10)) continue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)cs, (unsigned)c->p, 1);
@@ -987,7 +1072,7 @@ int dstage_cluster(Ctx *c, int S, int BC) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int active = 0;
-        if (cudaOccupancyMaxActiveClusters(&active, k_wide_dstage<T, NR>, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&active, k_wide_dstage<T, TT, NR>, &cfg) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -1002,39 +1087,46 @@ int dstage_cluster(Ctx *c, int S, int BC) {
 
 // 4-D view of a tile kind for the D-stage's boxes: [tile][t][phase][column]
 // with line a = phase + CS t; box 16 lines (t) x BC columns.
-bool dstage_map(CUtensorMap *map, const void *base, bool fp64, int W, int CS, int64_t ntiles, int BC,
-                std::string *err) {
-    const int64_t es = fp64 ? 8 : 4;
+bool dstage_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_t es, int W, int CS,
+                int64_t ntiles, int BC, std::string *err) {
     cuuint64_t dims[4] = {(cuuint64_t)W, (cuuint64_t)CS, (cuuint64_t)(W / CS), (cuuint64_t)ntiles};
     cuuint64_t strides[3] = {(cuuint64_t)(W * es), (cuuint64_t)(CS * W * es), (cuuint64_t)((int64_t)W * W * es)};
     cuuint32_t box[4] = {(cuuint32_t)BC, 1u, (cuuint32_t)DS_GL, 1u};
     cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
-    return encode_tensor_map(map, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base,
-                             dims, strides, box, estr, err);
+    return encode_tensor_map(map, dt, 4, base, dims, strides, box, estr, err);
 }
 
-template <typename T, int NR>
+template <typename TT> constexpr CUtensorMapDataType tile_dtype() {
+    return sizeof(TT) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+           : sizeof(TT) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+}
+
+template <typename T, typename TT, int NR>
 bool launch_dstage(Ctx *c, bool trans, int c0) {
     const int W = c->W;
-    const int BC = std::min(W, (int)(1024 / sizeof(T)));  // box columns: at most 1 KB per line
-    // A: row-major tiles (lines = rows); A^T: column-major tiles (lines = columns)
-    void *const *src = trans ? c->WF : c->WFr;
+    // box columns: at most 1 KB per line and 256 elements (the TMA box limit)
+    const int BC = std::min(std::min(W, 256), (int)(1024 / sizeof(TT)));
+    // A: row-major tiles (lines = rows); A^T: column-major tiles (lines = columns);
+    // BF16 factors: the operand-type copies the tensor-core products wrote
+    const bool bft = sizeof(TT) == 2;
+    void *const *src = trans ? (bft ? c->WFoc : c->WF) : (bft ? c->WFor : c->WFr);
     const void *kinds[4] = {trans ? src[2] : src[3],   // Lo: U_{J-1,J}^T / L_{J,J-1}
                             trans ? src[1] : src[0],   // D: U_JJ^{-T} / L_JJ^{-1}
                             trans ? src[3] : src[2],   // Up: L_{J+1,J}^T / U_{J,J+1}
                             trans ? src[0] : src[1]};  // E: L_JJ^{-T} / U_JJ^{-1}
-    const int S = (int)std::min<size_t>(16, (160u << 10) / ((size_t)DS_GL * BC * sizeof(T)));  // ring slots
-    cudaFuncSetAttribute(k_wide_dstage<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10);
-    const int CS = dstage_cluster<T, NR>(c, S, BC);
+    const int S = (int)std::min<size_t>(16, (160u << 10) / ((size_t)DS_GL * BC * sizeof(TT)));  // ring slots
+    cudaFuncSetAttribute(k_wide_dstage<T, TT, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10);
+    const int CS = dstage_cluster<T, TT, NR>(c, S, BC);
     if (CS == 0) {
         c->err = "no cluster shape of the wide D-stage fits on this GPU";
         return false;
     }
     DsMaps maps;
     for (int q = 0; q < 4; ++q)
-        if (!dstage_map(&maps.m[q], kinds[q], sizeof(T) == 8, W, CS, (int64_t)c->p * c->NBW, BC, &c->err))
+        if (!dstage_map(&maps.m[q], kinds[q], tile_dtype<TT>(), (int64_t)sizeof(TT), W, CS, (int64_t)c->p * c->NBW,
+                        BC, &c->err))
             return false;
-    const size_t smem = dstage_smem<T, NR>(W, CS, S, BC);
+    const size_t smem = dstage_smem<T, TT, NR>(W, CS, S, BC);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)CS, (unsigned)c->p, 1);
     cfg.blockDim = dim3(DS_THREADS, 1, 1);
@@ -1050,7 +1142,7 @@ bool launch_dstage(Ctx *c, bool trans, int c0) {
     c->dcs = CS;
     cudaError_t e = cudaSuccess;
     const bool ok = launch(c, KID_WIDE_DSTAGE, [&] {
-        e = cudaLaunchKernelEx(&cfg, k_wide_dstage<T, NR>, maps, W, c->NBW, c->PS, c0, S, BC, (T *)c->WV1,
+        e = cudaLaunchKernelEx(&cfg, k_wide_dstage<T, TT, NR>, maps, W, c->NBW, c->PS, c0, S, BC, (T *)c->WV1,
                                (T *)c->WV2, c->gemm_err);
     });
     if (e != cudaSuccess) {
@@ -1060,18 +1152,27 @@ bool launch_dstage(Ctx *c, bool trans, int c0) {
     return ok;
 }
 
-template <typename T>
-bool run_dstage_chain(Ctx *c, int nrhs, bool trans) {
+template <typename T, typename TT>
+bool dstage_chain_tt(Ctx *c, int nrhs, bool trans) {
     for (int c0 = 0; c0 < nrhs; c0 += 4) {
         // three columns run as four: the fourth panel column is independent of
         // the others and never read back
         const int nc = std::min(4, nrhs - c0);
-        const bool ok = nc == 1   ? launch_dstage<T, 1>(c, trans, c0)
-                        : nc == 2 ? launch_dstage<T, 2>(c, trans, c0)
-                                  : launch_dstage<T, 4>(c, trans, c0);
+        const bool ok = nc == 1   ? launch_dstage<T, TT, 1>(c, trans, c0)
+                        : nc == 2 ? launch_dstage<T, TT, 2>(c, trans, c0)
+                                  : launch_dstage<T, TT, 4>(c, trans, c0);
         if (!ok) return false;
     }
     return true;
+}
+
+// BF16 factors: the D-stage streams the BF16 copies of the factor tiles (half
+// the bytes of the FP32 tiles) and accumulates in FP32
+template <typename T>
+bool run_dstage_chain(Ctx *c, int nrhs, bool trans) {
+    if constexpr (sizeof(T) == 4)
+        if (c->gpath == 2) return dstage_chain_tt<T, __nv_bfloat16>(c, nrhs, trans);
+    return dstage_chain_tt<T, T>(c, nrhs, trans);
 }
 
 // ---------------------------------------------------------------------------
@@ -1139,16 +1240,15 @@ bool cholqr3(Ctx *c, void *Y, void *Qout) {
     for (int pass = 0; pass < 3; ++pass) {
         // pass 0: Y -> Qout (shifted); 1: Qout -> Y; 2: Y -> Qout
         void *src = (pass == 1) ? Qout : Y, *dst = (pass == 1) ? Y : Qout;
-        const dim3 gg((unsigned)((lp + 63) / 64), (unsigned)((lp + 63) / 64), (unsigned)nm);
+        const int tiles = (lp + 63) / 64, nch = gram_chunks(PS);
+        const dim3 gg((unsigned)(tiles * tiles), (unsigned)nch, (unsigned)nm);
         const dim3 gq((unsigned)((PS + 63) / 64), (unsigned)((lp + 63) / 64), (unsigned)nm);
         const bool ok =
             launch(c, KID_WIDE_CHOLQR, [&] {
-                k_simt_gemm<T><<<gg, 256, 0, c->stream>>>(lp, lp, (int)PS, T(1), T(0), (const T *)src, PS, 1, sY,
-                                                          (const T *)src, PS, 1, sY, (T *)c->WG, lp, sG, nullptr, 0,
-                                                          0);
+                k_gram_part<T><<<gg, 256, 0, c->stream>>>((const T *)src, lp, PS, sY, (T *)c->WGp);
             }) &&
             launch(c, KID_WIDE_CHOLQR, [&] {
-                k_to_f64<T><<<64, 256, 0, c->stream>>>((const T *)c->WG, c->WGd, nm * sG);
+                k_gram_sum<T><<<256, 256, 0, c->stream>>>((const T *)c->WGp, nch, sG, nm * sG, c->WGd);
             }) &&
             launch(c, KID_WIDE_CHOLQR, [&] {
                 k_chol_inv<T><<<nm, 256, smem, c->stream>>>(c->WGd, lp, ell, PS, u, pass == 0 ? 1 : 0, (T *)c->WRi);
@@ -1404,7 +1504,8 @@ bool wide_setup(Ctx *c) {
     auto al = [&](void **ptr, size_t bytes) { return cudaMalloc(ptr, bytes) == cudaSuccess; };
     bool ok = true;
     // factor tiles: f and fr always (the D-stage reads fr for A, f for A^T);
-    // operand copies in BF16 mode (TF32: they alias f / fr)
+    // operand copies in BF16 mode (TF32: they alias f / fr), which the BF16
+    // D-stage reads instead
     for (int kind = 0; kind < 4 && ok; ++kind) {
         ok = al(&c->WF[kind], p * NB * WW * tz) && al(&c->WFr[kind], p * NB * WW * tz);
         if (ok && bf) ok = al(&c->WFoc[kind], p * NB * WW * oz) && al(&c->WFor[kind], p * NB * WW * oz);
@@ -1432,6 +1533,7 @@ bool wide_setup(Ctx *c) {
         ok = al(&c->WP1, panel * tz) && al(&c->WP2, panel * tz) && al(&c->WTip, 2 * p * WL * tz) &&
              al(&c->WOm, 2 * p * WL * (tc ? oz : tz)) && al(&c->WQk, 2 * p * PS * lp * tz) &&
              al(&c->WZk, 2 * p * WL * tz) && al(&c->WG, 2 * p * lp * lp * tz) &&
+             al(&c->WGp, 2 * p * (size_t)gram_chunks(PS) * lp * lp * tz) &&
              al((void **)&c->WGd, 2 * p * lp * lp * 8) && al(&c->WRi, 2 * p * lp * lp * tz) &&
              al(&c->WE, 2 * p * (size_t)std::max(r, 1) * lp * tz) && al(&c->WCpl[0], 2 * p * WW * tz);
         if (ok && tc) {
@@ -1473,7 +1575,7 @@ void wide_free(Ctx *c) {
     if (c->WCpl[2] != c->WCpl[0]) ptrs.push_back(c->WCpl[2]);
     ptrs.push_back(c->WCpl[3]);
     c->WCpl[0] = c->WCpl[1] = c->WCpl[2] = c->WCpl[3] = nullptr;
-    for (void *q : {c->WP1, c->WP2, c->WP1c, c->WP2c, c->WTip, c->WTipc, c->WOm, c->WQk, c->WZk, c->WZc, c->WG,
+    for (void *q : {c->WP1, c->WP2, c->WP1c, c->WP2c, c->WTip, c->WTipc, c->WOm, c->WQk, c->WZk, c->WZc, c->WG, c->WGp,
                     (void *)c->WGd, c->WRi, c->WE, c->WV1, c->WV2, (void *)c->diag_list, (void *)c->gemm_err})
         ptrs.push_back(q);
     for (void *q : ptrs)

@@ -2,9 +2,10 @@
 LU (k <= 64, unpivoted, FP32 or FP64 working precision) the upload runs in
 partition groups on its own stream, the interface columns first for the
 coupling branch, and every group's band LU starts when its columns land.
-The kernels and their order within a partition are those of a device band,
-so the factors, and the solution, agree bit for bit with the device-band
-factorisation; a pageable (unpinned) band takes the same path."""
+The kernels and their order within a partition are those of one LU launch
+over all partitions (a device band; a profiling handle also uploads a host
+band in one copy), so the factors, and the solution, agree bit for bit; a
+pageable (unpinned) band takes the same path."""
 import numpy as np
 import pytest
 
@@ -45,9 +46,10 @@ def test_host_band_equals_device_band(torch_cuda, case, pinned):
         hb = hb.pin_memory()
     db = hb.cuda()
     out = []
-    for band in (db, hb, hb):   # each handle factors twice: the second upload reuses its streams
+    # each handle factors twice (the second upload reuses its streams)
+    for band, profile in ((db, False), (hb, True), (hb, False), (hb, False)):
         with LRSpike(n, k, p, r, precision=precision, compress=compress, reduced=reduced, tol=1e-10,
-                     max_nrhs=nrhs) as s:
+                     max_nrhs=nrhs, profile=profile) as s:
             s.factor(band)
             x, info = s.solve(f)
             assert info["converged"]

@@ -90,15 +90,18 @@ def test_wide_solve_reaches_tolerance(torch_cuda, precision, transpose):
         assert rel(x, xs) <= 1e4 * tol
 
 
-@pytest.mark.parametrize("precision,bound", [("tf32", 2e-3), ("bf16", 3e-2)])
-def test_wide_tensor_core_preconditioner_error(torch_cuda, precision, bound):
+@pytest.mark.parametrize("precision,bound,n,k", [("tf32", 2e-3, 12000, 128), ("bf16", 3e-2, 12000, 128),
+                                                 ("tf32", 2e-3, 40000, 520), ("bf16", 3e-2, 40000, 520)])
+def test_wide_tensor_core_preconditioner_error(torch_cuda, precision, bound, n, k):
     """One application with tensor-core block products against the FP64
     oracle.  TF32 keeps 10 mantissa bits (unit roundoff 2^-11 = 4.9e-4), BF16
     7 (2^-8 = 3.9e-3); the rounding of the operands of a product of order W
     enters M^{-1} f relatively at a few units of that roundoff through the
     well-conditioned block chain of a dominant band, so the bounds are four
-    (TF32) and eight (BF16) times the operand roundoff."""
-    n, k, p, r = 12000, 128, 4, 16
+    (TF32) and eight (BF16) times the operand roundoff.  With BF16 factors the
+    D-stage also reads BF16 tiles: one more rounding of the same size per
+    product.  k = 520 (W = 576): D-stage boxes of 256 columns, three per line."""
+    p, r = 4, 16
     ab = inputs.dominant_band(n, k, 1.2, 31)
     f = inputs.rhs(n, 2, 31)
     fac = O.factor(ab, k, p, r, reduced="truncated")
