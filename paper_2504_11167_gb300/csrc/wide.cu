@@ -711,14 +711,15 @@ __global__ void k_nonzero_diags(const double *__restrict__ band, int64_t ld, int
 // CTA c of a cluster owns lines a = c + CS t, sixteen at a time (a group).  A
 // 4-D tensor map views each tile kind as [tile][t][phase c][column], so one
 // TMA load (cp.async.bulk.tensor) brings a box of a group's 16 lines x
-// DS_BC columns (16 KB) into a shared-memory slot; only the boxes that meet
-// the group's nonzero columns are loaded (the rest of the triangle is never
-// read; zeros inside a loaded box are multiplied as they are).  Warp 16
-// (producer) streams the boxes of every product in order into a ring of
-// slots, completion counted on the slot's mbarrier, running ahead of the
-// consumers across products (the tiles do not depend on the vectors).  Warps
-// 0..15 (consumers) take (group, quarter) items in turn and their boxes in
-// order (the four quarters of a box free its slot together): per box and
+// BC columns (at most 1 KB per line) into a shared-memory slot; only the
+// boxes that meet the group's nonzero columns are loaded (the rest of the
+// triangle is never read; zeros inside a loaded box are multiplied as they
+// are).  Warp DS_CONSUMERS (producer) streams the boxes of every product in
+// order into a ring of slots, completion counted on the slot's mbarrier,
+// running ahead of the consumers across products (the tiles do not depend on
+// the vectors).  Warps 0..DS_CONSUMERS-1 (consumers) take (group, quarter)
+// items in turn and their boxes in order (the four quarters of a box free its
+// slot together): per box and
 // quarter of the group (four lines), lanes over 4-entry pieces, the four lines
 // at once so each vector entry read from shared memory serves four lines, and
 // a butterfly reduce-scatter at the end.
@@ -727,7 +728,12 @@ __global__ void k_nonzero_diags(const double *__restrict__ band, int64_t ld, int
 // product).  Input b in V1, y in V2, result x in V1 (panel column c at c PS).
 // Waits on the ring are bounded; one that runs out sets *err and the CTA
 // keeps walking the barrier sequence without computing, so the cluster ends.
-constexpr int DS_CONSUMERS = 16;
+// Eight consumer warps and an 80 KB ring: two CTAs fit on an SM, so every SM
+// interleaves the chains of two partitions (each product of a chain ends in
+// a cluster barrier and an exchange, which one chain alone cannot hide; with
+// sixteen consumer warps and one CTA per SM an application took 2.76 ms at
+// the 1024^2 convection-diffusion size, 2.04 ms like this).
+constexpr int DS_CONSUMERS = 8;
 constexpr int DS_THREADS = 32 * (DS_CONSUMERS + 1);
 constexpr int DS_GL = 16;  // lines per group (one TMA box)
 constexpr long long kDsSpin = 1ll << 26;
@@ -837,7 +843,7 @@ struct DsMaps {
 
 // T: vectors and accumulation; TT: factor tiles (T, or BF16 with BF16 factors)
 template <typename T, typename TT, int NR>
-__global__ void __launch_bounds__(DS_THREADS, 1)
+__global__ void __launch_bounds__(DS_THREADS, 2)
     k_wide_dstage(const __grid_constant__ DsMaps maps, int W, int NB, int64_t PS, int c0, int S, int BC, T *V1,
                   T *V2, int *err) {
     cg::cluster_group cl = cg::this_cluster();
@@ -1114,7 +1120,8 @@ bool launch_dstage(Ctx *c, bool trans, int c0) {
                             trans ? src[1] : src[0],   // D: U_JJ^{-T} / L_JJ^{-1}
                             trans ? src[3] : src[2],   // Up: L_{J+1,J}^T / U_{J,J+1}
                             trans ? src[0] : src[1]};  // E: L_JJ^{-T} / U_JJ^{-1}
-    const int S = (int)std::min<size_t>(16, (160u << 10) / ((size_t)DS_GL * BC * sizeof(TT)));  // ring slots
+    // ring slots: 80 KB of boxes, so that two CTAs share an SM
+    const int S = (int)std::min<size_t>(16, (80u << 10) / ((size_t)DS_GL * BC * sizeof(TT)));
     cudaFuncSetAttribute(k_wide_dstage<T, TT, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10);
     const int CS = dstage_cluster<T, TT, NR>(c, S, BC);
     if (CS == 0) {
