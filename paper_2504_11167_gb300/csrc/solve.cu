@@ -523,19 +523,33 @@ __global__ void __launch_bounds__(Geo<KB>::NT, 2)
 }
 
 // x (+)= nrm * (g - u_T zeta - u_W omega) for one partition's rows.  Each
-// thread reads its row of u once and updates all NC (>= nrhs) columns in
-// registers; per column the expression is the same as in the one-column
-// form (d -= u_j z_j + u_j+1 z_j+1 + ...), so the rounding is unchanged.
+// thread updates all NC (>= nrhs) columns of its row in registers; per column
+// the expression is the same as in the one-column form (d -= u_j z_j +
+// u_j+1 z_j+1 + ...), so the rounding is unchanged.  The CTA's rows of u
+// (row-major, 2r values a row) are staged 32 columns at a time in shared
+// memory with coalesced loads (rows padded to RU_LD values: conflict-free
+// 16-byte reads for FP32, 2-way for FP64), and each thread reads its row there.
+constexpr int RU_CW = 32;
+template <typename T> constexpr int ru_ld() { return sizeof(T) == 4 ? RU_CW + 4 : RU_CW + 1; }
+template <typename T>
+size_t retrieve_smem(int n2, int nrhs) {
+    return ((size_t)n2 * nrhs + 2) / 2 * 2 * sizeof(double) + (size_t)RBS * ru_ld<T>() * sizeof(T);
+}
+
 template <typename T, int NC>
 __global__ void __launch_bounds__(RBS)
     k_retrieve(const T *__restrict__ Gv, const T *__restrict__ Ucat, const double *__restrict__ zr,
                Parts P, int r, int64_t n, int nrhs, const double *__restrict__ nrm, double *__restrict__ x,
                int64_t ld, int accumulate, const int *skip) {
-    extern __shared__ double zs[];  // [2r][nrhs]: zeta_part, omega_part
+    extern __shared__ double zs[];  // [2r][nrhs]: zeta_part, omega_part; then the staged u rows
     if (skip && *skip) return;
+    constexpr int LDU = ru_ld<T>();
     const int part = blockIdx.y;
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
+    const int64_t first = blockIdx.x * (int64_t)RBS;
+    if (first >= ni) return;  // the whole CTA lies past this partition's rows
     const int n2 = 2 * r;
+    T *us = reinterpret_cast<T *>(zs + ((int64_t)n2 * nrhs + 2) / 2 * 2);
     for (int e = threadIdx.x; e < n2 * nrhs; e += RBS) {
         const int j = e / nrhs, c = e % nrhs;
         double v = 0.0;
@@ -543,32 +557,44 @@ __global__ void __launch_bounds__(RBS)
         else if (part >= 1) v = zr[((int64_t)(part - 1) * n2 + j) * nrhs + c];
         zs[e] = v;
     }
-    __syncthreads();
-    const int64_t row = blockIdx.x * (int64_t)RBS + threadIdx.x;
-    if (row >= ni) return;
-    const int64_t gi = s + row;
+    const int rows = (int)min((int64_t)RBS, ni - first);
+    const bool live = threadIdx.x < rows;
+    const int64_t gi = s + first + threadIdx.x;
     T d[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) d[c] = (c < nrhs) ? Gv[c * n + gi] : T(0);
-    const T *u = Ucat + gi * n2;
-    int j = 0;
-    if constexpr (sizeof(T) == 4) {
-        if ((n2 & 3) == 0)
-            for (; j < n2; j += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(u + j);
+    for (int c = 0; c < NC; ++c) d[c] = (live && c < nrhs) ? Gv[c * n + gi] : T(0);
+    const T *ublk = Ucat + (s + first) * n2;
+    for (int j0 = 0; j0 < n2; j0 += RU_CW) {
+        const int cw = min(RU_CW, n2 - j0);
+        __syncthreads();  // zs written; the previous chunk consumed
+        for (int e = threadIdx.x; e < rows * cw; e += RBS) {
+            const int a = e / cw, j = e % cw;
+            us[a * LDU + j] = ublk[(int64_t)a * n2 + j0 + j];
+        }
+        __syncthreads();
+        if (!live) continue;
+        const T *u = us + threadIdx.x * LDU;
+        int j = 0;
+        if constexpr (sizeof(T) == 4) {
+            if ((n2 & 3) == 0)
+                for (; j < cw; j += 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(u + j);
+                    const int jz = j0 + j;
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    if (c < nrhs)
-                        d[c] -= v.x * (T)zs[j * nrhs + c] + v.y * (T)zs[(j + 1) * nrhs + c] +
-                                v.z * (T)zs[(j + 2) * nrhs + c] + v.w * (T)zs[(j + 3) * nrhs + c];
-            }
-    }
-    for (; j < n2; ++j) {
-        const T uj = u[j];
+                    for (int c = 0; c < NC; ++c)
+                        if (c < nrhs)
+                            d[c] -= v.x * (T)zs[jz * nrhs + c] + v.y * (T)zs[(jz + 1) * nrhs + c] +
+                                    v.z * (T)zs[(jz + 2) * nrhs + c] + v.w * (T)zs[(jz + 3) * nrhs + c];
+                }
+        }
+        for (; j < cw; ++j) {
+            const T uj = u[j];
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-            if (c < nrhs) d[c] -= uj * (T)zs[j * nrhs + c];
+            for (int c = 0; c < NC; ++c)
+                if (c < nrhs) d[c] -= uj * (T)zs[(j0 + j) * nrhs + c];
+        }
     }
+    if (!live) return;
 #pragma unroll
     for (int c = 0; c < NC; ++c)
         if (c < nrhs) {
@@ -862,7 +888,9 @@ static bool retrieve_impl(Ctx *c, double *x, int64_t ld, int nrhs, int acc) {
     }
     Parts P{c->off_d, c->boff_d, c->p};
     dim3 grid(row_blocks(c->maxni), c->p);
-    const size_t smem = (size_t)(2 * c->r * nrhs + 1) * sizeof(double);
+    const size_t smem = retrieve_smem<T>(2 * c->r, nrhs);
+    for (auto kern : {k_retrieve<T, 4>, k_retrieve<T, 8>, k_retrieve<T, 16>})
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return launch(c, KID_RETRIEVE, [&] {
         if (nrhs <= 4)
             k_retrieve<T, 4><<<grid, RBS, smem, c->stream>>>((const T *)c->Gv, (const T *)c->Ucat, c->zr, P, c->r,

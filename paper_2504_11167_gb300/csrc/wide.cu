@@ -663,26 +663,32 @@ __global__ void k_wide_unpack_t(const T *__restrict__ V, const double *__restric
     }
 }
 
-// psi_{i-1}[0:r] = P_{i-1} g_t,  psi_i[r:2r] = Q_{i+1} g_b  (FP64)
+// psi_{i-1}[0:r] = P_{i-1} g_t,  psi_i[r:2r] = Q_{i+1} g_b  (FP64): one warp
+// per (side, j, column) of a partition, lanes over the k tip rows (coalesced
+// reads of the P / Q row and of g), partial sums added by a warp reduction.
+constexpr int PSI_WARPS = 8;
 template <typename T>
-__global__ void k_wide_psi(const T *__restrict__ Gv, const T *__restrict__ PQ, int W, Parts P, int k, int r,
-                           int64_t n, int nrhs, double *__restrict__ psi) {
-    const int part = blockIdx.x;
+__global__ void __launch_bounds__(32 * PSI_WARPS)
+    k_wide_psi(const T *__restrict__ Gv, const T *__restrict__ PQ, int W, Parts P, int k, int r, int64_t n,
+               int nrhs, double *__restrict__ psi) {
+    const int part = blockIdx.x, lane = threadIdx.x & 31;
+    const int o = blockIdx.y * PSI_WARPS + (threadIdx.x >> 5);
+    if (o >= 2 * r * nrhs) return;  // warp-uniform
     const int64_t s = P.off[part], ni = P.off[part + 1] - s;
     const int n2 = 2 * r;
-    for (int o = threadIdx.x; o < 2 * r * nrhs; o += blockDim.x) {
-        const int side = o / (r * nrhs), rem = o % (r * nrhs), j = rem / nrhs, c = rem % nrhs;
-        if (side == 0 && part >= 1) {
-            const T *Pm = PQ + ((int64_t)(part - 1) * 2 + 0) * r * W + (int64_t)j * W;
-            double acc = 0.0;
-            for (int q = 0; q < k; ++q) acc += (double)Pm[q] * (double)Gv[c * n + s + q];
-            psi[((int64_t)(part - 1) * n2 + j) * nrhs + c] = acc;
-        } else if (side == 1 && part <= P.p - 2) {
-            const T *Qm = PQ + ((int64_t)(part + 1) * 2 + 1) * r * W + (int64_t)j * W;
-            double acc = 0.0;
-            for (int q = 0; q < k; ++q) acc += (double)Qm[q] * (double)Gv[c * n + s + ni - k + q];
-            psi[((int64_t)part * n2 + r + j) * nrhs + c] = acc;
-        }
+    const int side = o / (r * nrhs), rem = o % (r * nrhs), j = rem / nrhs, c = rem % nrhs;
+    if (side == 0 && part >= 1) {
+        const T *Pm = PQ + ((int64_t)(part - 1) * 2 + 0) * r * W + (int64_t)j * W;
+        double acc = 0.0;
+        for (int q = lane; q < k; q += 32) acc += (double)Pm[q] * (double)Gv[c * n + s + q];
+        acc = warp_sum(acc);
+        if (lane == 0) psi[((int64_t)(part - 1) * n2 + j) * nrhs + c] = acc;
+    } else if (side == 1 && part <= P.p - 2) {
+        const T *Qm = PQ + ((int64_t)(part + 1) * 2 + 1) * r * W + (int64_t)j * W;
+        double acc = 0.0;
+        for (int q = lane; q < k; q += 32) acc += (double)Qm[q] * (double)Gv[c * n + s + ni - k + q];
+        acc = warp_sum(acc);
+        if (lane == 0) psi[((int64_t)part * n2 + r + j) * nrhs + c] = acc;
     }
 }
 
@@ -1721,8 +1727,9 @@ static bool wide_dstage_t(Ctx *c, const double *rin, int nrhs, bool trans, doubl
         return false;
     if (p < 2 || c->r == 0) return true;
     return launch(c, KID_WIDE_VEC, [&] {
-        k_wide_psi<T><<<p, 256, 0, c->stream>>>((const T *)c->Gv, (const T *)c->PQ, W, P, c->k, c->r, c->n, nrhs,
-                                                 c->psi);
+        const dim3 grid((unsigned)p, (unsigned)((2 * c->r * nrhs + PSI_WARPS - 1) / PSI_WARPS));
+        k_wide_psi<T><<<grid, 32 * PSI_WARPS, 0, c->stream>>>((const T *)c->Gv, (const T *)c->PQ, W, P, c->k, c->r,
+                                                               c->n, nrhs, c->psi);
     });
 }
 
