@@ -529,11 +529,14 @@ __global__ void __launch_bounds__(Geo<KB>::NT, 2)
 // (row-major, 2r values a row) are staged 32 columns at a time in shared
 // memory with coalesced loads (rows padded to RU_LD values: conflict-free
 // 16-byte reads for FP32, 2-way for FP64), and each thread reads its row there.
+// zeta and omega are converted to the working precision once, when staged (a
+// conversion per use would run on GB300's slow FP64 units).
 constexpr int RU_CW = 32;
 template <typename T> constexpr int ru_ld() { return sizeof(T) == 4 ? RU_CW + 4 : RU_CW + 1; }
+template <typename T> __host__ __device__ inline size_t retrieve_zbytes(int n2, int nrhs) { return ((size_t)n2 * nrhs * sizeof(T) + 15) / 16 * 16; }
 template <typename T>
 size_t retrieve_smem(int n2, int nrhs) {
-    return ((size_t)n2 * nrhs + 2) / 2 * 2 * sizeof(double) + (size_t)RBS * ru_ld<T>() * sizeof(T);
+    return retrieve_zbytes<T>(n2, nrhs) + (size_t)RBS * ru_ld<T>() * sizeof(T);
 }
 
 template <typename T, int NC>
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(RBS)
     k_retrieve(const T *__restrict__ Gv, const T *__restrict__ Ucat, const double *__restrict__ zr,
                Parts P, int r, int64_t n, int nrhs, const double *__restrict__ nrm, double *__restrict__ x,
                int64_t ld, int accumulate, const int *skip) {
-    extern __shared__ double zs[];  // [2r][nrhs]: zeta_part, omega_part; then the staged u rows
+    extern __shared__ __align__(16) unsigned char rsm[];  // [2r][nrhs] zeta_part, omega_part; staged u rows
     if (skip && *skip) return;
     constexpr int LDU = ru_ld<T>();
     const int part = blockIdx.y;
@@ -549,13 +552,14 @@ __global__ void __launch_bounds__(RBS)
     const int64_t first = blockIdx.x * (int64_t)RBS;
     if (first >= ni) return;  // the whole CTA lies past this partition's rows
     const int n2 = 2 * r;
-    T *us = reinterpret_cast<T *>(zs + ((int64_t)n2 * nrhs + 2) / 2 * 2);
+    T *zs = reinterpret_cast<T *>(rsm);
+    T *us = reinterpret_cast<T *>(rsm + retrieve_zbytes<T>(n2, nrhs));
     for (int e = threadIdx.x; e < n2 * nrhs; e += RBS) {
         const int j = e / nrhs, c = e % nrhs;
         double v = 0.0;
         if (j < r) { if (part <= P.p - 2) v = zr[((int64_t)part * n2 + j) * nrhs + c]; }
         else if (part >= 1) v = zr[((int64_t)(part - 1) * n2 + j) * nrhs + c];
-        zs[e] = v;
+        zs[e] = (T)v;
     }
     const int rows = (int)min((int64_t)RBS, ni - first);
     const bool live = threadIdx.x < rows;
@@ -583,15 +587,15 @@ __global__ void __launch_bounds__(RBS)
 #pragma unroll
                     for (int c = 0; c < NC; ++c)
                         if (c < nrhs)
-                            d[c] -= v.x * (T)zs[jz * nrhs + c] + v.y * (T)zs[(jz + 1) * nrhs + c] +
-                                    v.z * (T)zs[(jz + 2) * nrhs + c] + v.w * (T)zs[(jz + 3) * nrhs + c];
+                            d[c] -= v.x * zs[jz * nrhs + c] + v.y * zs[(jz + 1) * nrhs + c] +
+                                    v.z * zs[(jz + 2) * nrhs + c] + v.w * zs[(jz + 3) * nrhs + c];
                 }
         }
         for (; j < cw; ++j) {
             const T uj = u[j];
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                if (c < nrhs) d[c] -= uj * (T)zs[(j0 + j) * nrhs + c];
+                if (c < nrhs) d[c] -= uj * zs[(j0 + j) * nrhs + c];
         }
     }
     if (!live) return;
