@@ -240,9 +240,21 @@ __global__ void __launch_bounds__(ColGeo<T, KB>::NT, sizeof(T) == 4 ? 2 : 1)
         for (int u = 0; u < TR; ++u) {
             ld_row<T, TR>(RB + u * KB + tx * TR, ur[u]);
 #pragma unroll
-            for (int p = 0; p < u; ++p)
+            for (int p = 0; p < u; ++p) {
+                if constexpr (sizeof(T) == 4 && TR % 2 == 0) {
+                    const float2 nl = make_float2(-pv[u][p], -pv[u][p]);
 #pragma unroll
-                for (int c = 0; c < TR; ++c) ur[u][c] -= pv[u][p] * ur[p][c];
+                    for (int c = 0; c < TR; c += 2) {
+                        const float2 o = __ffma2_rn(nl, make_float2(ur[p][c], ur[p][c + 1]),
+                                                    make_float2(ur[u][c], ur[u][c + 1]));
+                        ur[u][c] = o.x;
+                        ur[u][c + 1] = o.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < TR; ++c) ur[u][c] -= pv[u][p] * ur[p][c];
+                }
+            }
         }
         {
             T cb[TR][TR];  // cb[u][r]
@@ -272,12 +284,30 @@ __global__ void __launch_bounds__(ColGeo<T, KB>::NT, sizeof(T) == 4 ? 2 : 1)
                 for (int r = 0; r < TR; ++r) w[r][v] = ec[r];
             }
         }
+        if constexpr (sizeof(T) == 4 && TR % 2 == 0) {
+            // two columns per packed FP32 FMA: each half of __ffma2_rn rounds
+            // like fmaf, so the window holds the values of the scalar form
 #pragma unroll
-        for (int u = 0; u < TR; ++u)
+            for (int u = 0; u < TR; ++u)
 #pragma unroll
-            for (int r = 0; r < TR; ++r)
+                for (int r = 0; r < TR; ++r) {
+                    const float2 nm = make_float2(-m[r][u], -m[r][u]);
 #pragma unroll
-                for (int c = 0; c < TR; ++c) w[r][c] -= m[r][u] * ur[u][c];
+                    for (int c = 0; c < TR; c += 2) {
+                        const float2 o = __ffma2_rn(nm, make_float2(ur[u][c], ur[u][c + 1]),
+                                                    make_float2(w[r][c], w[r][c + 1]));
+                        w[r][c] = o.x;
+                        w[r][c + 1] = o.y;
+                    }
+                }
+        } else {
+#pragma unroll
+            for (int u = 0; u < TR; ++u)
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int c = 0; c < TR; ++c) w[r][c] -= m[r][u] * ur[u][c];
+        }
         // outputs: multipliers (staged), scaled pivot rows, 1/u_jj; in the leaving
         // slots the pivot block's own L_p (below) and U_p (above) entries
         if (tx == 0) {
