@@ -642,12 +642,27 @@ __device__ __forceinline__ void tile4_mac(const T *A, const T *B, int ldm, int i
         for (int i = 0; i < 4; ++i) ld_row<T, 4>(A + (i0 + i) * ldm + q, av[i]);
 #pragma unroll
         for (int u = 0; u < 4; ++u) ld_row<T, 4>(B + (q + u) * ldm + j0, bv[u]);
+        if constexpr (sizeof(T) == 4) {
+            // two columns per packed FP32 FMA (each half rounds like fmaf)
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += av[i][u] * bv[u][j];
+                    for (int j = 0; j < 4; j += 2) {
+                        const float2 o = __ffma2_rn(make_float2(av[i][u], av[i][u]), make_float2(bv[u][j], bv[u][j + 1]),
+                                                    make_float2(acc[i][j], acc[i][j + 1]));
+                        acc[i][j] = o.x;
+                        acc[i][j + 1] = o.y;
+                    }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += av[i][u] * bv[u][j];
+        }
     }
 }
 
