@@ -132,3 +132,35 @@ def test_graph_replays_reset_the_exit_flag(torch_cuda):
     for a, c in zip(x1, b.x):
         assert torch.equal(a, c)
     b.close()
+
+
+@pytest.mark.parametrize("pivoting,transpose,nrhs", [(False, True, 1), (True, False, 1), (True, True, 1),
+                                                     (False, False, 3), (False, True, 3)])
+def test_graph_safe_exit_on_every_kernel_path(torch_cuda, pivoting, transpose, nrhs):
+    """The early exit on the other kernels a graph-safe step runs: the
+    transposed D-stage, the pivoted D-stages, the multi-column retrieval.  A
+    solve enqueued with 40 steps equals, bit for bit, one enqueued with
+    exactly the steps it reports, and every column meets tol."""
+    torch = torch_cuda
+    from paper_2504_11167_gb300.solver import LRSpike
+    n, k, p, r = 24000, 16, 6, 4
+    ab = inputs.dominant_band(n, k, 0.8 if pivoting else 1.5, 91)
+    f = inputs.rhs(n, nrhs, 91)
+    band = torch.from_numpy(ab).cuda()
+    ft = torch.from_numpy(np.ascontiguousarray(f.T)).cuda()
+
+    def graph_safe(max_iter):
+        with LRSpike(n, k, p, r, precision="fp32", reduced="truncated", outer="ir", tol=1e-10,
+                     max_iter=max_iter, max_nrhs=nrhs, pivoting=pivoting, graph_safe=True) as s:
+            s.factor(band)
+            x = torch.empty_like(ft)
+            (s.solve_transpose if transpose else s.solve)(ft, x)
+            info = s.finish(nrhs=nrhs, allow_unconverged=True)
+        return x, info
+
+    x40, i40 = graph_safe(40)
+    assert i40["converged"] and 1 <= i40["iterations"] < 40
+    assert max(i40["rel_residual"][:nrhs]) <= 1e-10
+    xe, ie = graph_safe(i40["iterations"])
+    assert ie["iterations"] == i40["iterations"]
+    assert torch.equal(x40, xe)
