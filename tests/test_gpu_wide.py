@@ -53,6 +53,7 @@ CASES = [
     (9000, 130, 3, 10, 1.2, "full", 5),        # W = 192: unequal split 128 + 64, nrhs > 4
     (3000, 100, 1, 4, 1.5, "full", 1),         # p = 1: the wide band LU alone
     (6200, 1024, 3, 16, 1.1, "truncated", 4),  # W = 1024: the convection-diffusion block size
+    (8000, 96, 3, 8, 1.2, "truncated", 16),    # widest nrhs: four D-stage column chunks
 ]
 
 
@@ -131,11 +132,11 @@ def test_wide_rank64(torch_cuda, precision):
     FP64 oracle, and the refinement to 1e-10."""
     n, k, p, r = 20000, 192, 4, 64
     ab = inputs.dominant_band(n, k, 1.2, 41)
-    f = inputs.rhs(n, 1, 41)
+    f = inputs.rhs(n, 3, 41)  # three columns: the multi-column retrieval over 128 low-rank columns
     fac = O.factor(ab, k, p, r, reduced="truncated", threads=p)
     got, _ = gpu_solve(torch_cuda, ab, f, k, p, r, reduced="truncated", outer="none", precision=precision)
     assert rel(got, O.apply(fac, np.asarray(f))) <= (2e-3 if precision == "tf32" else 3e-2)
     x, info = gpu_solve(torch_cuda, ab, f, k, p, r, reduced="truncated", precision=precision, tol=1e-10)
     assert info["converged"]
     res = np.asarray(f) - O.band_matvec(ab, k, x)
-    assert np.linalg.norm(res) / np.linalg.norm(f) <= 1.01e-10
+    assert (np.linalg.norm(res, axis=0) / np.linalg.norm(f, axis=0)).max() <= 1.01e-10
