@@ -477,8 +477,34 @@ __global__ void __launch_bounds__(256)
             }
         }
     };
-    // acc (+/-)= tile rows a0..a0+3 x B over q in [q0, q1) (multiples of 4)
+    // acc (+/-)= tile rows a0..a0+3 x B over q in [q0, q1) (multiples of 4).
+    // One column per thread: the products of even and odd q go to the two
+    // halves of a packed FP32 FMA (__ffma2_rn), whose sum then updates acc.
     auto mac4 = [&](float (&acc)[4][MT], const float *tile, const float *B, int a0, int q0, int q1, bool sub) {
+        if constexpr (MT == 1) {
+            float2 s2[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s2[i] = make_float2(0.f, 0.f);
+            for (int q = q0; q < q1; q += 4) {
+                float av[4][4], bq[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ld_row<float, 4>(tile + (a0 + i) * LDT + q, av[i]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) bq[u] = B[(q + u) * LDM + c0];
+                const float2 b01 = make_float2(bq[0], bq[1]), b23 = make_float2(bq[2], bq[3]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    s2[i] = __ffma2_rn(make_float2(av[i][0], av[i][1]), b01, s2[i]);
+                    s2[i] = __ffma2_rn(make_float2(av[i][2], av[i][3]), b23, s2[i]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float t = s2[i].x + s2[i].y;
+                acc[i][0] = sub ? acc[i][0] - t : acc[i][0] + t;
+            }
+            return;
+        }
         for (int q = q0; q < q1; q += 4) {
             float av[4][4], bv[4][MT];
 #pragma unroll
