@@ -187,7 +187,12 @@ lrspike_status lrspike_create(const lrspike_options *opt, void *cuda_stream, lrs
  * band: (2k+1) x ld values as described above, FP64.  Device pointer: borrowed,
  * not copied -- the caller keeps it alive and unmodified until the next factor
  * or destroy, because every solve's FP64 residual reads it.  Host pointer
- * (pinned or pageable): copied into a device buffer owned by the handle.
+ * (pinned or pageable): copied into a device buffer owned by the handle; for
+ * the unpivoted k <= 64 FP32 / FP64 factorisation with p >= 2 (and profile 0)
+ * the copy runs on a further stream of the handle in 16 partition groups (the
+ * columns around every interface first) and each group's band LU starts when
+ * its columns have landed; the call returns after the factorisation, so the
+ * host buffer may be reused at once.
  * Errors: INVALID_ARG (NULL, ld < n), SINGULAR (a zero or non-finite pivot in
  * some A_i; the global row is in lrspike_last_error), CUDA. */
 lrspike_status lrspike_factor(lrspike_handle h, const double *band, int64_t ld);
