@@ -189,7 +189,7 @@ lrspike_status lrspike_create(const lrspike_options *opt, void *cuda_stream, lrs
  * or destroy, because every solve's FP64 residual reads it.  Host pointer
  * (pinned or pageable): copied into a device buffer owned by the handle; for
  * the unpivoted k <= 64 FP32 / FP64 factorisation with p >= 2 (and profile 0)
- * the copy runs on a further stream of the handle in 16 partition groups (the
+ * the copy runs on a further stream of the handle in min(p, 16) partition groups (the
  * columns around every interface first) and each group's band LU starts when
  * its columns have landed; the call returns after the factorisation, so the
  * host buffer may be reused at once.
